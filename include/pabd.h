@@ -1,0 +1,202 @@
+/*
+ * pabd.h -- C-ABI of the GB300 (sm_103a) Projective Affine Body Dynamics library.
+ *
+ * One time step is Algorithm 1 of "Projective Affine Body Dynamics for Multibody Systems":
+ * collision detection, the quaternion predictor, n_iter sweeps of the global solve
+ * (Eq. 19, one 12x12 system per affine body, no global Hessian) and the local solve
+ * (polar rotation, Sec. 4.3), then the velocity recovery of Sec. 4.4.  Every stage runs
+ * in CUDA kernels on the caller's stream; the host only enqueues work.
+ *
+ * Conventions shared by every call:
+ *   - All descriptors passed in are copied; the caller keeps ownership of its memory.
+ *     Host output buffers are caller-owned and must hold the documented number of values.
+ *   - Body and bond ids are dense and follow insertion order; they fix the deterministic
+ *     summation order of the per-body gathers, so results are identical run to run.
+ *   - Bodies of one group (an independent scene inside a batch) must be added
+ *     contiguously, with non-decreasing group ids starting at 0.
+ *   - pabd_add_* is legal only before the first pabd_step / pabd_detect; afterwards it
+ *     returns PABD_ERR_STATE.
+ *   - Kernels run asynchronously on desc.stream.  A device-side error (capacity overflow,
+ *     non-finite state) is latched on the device and returned by the next call that
+ *     synchronises (pabd_sync, pabd_read_*), or by pabd_step once the earlier work is done.
+ *   - Every function returns PABD_ERR_ARG for NULL handles or out-of-range arguments and
+ *     PABD_ERR_CUDA when a CUDA runtime call fails (see pabd_last_cuda_error).
+ */
+#ifndef PABD_H
+#define PABD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PABD_OK = 0,
+    PABD_ERR_ARG = 1,       /* invalid argument */
+    PABD_ERR_OOM = 2,       /* device allocation failed */
+    PABD_ERR_CAPACITY = 3,  /* more pairs / contacts than the scene's capacity (truncated) */
+    PABD_ERR_DIVERGED = 4,  /* a body's state became non-finite */
+    PABD_ERR_TIMEOUT = 5,   /* a bounded device-side wait gave up */
+    PABD_ERR_CUDA = 6,      /* a CUDA runtime call failed */
+    PABD_ERR_STATE = 7      /* call not legal in the scene's current state */
+} pabd_status;
+
+#define PABD_WORLD 0xFFFFFFFFu
+
+/* Bond types.  Energies Psi(d) of the distance d between the two material points
+ * (Eq. 10-11, 15-17), split phi = phi+ + phi- for the semi-implicit sweep:
+ *   SPHERICAL   zero-length bond, Psi = kappa d^2 / 2 (spherical joint)
+ *   SPRING      Psi = kappa (d - rest_len)^2 / 2 (Eq. 26); phi+ = kappa d, phi- = -kappa l
+ *   ELASTIC_NL  phi = (kappa/3)(d^3/l^2 - l): strain-stiffening, small-strain stiffness kappa;
+ *               phi+ = phi'(d) d, phi- = phi(d) - phi'(d) d
+ *   REVOLUTE    hinge about `axis` (body_i frame) through the pivot: two zero-length bonds
+ *               at pivot +- arm * axis in both bodies' frames (creates 2 bond ids)
+ *   DRIVE       zero-length bond pulling the child point pivot_j + arm * r_j to the parent
+ *               point pivot_i + arm * Rot(axis, theta(t)) r_i, theta(t) = drive_amp *
+ *               sin(2 pi t / drive_period + drive_phase), t the end time of the step;
+ *               r_i is a fixed unit vector orthogonal to the axis.
+ * Directions given in body_i's frame are carried into body_j's frame through the bodies'
+ * orientations at the time the bond is added. */
+typedef enum {
+    PABD_SPHERICAL = 0,
+    PABD_SPRING = 1,
+    PABD_ELASTIC_NL = 2,
+    PABD_REVOLUTE = 3,
+    PABD_DRIVE = 4
+} pabd_bond_type;
+
+typedef struct pabd_scene pabd_scene; /* opaque, owned by the library */
+
+/* Scene parameters.  Ground and contacts are scene-level (Alg. 1 "collision detection");
+ * contact bonds are rebuilt every step and are never added by the user. */
+typedef struct {
+    double h;                 /* time step */
+    double gravity[3];
+    int n_iter;               /* fixed number of global/local sweeps per step (>= 1) */
+    int has_ground;           /* ground plane ground_n . y = ground_d */
+    double ground_n[3];
+    double ground_d;
+    double mu;                /* Coulomb friction coefficient of every contact */
+    double c_kappa;           /* contact stiffness kappa_c = c_kappa * min(m_i, m_j) / h^2 */
+    double d_hat_rel;         /* contact distance dhat = d_hat_rel * smallest edge of the body */
+    double margin;            /* absolute extra inflation of every body's contact box */
+    int project;              /* 1: local solve (polar rotation); 0: affine bodies */
+    int body_contacts;        /* 0: only ground contacts */
+    double large_he;          /* bodies with a half extent above this skip the grid */
+    int precision_policy;     /* 0: FP32 solves; 1: FP64 per-body solve where ill-conditioned */
+    size_t max_pairs;         /* capacities; 0 = 16 per body */
+    size_t max_contacts;      /* 0 = 24 per body */
+    void* stream;             /* cudaStream_t on which all work is enqueued (NULL: default) */
+    /* optional device allocator (e.g. a framework's caching allocator); NULL: cudaMalloc */
+    void* (*alloc)(size_t bytes, void* ctx);
+    void (*free)(void* ptr, void* ctx);
+    void* alloc_ctx;
+} pabd_scene_desc;
+
+/* A box body: half extents he, material origin at the centre of mass (so the generalised
+ * mass of Thm 4.1 is block diagonal with Pi_0 = m diag(he^2)/3).  quat is (x, y, z, w). */
+typedef struct {
+    double he[3];
+    double mass;
+    double c[3];
+    double quat[4];
+    double v[3];
+    double omega[3];          /* world frame */
+    int pinned;               /* kinematic: never moves, infinite mass */
+    int group;                /* independent scene id (no contacts across groups) */
+} pabd_body_desc;
+
+typedef struct {
+    int type;                 /* pabd_bond_type */
+    uint32_t body_i, body_j;  /* body_j may be PABD_WORLD (then x_j is a world point) */
+    double x_i[3], x_j[3];    /* material points (pivots for REVOLUTE / DRIVE) */
+    double axis[3];           /* REVOLUTE / DRIVE axis in body_i's frame */
+    double kappa, rest_len, arm;
+    double drive_amp, drive_period, drive_phase;
+} pabd_bond_desc;
+
+/* State rows exchanged with the host: 22 doubles per body,
+ * c[3], A[9] (row-major, rows a_k of Eq. 1), quat[4] (x, y, z, w), v[3], omega[3]. */
+#define PABD_STATE_COLS 22
+
+typedef struct {
+    int64_t n_bodies, n_groups, n_static_bonds, n_bonds, n_pairs, n_contacts;
+    int64_t step_index;
+    int64_t max_pairs, max_contacts;
+    int64_t graph_nodes;      /* kernel + memset nodes of one captured step */
+    int64_t launches;         /* kernels launched by this scene so far */
+    int64_t fp64_bodies;      /* bodies whose solve is statically flagged for FP64 */
+    int64_t device_bytes;     /* device memory held by the scene */
+} pabd_info;
+
+/* Create an empty scene on the current CUDA device.  *out receives the handle. */
+pabd_status pabd_create_scene(const pabd_scene_desc* desc, pabd_scene** out);
+
+/* Append one body; *out_id (may be NULL) receives its id. */
+pabd_status pabd_add_body(pabd_scene* s, const pabd_body_desc* b, uint32_t* out_id);
+
+/* Append one user bond. out_ids (capacity >= 2, may be NULL) receives the internal bond
+ * ids it expands to; *n_out (may be NULL) their number (REVOLUTE: 2, others: 1). */
+pabd_status pabd_add_bond(pabd_scene* s, const pabd_bond_desc* b, uint32_t* out_ids, int* n_out);
+
+/* Advance nsteps time steps (asynchronous on desc.stream; one CUDA graph launch each). */
+pabd_status pabd_step(pabd_scene* s, int nsteps);
+
+/* Same work launched kernel by kernel without the CUDA graph (the plain path). */
+pabd_status pabd_step_eager(pabd_scene* s, int nsteps);
+
+/* Stage timing.  With profiling on, pabd_step launches a second captured graph that also
+ * records CUDA events between the stages, waits for each step and accumulates the times
+ * (milliseconds) read back by pabd_read_profile into PABD_PROFILE_SLOTS doubles:
+ *   [0] steps, [1] drives + collision detection, [2] CSR build, [3] predictor,
+ *   [4] bond kernels, [5] solve kernels, [6] finalize + residual, [7] bond launches,
+ *   [8] solve launches, [9] whole steps, [10] sum over steps of the bond count.
+ * reset != 0 clears the accumulators after reading. */
+#define PABD_PROFILE_SLOTS 11
+pabd_status pabd_set_profiling(pabd_scene* s, int on);
+pabd_status pabd_read_profile(pabd_scene* s, double* out, size_t n, int reset);
+
+/* Collision detection only, on the current state (fills pairs and contacts). */
+pabd_status pabd_detect(pabd_scene* s);
+
+/* Wait for the scene's stream; returns the first latched device error, if any. */
+pabd_status pabd_sync(pabd_scene* s);
+
+/* Copy the state of all bodies to / from host rows (n_bodies x PABD_STATE_COLS doubles).
+ * Reads synchronise; writes are ordered on the stream before later steps. */
+pabd_status pabd_read_state(pabd_scene* s, double* host_rows, size_t n_bodies);
+pabd_status pabd_write_state(pabd_scene* s, const double* host_rows, size_t n_bodies);
+
+/* Set the index n of the next step (its end time is (n + 1) h, used by DRIVE bonds);
+ * ordered on the stream like a state write. */
+pabd_status pabd_set_step_index(pabd_scene* s, int64_t step_index);
+
+/* Broad-phase pairs of the last detection: *n receives the count; up to cap (i, j)
+ * int32 pairs (i < j, sorted) are written to host_pairs. */
+pabd_status pabd_read_pairs(pabd_scene* s, int32_t* host_pairs, size_t cap, size_t* n);
+
+/* Contact bonds of the last detection, in bond order: meta (type 5 = body-body, 6 =
+ * ground; i; j or -1) as 3 int32 per contact, data as 11 float per contact:
+ * x_i[3], x_j[3] (material point of j, or world anchor), N[3], dhat, w = h^2 kappa_c. */
+pabd_status pabd_read_contacts(pabd_scene* s, int32_t* host_meta, float* host_data, size_t cap, size_t* n);
+
+/* Per-group residual sqrt(sum_i |q_i^{k+1} - q_i^k|^2) of the last sweep of the last step. */
+pabd_status pabd_read_residual(pabd_scene* s, double* host_out, size_t n_groups);
+
+pabd_status pabd_get_info(pabd_scene* s, pabd_info* info);
+
+/* Release all device memory of the scene (synchronises its stream). */
+pabd_status pabd_destroy_scene(pabd_scene* s);
+
+const char* pabd_status_str(pabd_status st);
+
+/* Text of the last CUDA runtime error seen by the library in this thread. */
+const char* pabd_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PABD_H */

@@ -1,0 +1,371 @@
+"""Python binding of the GB300 Projective Affine Body Dynamics library (``libpabd.so``).
+
+Argument marshalling only: every stage of a step runs in the library's CUDA kernels.
+The module-level functions carry the C-ABI's names (``pabd_create_scene``,
+``pabd_add_body``, ``pabd_add_bond``, ``pabd_step``, ``pabd_read_state`` ...); ``Scene``
+builds a library scene from a ``scenes.Scene`` description.  PyTorch is used only to
+provide the device memory (its caching allocator) and the CUDA stream.
+
+Importing this package raises ImportError when ``libpabd.so`` has not been built (run
+``__graft_entry__.build()``): there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpabd.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first (python -c "
+                      "'import __graft_entry__ as g; g.build()')")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+STATE_COLS = 22
+WORLD = 0xFFFFFFFF
+OK, ERR_ARG, ERR_OOM, ERR_CAPACITY, ERR_DIVERGED, ERR_TIMEOUT, ERR_CUDA, ERR_STATE = range(8)
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+D3 = ctypes.c_double * 3
+
+
+class pabd_scene_desc(ctypes.Structure):
+    _fields_ = [
+        ("h", ctypes.c_double), ("gravity", D3), ("n_iter", ctypes.c_int),
+        ("has_ground", ctypes.c_int), ("ground_n", D3), ("ground_d", ctypes.c_double),
+        ("mu", ctypes.c_double), ("c_kappa", ctypes.c_double), ("d_hat_rel", ctypes.c_double),
+        ("margin", ctypes.c_double), ("project", ctypes.c_int), ("body_contacts", ctypes.c_int),
+        ("large_he", ctypes.c_double), ("precision_policy", ctypes.c_int),
+        ("max_pairs", ctypes.c_size_t), ("max_contacts", ctypes.c_size_t),
+        ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
+    ]
+
+
+class pabd_body_desc(ctypes.Structure):
+    _fields_ = [
+        ("he", D3), ("mass", ctypes.c_double), ("c", D3), ("quat", ctypes.c_double * 4),
+        ("v", D3), ("omega", D3), ("pinned", ctypes.c_int), ("group", ctypes.c_int),
+    ]
+
+
+class pabd_bond_desc(ctypes.Structure):
+    _fields_ = [
+        ("type", ctypes.c_int), ("body_i", ctypes.c_uint32), ("body_j", ctypes.c_uint32),
+        ("x_i", D3), ("x_j", D3), ("axis", D3), ("kappa", ctypes.c_double), ("rest_len", ctypes.c_double),
+        ("arm", ctypes.c_double), ("drive_amp", ctypes.c_double), ("drive_period", ctypes.c_double),
+        ("drive_phase", ctypes.c_double),
+    ]
+
+
+class pabd_info(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "n_bodies", "n_groups", "n_static_bonds", "n_bonds", "n_pairs", "n_contacts", "step_index",
+        "max_pairs", "max_contacts", "graph_nodes", "launches", "fp64_bodies", "device_bytes")]
+
+
+_P = ctypes.c_void_p
+_PD = ctypes.POINTER(ctypes.c_double)
+_PF = ctypes.POINTER(ctypes.c_float)
+_PI32 = ctypes.POINTER(ctypes.c_int32)
+_PU32 = ctypes.POINTER(ctypes.c_uint32)
+_PSZ = ctypes.POINTER(ctypes.c_size_t)
+
+_SIGS = {
+    "pabd_create_scene": [ctypes.POINTER(pabd_scene_desc), ctypes.POINTER(_P)],
+    "pabd_add_body": [_P, ctypes.POINTER(pabd_body_desc), _PU32],
+    "pabd_add_bond": [_P, ctypes.POINTER(pabd_bond_desc), _PU32, ctypes.POINTER(ctypes.c_int)],
+    "pabd_step": [_P, ctypes.c_int],
+    "pabd_step_eager": [_P, ctypes.c_int],
+    "pabd_detect": [_P],
+    "pabd_sync": [_P],
+    "pabd_read_state": [_P, _PD, ctypes.c_size_t],
+    "pabd_write_state": [_P, _PD, ctypes.c_size_t],
+    "pabd_set_step_index": [_P, ctypes.c_int64],
+    "pabd_set_profiling": [_P, ctypes.c_int],
+    "pabd_read_profile": [_P, _PD, ctypes.c_size_t, ctypes.c_int],
+    "pabd_read_pairs": [_P, _PI32, ctypes.c_size_t, _PSZ],
+    "pabd_read_contacts": [_P, _PI32, _PF, ctypes.c_size_t, _PSZ],
+    "pabd_read_residual": [_P, _PD, ctypes.c_size_t],
+    "pabd_get_info": [_P, ctypes.POINTER(pabd_info)],
+    "pabd_destroy_scene": [_P],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = ctypes.c_int
+_lib.pabd_status_str.argtypes = [ctypes.c_int]
+_lib.pabd_status_str.restype = ctypes.c_char_p
+_lib.pabd_last_cuda_error.argtypes = []
+_lib.pabd_last_cuda_error.restype = ctypes.c_char_p
+
+EXPORTED = sorted(list(_SIGS) + ["pabd_status_str", "pabd_last_cuda_error"])
+
+
+class PabdError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = _lib.pabd_status_str(code).decode()
+        if code == ERR_CUDA:
+            msg += ": " + _lib.pabd_last_cuda_error().decode()
+        super().__init__(f"{where}: {msg}")
+        self.code = code
+
+
+def _check(code: int, where: str, allow=()):
+    if code != OK and code not in allow:
+        raise PabdError(code, where)
+    return code
+
+
+# ---- C-ABI, same names, argument marshalling only ----
+
+def pabd_create_scene(desc: pabd_scene_desc):
+    h = _P()
+    _check(_lib.pabd_create_scene(ctypes.byref(desc), ctypes.byref(h)), "pabd_create_scene")
+    return h
+
+
+def pabd_add_body(s, body: pabd_body_desc) -> int:
+    out = ctypes.c_uint32()
+    _check(_lib.pabd_add_body(s, ctypes.byref(body), ctypes.byref(out)), "pabd_add_body")
+    return out.value
+
+
+def pabd_add_bond(s, bond: pabd_bond_desc):
+    ids = (ctypes.c_uint32 * 2)()
+    n = ctypes.c_int()
+    _check(_lib.pabd_add_bond(s, ctypes.byref(bond), ids, ctypes.byref(n)), "pabd_add_bond")
+    return list(ids[: n.value])
+
+
+def pabd_step(s, nsteps: int = 1):
+    return _check(_lib.pabd_step(s, nsteps), "pabd_step")
+
+
+def pabd_step_eager(s, nsteps: int = 1):
+    return _check(_lib.pabd_step_eager(s, nsteps), "pabd_step_eager")
+
+
+def pabd_detect(s):
+    return _check(_lib.pabd_detect(s), "pabd_detect")
+
+
+def pabd_sync(s, allow=()):
+    return _check(_lib.pabd_sync(s), "pabd_sync", allow)
+
+
+def pabd_read_state(s, n_bodies: int, out: np.ndarray | None = None) -> np.ndarray:
+    if out is None:
+        out = np.empty((n_bodies, STATE_COLS), dtype=np.float64)
+    assert out.dtype == np.float64 and out.flags.c_contiguous and out.shape == (n_bodies, STATE_COLS)
+    _check(_lib.pabd_read_state(s, out.ctypes.data_as(_PD), n_bodies), "pabd_read_state")
+    return out
+
+
+def pabd_write_state(s, rows: np.ndarray):
+    rows = np.ascontiguousarray(rows, dtype=np.float64)
+    _check(_lib.pabd_write_state(s, rows.ctypes.data_as(_PD), rows.shape[0]), "pabd_write_state")
+
+
+def pabd_set_step_index(s, k: int):
+    _check(_lib.pabd_set_step_index(s, int(k)), "pabd_set_step_index")
+
+
+PROFILE_KEYS = ("steps", "collision_ms", "csr_ms", "predict_ms", "bond_ms", "solve_ms", "finalize_ms",
+                "bond_launches", "solve_launches", "step_ms", "bonds_sum")
+
+
+def pabd_set_profiling(s, on: bool):
+    _check(_lib.pabd_set_profiling(s, int(bool(on))), "pabd_set_profiling")
+
+
+def pabd_read_profile(s, reset: bool = False) -> dict:
+    out = np.zeros(len(PROFILE_KEYS))
+    _check(_lib.pabd_read_profile(s, out.ctypes.data_as(_PD), len(PROFILE_KEYS), int(bool(reset))),
+           "pabd_read_profile")
+    return dict(zip(PROFILE_KEYS, out.tolist()))
+
+
+def pabd_read_pairs(s) -> np.ndarray:
+    n = ctypes.c_size_t()
+    _check(_lib.pabd_read_pairs(s, None, 0, ctypes.byref(n)), "pabd_read_pairs", (ERR_CAPACITY,))
+    out = np.zeros((max(n.value, 1), 2), dtype=np.int32)
+    _check(_lib.pabd_read_pairs(s, out.ctypes.data_as(_PI32), n.value, ctypes.byref(n)), "pabd_read_pairs",
+           (ERR_CAPACITY,))
+    return out[: n.value]
+
+
+def pabd_read_contacts(s):
+    n = ctypes.c_size_t()
+    _check(_lib.pabd_read_contacts(s, None, None, 0, ctypes.byref(n)), "pabd_read_contacts", (ERR_CAPACITY,))
+    meta = np.zeros((max(n.value, 1), 3), dtype=np.int32)
+    data = np.zeros((max(n.value, 1), 11), dtype=np.float32)
+    _check(_lib.pabd_read_contacts(s, meta.ctypes.data_as(_PI32), data.ctypes.data_as(_PF), n.value,
+                                   ctypes.byref(n)), "pabd_read_contacts", (ERR_CAPACITY,))
+    return meta[: n.value], data[: n.value]
+
+
+def pabd_read_residual(s, n_groups: int) -> np.ndarray:
+    out = np.zeros(max(n_groups, 1))
+    _check(_lib.pabd_read_residual(s, out.ctypes.data_as(_PD), n_groups), "pabd_read_residual")
+    return out[:n_groups]
+
+
+def pabd_get_info(s) -> dict:
+    info = pabd_info()
+    _check(_lib.pabd_get_info(s, ctypes.byref(info)), "pabd_get_info")
+    return {n: getattr(info, n) for n, _ in pabd_info._fields_}
+
+
+def pabd_destroy_scene(s):
+    return _check(_lib.pabd_destroy_scene(s), "pabd_destroy_scene")
+
+
+# ---- torch plumbing: device memory and stream ----
+
+class _TorchAllocator:
+    """Routes the library's device allocations through PyTorch's caching allocator."""
+
+    def __init__(self, device: int, stream: int):
+        import torch
+        self._torch = torch
+        self.device = device
+        self.stream = stream
+        self.alloc_cb = ALLOC_FN(self._alloc)
+        self.free_cb = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, ctx):
+        try:
+            return self._torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream)
+        except Exception:
+            return None
+
+    def _free(self, ptr, ctx):
+        self._torch.cuda.caching_allocator_delete(ptr)
+
+
+def scene_desc(params: dict, stream=0, allocator: _TorchAllocator | None = None, precision_policy=1,
+               max_pairs=0, max_contacts=0) -> pabd_scene_desc:
+    d = pabd_scene_desc()
+    d.h = params["h"]
+    d.gravity = D3(*params["gravity"])
+    d.n_iter = int(params["n_iter"])
+    d.has_ground = int(params["has_ground"])
+    d.ground_n = D3(*params["ground_n"])
+    d.ground_d = params["ground_d"]
+    d.mu = params["mu"]
+    d.c_kappa = params["c_kappa"]
+    d.d_hat_rel = params["d_hat_rel"]
+    d.margin = params["margin"]
+    d.project = int(params["project"])
+    d.body_contacts = int(params["body_contacts"])
+    d.large_he = params["large_he"]
+    d.precision_policy = int(precision_policy)
+    d.max_pairs = int(max_pairs)
+    d.max_contacts = int(max_contacts)
+    d.stream = stream or None
+    if allocator is not None:
+        d.alloc = allocator.alloc_cb
+        d.free = allocator.free_cb
+    else:
+        d.alloc = ALLOC_FN()
+        d.free = FREE_FN()
+    return d
+
+
+class Scene:
+    """A library scene built from a ``scenes.Scene`` (bodies and user bonds)."""
+
+    def __init__(self, scene, device: int = 0, stream=None, torch_memory: bool = True, precision_policy: int = 1,
+                 max_pairs: int = 0, max_contacts: int = 0):
+        import torch
+        torch.cuda.set_device(device)
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.torch_stream = stream
+        self._alloc = _TorchAllocator(device, stream.cuda_stream) if torch_memory else None
+        self.desc = scene_desc(scene.params, stream.cuda_stream, self._alloc, precision_policy, max_pairs,
+                               max_contacts)
+        self.h = pabd_create_scene(self.desc)
+        self.n = scene.n_bodies
+        self.n_groups = scene.n_groups
+        for b in scene.bodies:
+            bd = pabd_body_desc()
+            bd.he = D3(*b["he"])
+            bd.mass = float(b["mass"])
+            bd.c = D3(*b["c"])
+            bd.quat = (ctypes.c_double * 4)(*b["quat"])
+            bd.v = D3(*b["v"])
+            bd.omega = D3(*b["omega"])
+            bd.pinned = int(b["pinned"])
+            bd.group = int(b["group"])
+            pabd_add_body(self.h, bd)
+        for bo in scene.bonds:
+            bb = pabd_bond_desc()
+            bb.type = int(bo["type"])
+            bb.body_i = int(bo["i"])
+            bb.body_j = WORLD if int(bo["j"]) < 0 else int(bo["j"])
+            bb.x_i = D3(*bo["xi"])
+            bb.x_j = D3(*bo["xj"])
+            bb.axis = D3(*bo["axis"])
+            bb.kappa = float(bo["kappa"])
+            bb.rest_len = float(bo["rest"])
+            bb.arm = float(bo["arm"])
+            bb.drive_amp = float(bo["amp"])
+            bb.drive_period = float(bo["period"])
+            bb.drive_phase = float(bo["phase"])
+            pabd_add_bond(self.h, bb)
+
+    def close(self):
+        if getattr(self, "h", None):
+            pabd_destroy_scene(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int = 1):
+        pabd_step(self.h, n)
+
+    def step_eager(self, n: int = 1):
+        pabd_step_eager(self.h, n)
+
+    def detect(self):
+        pabd_detect(self.h)
+
+    def sync(self, allow=()):
+        return pabd_sync(self.h, allow)
+
+    def state(self, out=None) -> np.ndarray:
+        return pabd_read_state(self.h, self.n, out)
+
+    def set_state(self, rows: np.ndarray):
+        pabd_write_state(self.h, rows)
+
+    def set_step_index(self, k: int):
+        pabd_set_step_index(self.h, k)
+
+    def set_profiling(self, on: bool):
+        pabd_set_profiling(self.h, on)
+
+    def profile(self, reset: bool = False) -> dict:
+        return pabd_read_profile(self.h, reset)
+
+    def pairs(self) -> np.ndarray:
+        return pabd_read_pairs(self.h)
+
+    def contacts(self):
+        return pabd_read_contacts(self.h)
+
+    def residual(self) -> np.ndarray:
+        return pabd_read_residual(self.h, self.n_groups)
+
+    def info(self) -> dict:
+        return pabd_get_info(self.h)

@@ -1,0 +1,437 @@
+// Collision detection (Alg. 1, first line) on the device.
+//
+// Broad phase: uniform grid hash.  Every body's inflated AABB is computed in IEEE single
+// precision with a fixed operation order; the cell size is the largest AABB width of the
+// grid bodies (times 1.01), so two overlapping boxes always sit in the same or in adjacent
+// cells.  Bodies are counting-sorted into hash buckets; each body scans the 27 cells around
+// its own and keeps the neighbours j > i whose boxes overlap, whose cell really is the
+// visited one (so hash collisions never duplicate a pair), that share its group and are
+// not joined to it by a user bond.  Bodies larger than the scene's `large_he` bypass the
+// grid and are tested against all bodies.  Each body's partner list is sorted, so the
+// final list is the sorted set of overlapping pairs -- independent of bucket order.
+//
+// Narrow phase: box-box contact manifold (reference face by separating axis over the six
+// face normals, incident face clipped against the reference face's side planes) and
+// corner-vs-ground-plane contacts, all in single precision with the same fixed operation
+// order as the specification in the tests' oracle; contacts are written in pair order
+// (then ground, in body order) through prefix sums, so the contact list is deterministic.
+//
+// All arithmetic here that decides an integer (overlap, inside, face) uses __fmul_rn /
+// __fadd_rn / __fsub_rn so that no multiply-add is contracted into an FMA.
+#include "pabd_internal.h"
+
+namespace pabd {
+
+#define FM(a, b) __fmul_rn((a), (b))
+#define FA(a, b) __fadd_rn((a), (b))
+#define FS(a, b) __fsub_rn((a), (b))
+
+constexpr int CT = 256;  // threads per block for per-body / per-pair kernels
+
+struct FBox {
+    float c[3], A[9], he[3], infl;
+};
+
+__device__ __forceinline__ void load_q(const float4* q, int b, float* c, float* A) {
+    float4 a = q[3 * b], bb = q[3 * b + 1], cc = q[3 * b + 2];
+    c[0] = a.x; c[1] = a.y; c[2] = a.z;
+    A[0] = a.w; A[1] = bb.x; A[2] = bb.y; A[3] = bb.z; A[4] = bb.w;
+    A[5] = cc.x; A[6] = cc.y; A[7] = cc.z; A[8] = cc.w;
+}
+
+__device__ __forceinline__ void load_box(const Dev& d, int b, FBox& f) {
+    load_q(d.qn, b, f.c, f.A);
+    float4 h = d.he[b];
+    f.he[0] = h.x; f.he[1] = h.y; f.he[2] = h.z;
+    f.infl = d.lo[b].w;
+}
+
+// inflation of one body: (dhat + h*|v|) + margin, dhat = d_hat_rel * (2 * min he)
+__device__ __forceinline__ float body_infl(const Dev& d, int b) {
+    float4 h = d.he[b];
+    float4 v = d.vel[b];
+    float dh = FM(d.p.d_hat_rel, FM(2.0f, fminf(fminf(h.x, h.y), h.z)));
+    float sp = __fsqrt_rn(FA(FA(FM(v.x, v.x), FM(v.y, v.y)), FM(v.z, v.z)));
+    return FA(FA(dh, FM(d.p.h, sp)), d.p.margin);
+}
+
+__global__ void k_aabb(Dev d) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= d.N) return;
+    float c[3], A[9];
+    load_q(d.qn, b, c, A);
+    float4 h = d.he[b];
+    float infl = body_infl(d, b);
+    float lo[3], hi[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float e = FA(FA(FA(FM(fabsf(A[3 * k]), h.x), FM(fabsf(A[3 * k + 1]), h.y)), FM(fabsf(A[3 * k + 2]), h.z)), infl);
+        lo[k] = FS(c[k], e);
+        hi[k] = FA(c[k], e);
+    }
+    d.lo[b] = make_float4(lo[0], lo[1], lo[2], infl);
+    d.hi[b] = make_float4(hi[0], hi[1], hi[2], 0.f);
+    if (!(d.bflags[b] & BF_LARGE)) {
+        float w = fmaxf(fmaxf(hi[0] - lo[0], hi[1] - lo[1]), hi[2] - lo[2]);
+        w = w * 1.01f + 1e-6f;
+        if (w < 1e30f) atomicMax(&d.ctr[C_CELLBITS], __float_as_int(w));  // positive floats order as ints
+    }
+}
+
+__device__ __forceinline__ int cell_coord(float x, float inv_cs) {
+    float t = floorf(x * inv_cs);
+    t = fminf(fmaxf(t, -1048576.f), 1048576.f);
+    return (int)t;
+}
+
+__device__ __forceinline__ int cell_hash(int x, int y, int z, int bits) {
+    unsigned h = (unsigned)x * 73856093u ^ (unsigned)y * 19349663u ^ (unsigned)z * 83492791u;
+    h ^= h >> 16;
+    h *= 0x7feb352du;
+    h ^= h >> 15;
+    return (int)(h & ((1u << bits) - 1u));
+}
+
+__global__ void k_cells(Dev d) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= d.N) return;
+    if (d.bflags[b] & BF_LARGE) { d.cell[b] = make_int4(0, 0, 0, -1); return; }
+    float cs = __int_as_float(d.ctr[C_CELLBITS]);
+    float inv = 1.0f / cs;
+    float4 a = d.qn[3 * b];
+    int x = cell_coord(a.x, inv), y = cell_coord(a.y, inv), z = cell_coord(a.z, inv);
+    int hb = cell_hash(x, y, z, d.table_bits);
+    d.cell[b] = make_int4(x, y, z, hb);
+    atomicAdd(&d.bucket_cnt[hb], 1);
+}
+
+__global__ void k_bucket_fill(Dev d) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= d.N) return;
+    int hb = d.cell[b].w;
+    if (hb < 0) return;
+    int pos = d.bucket_off[hb] + atomicAdd(&d.bucket_cur[hb], 1);
+    d.bucket_items[pos] = b;
+}
+
+__device__ __forceinline__ bool overlap(const float4& la, const float4& ha, const float4& lb, const float4& hb) {
+    return la.x <= hb.x && lb.x <= ha.x && la.y <= hb.y && lb.y <= ha.y && la.z <= hb.z && lb.z <= ha.z;
+}
+
+// pairs joined by a user bond never collide: binary search in the body's sorted list of
+// bonded partners (a CSR built once on the host)
+__device__ __forceinline__ bool adj_has(const Dev& d, int a, int b) {
+    if (!d.adj_off) return false;
+    int lo = d.adj_off[a], hi = d.adj_off[a + 1];
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        int v = d.adj_nbr[mid];
+        if (v == b) return true;
+        if (v < b) lo = mid + 1; else hi = mid;
+    }
+    return false;
+}
+
+__device__ __forceinline__ bool pair_ok(const Dev& d, int i, int j, int gi, int fi) {
+    if (d.group[j] != gi) return false;
+    int fj = d.bflags[j];
+    if ((fi & BF_PINNED) && (fj & BF_PINNED)) return false;
+    if (!overlap(d.lo[i], d.hi[i], d.lo[j], d.hi[j])) return false;
+    if (adj_has(d, i, j)) return false;
+    return true;
+}
+
+// Visit the partners j > i of body i in a fixed order; F(j) is called for each accepted j.
+template <class F>
+__device__ __forceinline__ void for_partners(const Dev& d, int i, F&& f) {
+    const int gi = d.group[i], fi = d.bflags[i];
+    if (fi & BF_LARGE) {
+        for (int j = i + 1; j < d.N; ++j)
+            if (pair_ok(d, i, j, gi, fi)) f(j);
+        return;
+    }
+    const int4 ci = d.cell[i];
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                int x = ci.x + dx, y = ci.y + dy, z = ci.z + dz;
+                int hb = cell_hash(x, y, z, d.table_bits);
+                int s = d.bucket_off[hb], e = d.bucket_off[hb + 1];
+                for (int k = s; k < e; ++k) {
+                    int j = d.bucket_items[k];
+                    if (j <= i) continue;
+                    int4 cj = d.cell[j];
+                    if (cj.x != x || cj.y != y || cj.z != z) continue;
+                    if (pair_ok(d, i, j, gi, fi)) f(j);
+                }
+            }
+    for (int k = 0; k < d.Nlarge; ++k) {
+        int j = d.large_ids[k];
+        if (j > i && pair_ok(d, i, j, gi, fi)) f(j);
+    }
+}
+
+__global__ void k_pair_count(Dev d) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.N) return;
+    int n = 0;
+    if (d.p.body_contacts) for_partners(d, i, [&](int) { ++n; });
+    d.pair_cnt[i] = n;
+}
+
+__global__ void k_pair_write(Dev d) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.N) return;
+    const int s = d.pair_off[i];
+    const int cap = d.cap_pairs;
+    int n = 0;
+    if (d.p.body_contacts) for_partners(d, i, [&](int j) {
+        if (s + n < cap) d.pairs[s + n] = make_int2(i, j);
+        ++n;
+    });
+    int e = min(s + n, cap);
+    // insertion sort of the partner list (ascending j)
+    for (int a = s + 1; a < e; ++a) {
+        int2 v = d.pairs[a];
+        int b = a - 1;
+        while (b >= s && d.pairs[b].y > v.y) { d.pairs[b + 1] = d.pairs[b]; --b; }
+        d.pairs[b + 1] = v;
+    }
+    if (i == d.N - 1) {
+        int tot = d.pair_off[d.N];
+        if (tot > cap) atomicOr(&d.ctr[C_STATUS], ST_CAPACITY);
+        d.ctr[C_NPAIRS] = min(tot, cap);
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// narrow phase
+// ------------------------------------------------------------------------------------
+
+struct CPt {
+    float u[3], x[3];
+};
+
+__device__ __forceinline__ float dot_col(const float* A, int l, const float* r) {
+    return FA(FA(FM(A[l], r[0]), FM(A[3 + l], r[1])), FM(A[6 + l], r[2]));
+}
+
+// Manifold of the pair (a, b); calls emit(i, j, x_i, x_j, N) for each contact, returns count.
+template <class Emit>
+__device__ int box_box(const FBox& fa, const FBox& fb, int a, int b, Emit&& emit) {
+    const float delta = FA(fa.infl, fb.infl);
+    float dv[3], dab[3], dba[3], R[9];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) dv[k] = FS(fa.c[k], fb.c[k]);
+#pragma unroll
+    for (int l = 0; l < 3; ++l) dab[l] = dot_col(fb.A, l, dv);
+    float dn[3] = {-dv[0], -dv[1], -dv[2]};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) dba[k] = dot_col(fa.A, k, dn);
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            R[3 * l + k] = FA(FA(FM(fb.A[l], fa.A[k]), FM(fb.A[3 + l], fa.A[3 + k])), FM(fb.A[6 + l], fa.A[6 + k]));
+    float best = 0.f;
+    int ref_b = 1, l = 0;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        float ext = FA(FA(FM(fabsf(R[3 * ax]), fa.he[0]), FM(fabsf(R[3 * ax + 1]), fa.he[1])), FM(fabsf(R[3 * ax + 2]), fa.he[2]));
+        float sep = FS(fabsf(dab[ax]), FA(fb.he[ax], ext));
+        if (ax == 0 || sep > best) { best = sep; ref_b = 1; l = ax; }
+    }
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        float ext = FA(FA(FM(fabsf(R[ax]), fb.he[0]), FM(fabsf(R[3 + ax]), fb.he[1])), FM(fabsf(R[6 + ax]), fb.he[2]));
+        float sep = FS(fabsf(dba[ax]), FA(fa.he[ax], ext));
+        if (sep > best) { best = sep; ref_b = 0; l = ax; }
+    }
+    if (!(best <= delta)) return 0;
+    const FBox& fr = ref_b ? fb : fa;
+    const FBox& fi = ref_b ? fa : fb;
+    const int ir = ref_b ? b : a, ii = ref_b ? a : b;
+    const float sg = ref_b ? (dab[l] >= 0.f ? 1.f : -1.f) : (dba[l] >= 0.f ? 1.f : -1.f);
+    float N[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) N[k] = FM(sg, fr.A[3 * k + l]);
+    int ki = 0;
+    float bestd = 0.f, dsel = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float dk = dot_col(fi.A, k, N);
+        if (k == 0 || fabsf(dk) > bestd) { bestd = fabsf(dk); ki = k; dsel = dk; }
+    }
+    const float si = dsel > 0.f ? -1.f : 1.f;
+    const int k1 = (ki + 1) % 3, k2 = (ki + 2) % 3;
+    const float sgn1[4] = {1.f, -1.f, -1.f, 1.f}, sgn2[4] = {1.f, 1.f, -1.f, -1.f};
+    CPt poly[8], tmp[8];
+    int np = 4;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        float x[3], y[3], r[3];
+        x[ki] = FM(si, fi.he[ki]);
+        x[k1] = FM(sgn1[v], fi.he[k1]);
+        x[k2] = FM(sgn2[v], fi.he[k2]);
+#pragma unroll
+        for (int dd = 0; dd < 3; ++dd) {
+            y[dd] = FA(FA(FA(fi.c[dd], FM(fi.A[3 * dd], x[0])), FM(fi.A[3 * dd + 1], x[1])), FM(fi.A[3 * dd + 2], x[2]));
+            r[dd] = FS(y[dd], fr.c[dd]);
+        }
+#pragma unroll
+        for (int m = 0; m < 3; ++m) { poly[v].u[m] = dot_col(fr.A, m, r); poly[v].x[m] = x[m]; }
+    }
+    const int m1 = (l + 1) % 3, m2 = (l + 2) % 3;
+    for (int pl = 0; pl < 4 && np > 0; ++pl) {
+        const int m = pl < 2 ? m1 : m2;
+        const float ps = (pl & 1) ? -1.f : 1.f, lim = fr.he[m];
+        int nt = 0;
+        for (int v = 0; v < np; ++v) {
+            const CPt& P = poly[v];
+            const CPt& Q = poly[(v + 1) % np];
+            float dp = FS(FM(ps, P.u[m]), lim), dq = FS(FM(ps, Q.u[m]), lim);
+            bool pin = dp <= 0.f, qin = dq <= 0.f;
+            if (pin) tmp[nt++] = P;
+            if (pin != qin) {
+                float t = __fdiv_rn(dp, FS(dp, dq));
+                CPt X;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    X.u[c] = FA(P.u[c], FM(t, FS(Q.u[c], P.u[c])));
+                    X.x[c] = FA(P.x[c], FM(t, FS(Q.x[c], P.x[c])));
+                }
+                tmp[nt++] = X;
+            }
+        }
+        np = nt;
+        for (int v = 0; v < nt; ++v) poly[v] = tmp[v];
+    }
+    int cnt = 0;
+    for (int v = 0; v < np; ++v) {
+        float hgt = FS(FM(sg, poly[v].u[l]), fr.he[l]);
+        if (!(hgt < delta)) continue;
+        float xj[3] = {poly[v].u[0], poly[v].u[1], poly[v].u[2]};
+        xj[l] = FM(sg, fr.he[l]);
+        emit(ii, ir, poly[v].x, xj, N, cnt);
+        ++cnt;
+    }
+    return cnt;
+}
+
+template <class Emit>
+__device__ int ground_corners(const Dev& d, const FBox& fa, int a, Emit&& emit) {
+    int cnt = 0;
+#pragma unroll 1
+    for (int k = 0; k < 8; ++k) {
+        float x[3] = {(k & 1) ? fa.he[0] : -fa.he[0], (k & 2) ? fa.he[1] : -fa.he[1], (k & 4) ? fa.he[2] : -fa.he[2]};
+        float y[3];
+#pragma unroll
+        for (int dd = 0; dd < 3; ++dd)
+            y[dd] = FA(FA(FA(fa.c[dd], FM(fa.A[3 * dd], x[0])), FM(fa.A[3 * dd + 1], x[1])), FM(fa.A[3 * dd + 2], x[2]));
+        float g = FS(FA(FA(FM(d.p.gn[0], y[0]), FM(d.p.gn[1], y[1])), FM(d.p.gn[2], y[2])), d.p.gd);
+        if (!(g < fa.infl)) continue;
+        float anc[3] = {FS(y[0], FM(g, d.p.gn[0])), FS(y[1], FM(g, d.p.gn[1])), FS(y[2], FM(g, d.p.gn[2]))};
+        emit(a, -1, x, anc, d.p.gn, cnt);
+        ++cnt;
+    }
+    return cnt;
+}
+
+__global__ void k_narrow_count(Dev d) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int np = d.ctr[C_NPAIRS];
+    if (t < np) {
+        int2 pr = d.pairs[t];
+        FBox fa, fb;
+        load_box(d, pr.x, fa);
+        load_box(d, pr.y, fb);
+        d.npc[t] = box_box(fa, fb, pr.x, pr.y, [](int, int, const float*, const float*, const float*, int) {});
+    }
+    if (t < d.N) {
+        int n = 0;
+        if (d.p.has_ground && !(d.bflags[t] & BF_PINNED)) {
+            FBox fa;
+            load_box(d, t, fa);
+            n = ground_corners(d, fa, t, [](int, int, const float*, const float*, const float*, int) {});
+        }
+        d.gnd_cnt[t] = n;
+    }
+}
+
+__device__ __forceinline__ float pair_dhat(const Dev& d, int i, int j) {
+    float di = d.he[i].w;
+    return j < 0 ? di : fminf(di, d.he[j].w);
+}
+
+__device__ __forceinline__ void write_contact(const Dev& d, int slot, int type, int i, int j, const float* xi,
+                                              const float* xj, const float* N) {
+    if (slot >= d.cap_contacts) return;
+    const int b = d.Nc + slot;
+    float mi = d.mass[i].x;
+    float mm;
+    if (j < 0) mm = mi;
+    else {
+        float mj = d.mass[j].x;
+        bool pi = d.bflags[i] & BF_PINNED, pj = d.bflags[j] & BF_PINNED;
+        mm = pj ? mi : (pi ? mj : fminf(mi, mj));
+    }
+    d.bmeta[b] = make_int4(i, j, type, 0);
+    d.bxi[b] = make_float4(xi[0], xi[1], xi[2], d.p.c_kappa * mm);
+    d.bxj[b] = make_float4(xj[0], xj[1], xj[2], pair_dhat(d, i, j));
+    d.bn[b] = make_float4(N[0], N[1], N[2], d.p.mu);
+}
+
+__global__ void k_narrow_write(Dev d) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int np = d.ctr[C_NPAIRS];
+    const int npc = d.npc_off[np];
+    if (t < np) {
+        int2 pr = d.pairs[t];
+        FBox fa, fb;
+        load_box(d, pr.x, fa);
+        load_box(d, pr.y, fb);
+        const int base = d.npc_off[t];
+        box_box(fa, fb, pr.x, pr.y, [&](int i, int j, const float* xi, const float* xj, const float* N, int k) {
+            write_contact(d, base + k, K_CONTACT, i, j, xi, xj, N);
+        });
+    }
+    if (t < d.N && d.gnd_cnt[t] > 0) {
+        FBox fa;
+        load_box(d, t, fa);
+        const int base = npc + d.gnd_off[t];
+        ground_corners(d, fa, t, [&](int i, int j, const float* xi, const float* xj, const float* N, int k) {
+            write_contact(d, base + k, K_GROUND, i, j, xi, xj, N);
+        });
+    }
+    if (t == 0) {
+        int nk = npc + d.gnd_off[d.N];
+        if (nk > d.cap_contacts) { atomicOr(&d.ctr[C_STATUS], ST_CAPACITY); nk = d.cap_contacts; }
+        d.ctr[C_NPC] = min(npc, d.cap_contacts);
+        d.ctr[C_NGC] = nk - min(npc, d.cap_contacts);
+        d.ctr[C_NBONDS] = d.Nc + nk;
+    }
+}
+
+static inline int nblk(int n) { return (n + CT - 1) / CT > 0 ? (n + CT - 1) / CT : 1; }
+
+void launch_collision(const Dev& d, cudaStream_t st, long long* launches) {
+    const int T = 1 << d.table_bits;
+    cudaMemsetAsync(d.bucket_cnt, 0, sizeof(int) * T, st);
+    cudaMemsetAsync(d.bucket_cur, 0, sizeof(int) * T, st);
+    cudaMemsetAsync(d.ctr + C_CELLBITS, 0, sizeof(int), st);
+    k_aabb<<<nblk(d.N), CT, 0, st>>>(d);
+    k_cells<<<nblk(d.N), CT, 0, st>>>(d);
+    scan_exclusive(d.bucket_cnt, d.bucket_off, nullptr, T, d.scan_scratch, st, launches);
+    k_bucket_fill<<<nblk(d.N), CT, 0, st>>>(d);
+    k_pair_count<<<nblk(d.N), CT, 0, st>>>(d);
+    scan_exclusive(d.pair_cnt, d.pair_off, nullptr, d.N, d.scan_scratch, st, launches);
+    k_pair_write<<<nblk(d.N), CT, 0, st>>>(d);
+    const int nt = d.cap_pairs > d.N ? d.cap_pairs : d.N;
+    k_narrow_count<<<nblk(nt), CT, 0, st>>>(d);
+    scan_exclusive(d.npc, d.npc_off, d.ctr + C_NPAIRS, d.cap_pairs, d.scan_scratch, st, launches);
+    scan_exclusive(d.gnd_cnt, d.gnd_off, nullptr, d.N, d.scan_scratch, st, launches);
+    k_narrow_write<<<nblk(nt), CT, 0, st>>>(d);
+    *launches += 7;
+}
+
+}  // namespace pabd

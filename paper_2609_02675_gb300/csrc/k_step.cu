@@ -1,0 +1,215 @@
+// Per-step kernels around the sweep: the predictor and the velocity recovery of Alg. 1,
+// the time-dependent drive anchors, the CSR of bond ends and the per-group residual.
+#include "pabd_internal.h"
+
+namespace pabd {
+
+constexpr int ST_T = 256;
+static inline int nblk(int n) { return n > 0 ? (n + ST_T - 1) / ST_T : 1; }
+
+__device__ __forceinline__ void quat_to_mat(float4 q, float* R) {
+    float x = q.x, y = q.y, z = q.z, w = q.w;
+    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - z * w);       R[2] = 2.f * (x * z + y * w);
+    R[3] = 2.f * (x * y + z * w);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - x * w);
+    R[6] = 2.f * (x * z - y * w);       R[7] = 2.f * (y * z + x * w);       R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+__device__ __forceinline__ void store_q(float4* q, int b, const float* c, const float* A) {
+    q[3 * b] = make_float4(c[0], c[1], c[2], A[0]);
+    q[3 * b + 1] = make_float4(A[1], A[2], A[3], A[4]);
+    q[3 * b + 2] = make_float4(A[5], A[6], A[7], A[8]);
+}
+
+// Predictor (Alg. 1): v* = v + h g; c* = c + h v*; Q* = normalise(Q + h/2 [w, 0] Q);
+// A* = R(Q*); s = q^0 = (c*, A*).  Pinned bodies keep q^n.
+__global__ void k_predict(Dev d) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= d.N) return;
+    if (d.bflags[b] & BF_PINNED) {
+        float4 a0 = d.qn[3 * b], a1 = d.qn[3 * b + 1], a2 = d.qn[3 * b + 2];
+        d.sq[3 * b] = a0; d.sq[3 * b + 1] = a1; d.sq[3 * b + 2] = a2;
+        d.qa[3 * b] = a0; d.qa[3 * b + 1] = a1; d.qa[3 * b + 2] = a2;
+        d.qb[3 * b] = a0; d.qb[3 * b + 1] = a1; d.qb[3 * b + 2] = a2;
+        d.qstar[b] = d.quat[b];
+        return;
+    }
+    const float h = d.p.h;
+    float4 v = d.vel[b], w = d.omg[b], Q = d.quat[b], c4 = d.qn[3 * b];
+    float vs[3] = {v.x + h * d.p.g[0], v.y + h * d.p.g[1], v.z + h * d.p.g[2]};
+    float cs[3] = {c4.x + h * vs[0], c4.y + h * vs[1], c4.z + h * vs[2]};
+    float4 wq = make_float4(w.x * Q.w + (w.y * Q.z - w.z * Q.y), w.y * Q.w + (w.z * Q.x - w.x * Q.z),
+                            w.z * Q.w + (w.x * Q.y - w.y * Q.x), -(w.x * Q.x + w.y * Q.y + w.z * Q.z));
+    const float hh = 0.5f * h;
+    float4 Qn = make_float4(Q.x + hh * wq.x, Q.y + hh * wq.y, Q.z + hh * wq.z, Q.w + hh * wq.w);
+    float inv = rsqrtf(Qn.x * Qn.x + Qn.y * Qn.y + Qn.z * Qn.z + Qn.w * Qn.w);
+    Qn.x *= inv; Qn.y *= inv; Qn.z *= inv; Qn.w *= inv;
+    float A[9];
+    quat_to_mat(Qn, A);
+    store_q(d.sq, b, cs, A);
+    store_q(d.qa, b, cs, A);
+    d.qstar[b] = Qn;
+}
+
+// Rotation matrix -> unit quaternion (Shepperd's method: divide by the largest of
+// 4w^2, 4x^2, 4y^2, 4z^2).
+__device__ __forceinline__ float4 mat_to_quat(const float* R) {
+    float tr = R[0] + R[4] + R[8];
+    float x, y, z, w;
+    if (tr >= R[0] && tr >= R[4] && tr >= R[8]) {
+        float s = sqrtf(1.f + tr) * 2.f;
+        w = 0.25f * s; x = (R[7] - R[5]) / s; y = (R[2] - R[6]) / s; z = (R[3] - R[1]) / s;
+    } else if (R[0] >= R[4] && R[0] >= R[8]) {
+        float s = sqrtf(1.f + R[0] - R[4] - R[8]) * 2.f;
+        x = 0.25f * s; w = (R[7] - R[5]) / s; y = (R[1] + R[3]) / s; z = (R[2] + R[6]) / s;
+    } else if (R[4] >= R[8]) {
+        float s = sqrtf(1.f + R[4] - R[0] - R[8]) * 2.f;
+        y = 0.25f * s; w = (R[2] - R[6]) / s; x = (R[1] + R[3]) / s; z = (R[5] + R[7]) / s;
+    } else {
+        float s = sqrtf(1.f + R[8] - R[0] - R[4]) * 2.f;
+        z = 0.25f * s; w = (R[3] - R[1]) / s; x = (R[2] + R[6]) / s; y = (R[5] + R[7]) / s;
+    }
+    float n = rsqrtf(x * x + y * y + z * z + w * w);
+    return make_float4(x * n, y * n, z * n, w * n);
+}
+
+// Velocity recovery (Alg. 1, Sec. 4.4): v = (c^{n+1} - c^n)/h;
+// [w]x = skew part of (A^{n+1} - A^n)(A^n)^T / h; Q^{n+1} = quat(A^{n+1}), sign-continuous.
+__global__ void k_finalize(Dev d, const float4* __restrict__ qf) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b == 0) atomicAdd((unsigned long long*)d.step_index, 1ull);
+    if (b >= d.N) return;
+    if (d.bflags[b] & BF_PINNED) return;
+    float4 n0 = d.qn[3 * b], n1 = d.qn[3 * b + 1], n2 = d.qn[3 * b + 2];
+    float4 f0 = qf[3 * b], f1 = qf[3 * b + 1], f2 = qf[3 * b + 2];
+    const float c0[3] = {n0.x, n0.y, n0.z}, c1[3] = {f0.x, f0.y, f0.z};
+    const float A0[9] = {n0.w, n1.x, n1.y, n1.z, n1.w, n2.x, n2.y, n2.z, n2.w};
+    const float A1[9] = {f0.w, f1.x, f1.y, f1.z, f1.w, f2.x, f2.y, f2.z, f2.w};
+    const float ih = d.p.inv_h;
+    bool finite = true;
+    float v[3];
+    for (int k = 0; k < 3; ++k) { v[k] = (c1[k] - c0[k]) * ih; finite &= isfinite(c1[k]); }
+    float W[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            float s = 0.f;
+            for (int k = 0; k < 3; ++k) s += (A1[3 * r + k] - A0[3 * r + k]) * A0[3 * c + k];
+            W[3 * r + c] = s * ih;
+        }
+    for (int k = 0; k < 9; ++k) finite &= isfinite(A1[k]);
+    if (!finite) atomicOr(&d.ctr[C_STATUS], ST_DIVERGED);
+    d.vel[b] = make_float4(v[0], v[1], v[2], 0.f);
+    d.omg[b] = make_float4(0.5f * (W[7] - W[5]), 0.5f * (W[2] - W[6]), 0.5f * (W[3] - W[1]), 0.f);
+    float4 Q;
+    if (d.p.project) {
+        Q = mat_to_quat(A1);
+        float4 Qo = d.quat[b];
+        if (Q.x * Qo.x + Q.y * Qo.y + Q.z * Qo.z + Q.w * Qo.w < 0.f) Q = make_float4(-Q.x, -Q.y, -Q.z, -Q.w);
+    } else {
+        Q = d.qstar[b];
+    }
+    d.quat[b] = Q;
+    d.qn[3 * b] = f0; d.qn[3 * b + 1] = f1; d.qn[3 * b + 2] = f2;
+}
+
+// Drive anchors at t = (step + 1) h: x_i = x_i0 + arm (cos th r + sin th (u x r)),
+// th = amp sin(2 pi t / period + phase).
+__global__ void k_drive_update(Dev d) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= d.Ndrive) return;
+    const double t = (double)(*d.step_index + 1) * d.p.h_d;
+    float4 a = d.drv[3 * k], r = d.drv[3 * k + 1], ur = d.drv[3 * k + 2];
+    float2 pp = d.drv_t[k];
+    const float th = r.w * sinf((float)(6.283185307179586 * t / (double)pp.x) + pp.y);
+    float cs, sn;
+    sincosf(th, &sn, &cs);
+    const int bi = d.drv_bond[k];
+    float4 cur = d.bxi[bi];
+    d.bxi[bi] = make_float4(a.x + a.w * (cs * r.x + sn * ur.x), a.y + a.w * (cs * r.y + sn * ur.y),
+                            a.z + a.w * (cs * r.z + sn * ur.z), cur.w);
+}
+
+// ---- CSR of bond ends: ends of dynamic bodies, sorted by (body, 2 * bond + side) ----
+
+__device__ __forceinline__ bool end_live(const Dev& d, int body) {
+    return body >= 0 && !(d.bflags[body] & BF_PINNED);
+}
+
+__global__ void k_csr_count(Dev d) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= d.ctr[C_NBONDS]) return;
+    int4 m = d.bmeta[b];
+    if (end_live(d, m.x)) atomicAdd(&d.end_cnt[m.x], 1);
+    if (end_live(d, m.y)) atomicAdd(&d.end_cnt[m.y], 1);
+}
+
+__global__ void k_csr_fill(Dev d) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= d.ctr[C_NBONDS]) return;
+    int4 m = d.bmeta[b];
+    if (end_live(d, m.x)) d.end_id[d.end_off[m.x] + atomicAdd(&d.end_cur[m.x], 1)] = 2 * b;
+    else d.end_pos[2 * b] = -1;
+    if (end_live(d, m.y)) d.end_id[d.end_off[m.y] + atomicAdd(&d.end_cur[m.y], 1)] = 2 * b + 1;
+    else d.end_pos[2 * b + 1] = -1;
+}
+
+// sort each body's slice of end ids, then record every end's slot and material point
+__global__ void k_csr_sort(Dev d) {
+    int body = blockIdx.x * blockDim.x + threadIdx.x;
+    if (body >= d.N) return;
+    const int s = d.end_off[body], e = d.end_off[body + 1];
+    for (int a = s + 1; a < e; ++a) {
+        int v = d.end_id[a];
+        int k = a - 1;
+        while (k >= s && d.end_id[k] > v) { d.end_id[k + 1] = d.end_id[k]; --k; }
+        d.end_id[k + 1] = v;
+    }
+    for (int p = s; p < e; ++p) {
+        int id = d.end_id[p];
+        int bond = id >> 1;
+        d.end_pos[id] = p;
+        float4 x = (id & 1) ? d.bxj[bond] : d.bxi[bond];
+        d.end_x[p] = make_float4(x.x, x.y, x.z, 0.f);
+    }
+}
+
+// per-group residual sqrt(sum over the group's bodies of |q^{k+1} - q^k|^2): one warp per
+// group, fixed lane order and shuffle tree (deterministic)
+__global__ void k_group_resid(Dev d) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= d.G) return;
+    const int s = d.group_off[warp], e = d.group_off[warp + 1];
+    double acc = 0.0;
+    for (int b = s + lane; b < e; b += 32) acc += d.resid_body[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) d.resid_group[warp] = sqrt(acc);
+}
+
+void launch_predict(const Dev& d, cudaStream_t st, long long* launches) {
+    k_predict<<<nblk(d.N), ST_T, 0, st>>>(d);
+    *launches += 1;
+}
+
+void launch_drive_update(const Dev& d, cudaStream_t st, long long* launches) {
+    if (d.Ndrive == 0) return;
+    k_drive_update<<<nblk(d.Ndrive), ST_T, 0, st>>>(d);
+    *launches += 1;
+}
+
+void launch_csr(const Dev& d, cudaStream_t st, long long* launches) {
+    cudaMemsetAsync(d.end_cnt, 0, sizeof(int) * d.N, st);
+    cudaMemsetAsync(d.end_cur, 0, sizeof(int) * d.N, st);
+    k_csr_count<<<nblk(d.cap_bonds), ST_T, 0, st>>>(d);
+    scan_exclusive(d.end_cnt, d.end_off, nullptr, d.N, d.scan_scratch, st, launches);
+    k_csr_fill<<<nblk(d.cap_bonds), ST_T, 0, st>>>(d);
+    k_csr_sort<<<nblk(d.N), ST_T, 0, st>>>(d);
+    *launches += 3;
+}
+
+void launch_finalize(const Dev& d, const float4* q_fin, cudaStream_t st, long long* launches) {
+    k_finalize<<<nblk(d.N), ST_T, 0, st>>>(d, q_fin);
+    k_group_resid<<<(d.G * 32 + ST_T - 1) / ST_T > 0 ? (d.G * 32 + ST_T - 1) / ST_T : 1, ST_T, 0, st>>>(d);
+    *launches += 2;
+}
+
+}  // namespace pabd

@@ -1,0 +1,742 @@
+// Host side of the C-ABI: scene construction, upload to the device, the step sequence of
+// Alg. 1 (captured once as a CUDA graph and replayed per step), state exchange and errors.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/pabd.h"
+#include "pabd_internal.h"
+
+using namespace pabd;
+
+namespace {
+
+thread_local char g_cuda_err[256] = "";
+
+bool cuda_ok(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return true;
+    snprintf(g_cuda_err, sizeof g_cuda_err, "%s: %s", what, cudaGetErrorString(e));
+    return false;
+}
+
+#define CK(call)                                              \
+    do {                                                      \
+        if (!cuda_ok((call), #call)) return PABD_ERR_CUDA;    \
+    } while (0)
+
+struct HostBond {
+    int type;  // BondKind
+    int i, j;
+    double xi[3], xj[3];
+    double w, p1;  // w = h^2 kappa; p1 = rest length
+    // drive
+    double ui[3], ri[3], arm, amp, period, phase;
+};
+
+void quat_to_mat_d(const double* q, double* R) {
+    double x = q[0], y = q[1], z = q[2], w = q[3];
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - z * w);     R[2] = 2 * (x * z + y * w);
+    R[3] = 2 * (x * y + z * w);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - x * w);
+    R[6] = 2 * (x * z - y * w);     R[7] = 2 * (y * z + x * w);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+void normalize_quat(const double* q, double* o) {
+    double n = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    for (int k = 0; k < 4; ++k) o[k] = q[k] / n;
+}
+
+}  // namespace
+
+struct pabd_scene {
+    pabd_scene_desc desc;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    std::vector<pabd_body_desc> bodies;
+    std::vector<HostBond> bonds;
+    std::vector<int> drive_ids;
+    bool ready = false;
+    Dev d{};
+    std::vector<void*> allocs;
+    size_t bytes = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    size_t graph_nodes = 0;
+    long long launches = 0;
+    long long launches_per_step = 0;
+    int* h_status = nullptr;  // pinned
+    cudaEvent_t ev_status = nullptr;
+    bool status_pending = false;
+    int fp64_bodies = 0;
+    int latched = 0;
+    // stage timing: events recorded between the stages of a step, captured in a second graph
+    bool profiling = false;
+    std::vector<cudaEvent_t> prof_ev;
+    cudaGraph_t prof_graph = nullptr;
+    cudaGraphExec_t prof_exec = nullptr;
+    double prof_acc[PABD_PROFILE_SLOTS] = {0};
+
+    void* dalloc(size_t n) {
+        if (n == 0) n = 16;
+        n = (n + 255) & ~size_t(255);
+        void* p = nullptr;
+        if (desc.alloc) p = desc.alloc(n, desc.alloc_ctx);
+        else if (cudaMalloc(&p, n) != cudaSuccess) p = nullptr;
+        if (p) { allocs.push_back(p); bytes += n; }
+        return p;
+    }
+};
+
+namespace {
+
+pabd_status status_from_bits(int bits) {
+    if (bits & ST_DIVERGED) return PABD_ERR_DIVERGED;
+    if (bits & ST_TIMEOUT) return PABD_ERR_TIMEOUT;
+    if (bits & ST_CAPACITY) return PABD_ERR_CAPACITY;
+    return PABD_OK;
+}
+
+template <class T>
+bool alloc_arr(pabd_scene* s, T*& p, size_t n) {
+    p = static_cast<T*>(s->dalloc(sizeof(T) * (n ? n : 1)));
+    return p != nullptr;
+}
+
+// enqueue one time step of Alg. 1 on the scene's stream; with `ev` (5 + 2 n_iter events)
+// an event is recorded after every stage: [0] start, [1] drives + collision, [2] CSR,
+// [3] predictor, [4 + 2k] bond kernel of sweep k, [5 + 2k] solve of sweep k, [last] finalize
+void enqueue_step(pabd_scene* s, long long* launches, const cudaEvent_t* ev = nullptr) {
+    const Dev& d = s->d;
+    int e = 0;
+    auto mark = [&]() {
+        if (ev) cudaEventRecordWithFlags(ev[e++], s->st, cudaEventRecordExternal);
+    };
+    mark();
+    launch_drive_update(d, s->st, launches);
+    launch_collision(d, s->st, launches);
+    mark();
+    launch_csr(d, s->st, launches);
+    mark();
+    launch_predict(d, s->st, launches);
+    mark();
+    float4* cur = d.qa;
+    float4* nxt = d.qb;
+    for (int it = 0; it < d.p.n_iter; ++it) {
+        launch_bond(d, cur, s->st, launches);
+        mark();
+        launch_solve(d, cur, nxt, it == d.p.n_iter - 1, s->st, launches);
+        mark();
+        float4* t = cur; cur = nxt; nxt = t;
+    }
+    launch_finalize(d, cur, s->st, launches);
+    mark();
+}
+
+pabd_status finalize_scene(pabd_scene* s) {
+    if (s->ready) return PABD_OK;
+    const pabd_scene_desc& ds = s->desc;
+    const int N = (int)s->bodies.size();
+    const int Nc = (int)s->bonds.size();
+    Dev& d = s->d;
+    d = Dev{};
+    d.N = N;
+    d.Nc = Nc;
+    d.Ndrive = (int)s->drive_ids.size();
+    d.G = N ? s->bodies.back().group + 1 : 0;
+    // parameters
+    Params& p = d.p;
+    p.h = (float)ds.h; p.h2 = (float)(ds.h * ds.h); p.inv_h = (float)(1.0 / ds.h); p.h_d = ds.h;
+    for (int k = 0; k < 3; ++k) p.g[k] = (float)ds.gravity[k];
+    double gl = std::sqrt(ds.ground_n[0] * ds.ground_n[0] + ds.ground_n[1] * ds.ground_n[1] + ds.ground_n[2] * ds.ground_n[2]);
+    for (int k = 0; k < 3; ++k) p.gn[k] = (float)(gl > 0 ? ds.ground_n[k] / gl : 0.0);
+    p.gd = (float)ds.ground_d;
+    p.mu = (float)ds.mu; p.c_kappa = (float)ds.c_kappa; p.d_hat_rel = (float)ds.d_hat_rel; p.margin = (float)ds.margin;
+    p.n_iter = ds.n_iter; p.has_ground = ds.has_ground; p.project = ds.project; p.body_contacts = ds.body_contacts;
+    p.precision_policy = ds.precision_policy;
+    // capacities
+    d.cap_pairs = (int)(ds.max_pairs ? ds.max_pairs : (size_t)16 * (N > 64 ? N : 64));
+    d.cap_contacts = (int)(ds.max_contacts ? ds.max_contacts : (size_t)24 * (N > 64 ? N : 64));
+    d.cap_bonds = Nc + d.cap_contacts;
+    d.cap_ends = 2 * d.cap_bonds;
+    int bits = 6;
+    while ((1 << bits) < 2 * N) ++bits;
+    d.table_bits = bits;
+    const int T = 1 << bits;
+    if (T > 16000000 || d.cap_pairs > 16000000 || d.cap_bonds > 8000000) return PABD_ERR_ARG;
+
+    // host staging
+    std::vector<float4> qn(3 * N), vel(N), omg(N), quat(N), mass(N), he(N);
+    std::vector<int> flags(N), group(N), group_off(d.G + 1, 0), large;
+    std::vector<double> wsum(N, 0.0);
+    const float dr = (float)ds.d_hat_rel;
+    for (int b = 0; b < N; ++b) {
+        const pabd_body_desc& bd = s->bodies[b];
+        double Q[4], R[9];
+        normalize_quat(bd.quat, Q);
+        quat_to_mat_d(Q, R);
+        qn[3 * b] = make_float4((float)bd.c[0], (float)bd.c[1], (float)bd.c[2], (float)R[0]);
+        qn[3 * b + 1] = make_float4((float)R[1], (float)R[2], (float)R[3], (float)R[4]);
+        qn[3 * b + 2] = make_float4((float)R[5], (float)R[6], (float)R[7], (float)R[8]);
+        bool pin = bd.pinned != 0;
+        vel[b] = pin ? make_float4(0, 0, 0, 0) : make_float4((float)bd.v[0], (float)bd.v[1], (float)bd.v[2], 0);
+        omg[b] = pin ? make_float4(0, 0, 0, 0) : make_float4((float)bd.omega[0], (float)bd.omega[1], (float)bd.omega[2], 0);
+        quat[b] = make_float4((float)Q[0], (float)Q[1], (float)Q[2], (float)Q[3]);
+        // Thm 4.1 for a uniform box about its centre of mass: Pi_0 = m diag(he^2) / 3
+        double m = bd.mass;
+        mass[b] = make_float4((float)m, (float)(m * bd.he[0] * bd.he[0] / 3.0), (float)(m * bd.he[1] * bd.he[1] / 3.0),
+                              (float)(m * bd.he[2] * bd.he[2] / 3.0));
+        float hx = (float)bd.he[0], hy = (float)bd.he[1], hz = (float)bd.he[2];
+        float mn = std::fmin(std::fmin(hx, hy), hz);
+        he[b] = make_float4(hx, hy, hz, dr * (2.0f * mn));
+        int f = pin ? BF_PINNED : 0;
+        double hmax = std::fmax(std::fmax(bd.he[0], bd.he[1]), bd.he[2]);
+        if (hmax > ds.large_he) { f |= BF_LARGE; large.push_back(b); }
+        flags[b] = f;
+        group[b] = bd.group;
+        group_off[bd.group + 1] = b + 1;
+    }
+    for (int g = 1; g <= d.G; ++g) if (group_off[g] < group_off[g - 1]) group_off[g] = group_off[g - 1];
+    d.Nlarge = (int)large.size();
+    // static FP64 flag: sum of bond weights against the smallest mass-matrix diagonal
+    for (const HostBond& hb : s->bonds) {
+        if (hb.i >= 0) wsum[hb.i] += hb.w;
+        if (hb.j >= 0) wsum[hb.j] += hb.w;
+    }
+    s->fp64_bodies = 0;
+    for (int b = 0; b < N; ++b) {
+        const pabd_body_desc& bd = s->bodies[b];
+        double m = bd.mass;
+        double pmin = m * std::fmin(std::fmin(bd.he[0] * bd.he[0], bd.he[1] * bd.he[1]), bd.he[2] * bd.he[2]) / 3.0;
+        if (!(flags[b] & BF_PINNED) && wsum[b] > 1e3 * std::fmin(m, pmin)) { flags[b] |= BF_FP64; s->fp64_bodies++; }
+    }
+    // static bonds
+    std::vector<int4> bmeta(Nc);
+    std::vector<float4> bxi(Nc), bxj(Nc), bn(Nc);
+    std::vector<float4> drv(3 * d.Ndrive);
+    std::vector<float2> drv_t(d.Ndrive);
+    std::vector<int> drv_bond(d.Ndrive);
+    std::vector<std::vector<int>> adj(N);
+    for (int k = 0; k < Nc; ++k) {
+        const HostBond& hb = s->bonds[k];
+        bmeta[k] = make_int4(hb.i, hb.j, hb.type, 0);
+        bxi[k] = make_float4((float)hb.xi[0], (float)hb.xi[1], (float)hb.xi[2], (float)hb.w);
+        bxj[k] = make_float4((float)hb.xj[0], (float)hb.xj[1], (float)hb.xj[2], (float)hb.p1);
+        bn[k] = make_float4(0, 0, 0, 0);
+        if (hb.i >= 0 && hb.j >= 0) { adj[hb.i].push_back(hb.j); adj[hb.j].push_back(hb.i); }
+    }
+    for (int k = 0; k < d.Ndrive; ++k) {
+        const HostBond& hb = s->bonds[s->drive_ids[k]];
+        double ur[3] = {hb.ui[1] * hb.ri[2] - hb.ui[2] * hb.ri[1], hb.ui[2] * hb.ri[0] - hb.ui[0] * hb.ri[2],
+                        hb.ui[0] * hb.ri[1] - hb.ui[1] * hb.ri[0]};
+        drv[3 * k] = make_float4((float)hb.xi[0], (float)hb.xi[1], (float)hb.xi[2], (float)hb.arm);
+        drv[3 * k + 1] = make_float4((float)hb.ri[0], (float)hb.ri[1], (float)hb.ri[2], (float)hb.amp);
+        drv[3 * k + 2] = make_float4((float)ur[0], (float)ur[1], (float)ur[2], 0.f);
+        drv_t[k] = make_float2((float)hb.period, (float)hb.phase);
+        drv_bond[k] = s->drive_ids[k];
+        bmeta[s->drive_ids[k]].w = k;
+    }
+    std::vector<int> adj_off(N + 1, 0), adj_nbr;
+    for (int b = 0; b < N; ++b) {
+        std::vector<int>& v = adj[b];
+        std::sort(v.begin(), v.end());
+        v.erase(std::unique(v.begin(), v.end()), v.end());
+        adj_off[b + 1] = adj_off[b] + (int)v.size();
+        adj_nbr.insert(adj_nbr.end(), v.begin(), v.end());
+    }
+
+    // device allocations
+    bool ok = true;
+    ok &= alloc_arr(s, d.qn, 3 * N) && alloc_arr(s, d.qa, 3 * N) && alloc_arr(s, d.qb, 3 * N) && alloc_arr(s, d.sq, 3 * N);
+    ok &= alloc_arr(s, d.vel, N) && alloc_arr(s, d.omg, N) && alloc_arr(s, d.quat, N) && alloc_arr(s, d.qstar, N);
+    ok &= alloc_arr(s, d.mass, N) && alloc_arr(s, d.he, N);
+    ok &= alloc_arr(s, d.bflags, N) && alloc_arr(s, d.group, N) && alloc_arr(s, d.group_off, d.G + 1);
+    ok &= alloc_arr(s, d.large_ids, large.size());
+    ok &= alloc_arr(s, d.resid_body, N) && alloc_arr(s, d.resid_group, d.G);
+    ok &= alloc_arr(s, d.bmeta, d.cap_bonds) && alloc_arr(s, d.bxi, d.cap_bonds) && alloc_arr(s, d.bxj, d.cap_bonds) &&
+          alloc_arr(s, d.bn, d.cap_bonds);
+    ok &= alloc_arr(s, d.drv, 3 * d.Ndrive) && alloc_arr(s, d.drv_t, d.Ndrive) && alloc_arr(s, d.drv_bond, d.Ndrive);
+    ok &= alloc_arr(s, d.end_cnt, N) && alloc_arr(s, d.end_cur, N) && alloc_arr(s, d.end_off, N + 1);
+    ok &= alloc_arr(s, d.end_id, d.cap_ends) && alloc_arr(s, d.end_pos, d.cap_ends);
+    ok &= alloc_arr(s, d.ends, d.cap_ends) && alloc_arr(s, d.end_x, d.cap_ends);
+    ok &= alloc_arr(s, d.lo, N) && alloc_arr(s, d.hi, N) && alloc_arr(s, d.cell, N);
+    ok &= alloc_arr(s, d.bucket_cnt, T) && alloc_arr(s, d.bucket_cur, T) && alloc_arr(s, d.bucket_off, T + 1) &&
+          alloc_arr(s, d.bucket_items, N);
+    ok &= alloc_arr(s, d.pair_cnt, N) && alloc_arr(s, d.pair_off, N + 1) && alloc_arr(s, d.pairs, d.cap_pairs);
+    ok &= alloc_arr(s, d.npc, d.cap_pairs) && alloc_arr(s, d.npc_off, d.cap_pairs + 1);
+    ok &= alloc_arr(s, d.gnd_cnt, N) && alloc_arr(s, d.gnd_off, N + 1);
+    ok &= alloc_arr(s, d.ctr, C_COUNT) && alloc_arr(s, d.step_index, 1);
+    int ns = scan_scratch_ints(T);
+    ns = std::max(ns, scan_scratch_ints(N + 1));
+    ns = std::max(ns, scan_scratch_ints(d.cap_pairs));
+    ok &= alloc_arr(s, d.scan_scratch, ns);
+    if (!adj_nbr.empty()) {
+        ok &= alloc_arr(s, d.adj_off, N + 1) && alloc_arr(s, d.adj_nbr, adj_nbr.size());
+    }
+    if (!ok) return PABD_ERR_OOM;
+
+    cudaStream_t st = s->st;
+    auto up = [&](void* dst, const void* src, size_t n) { return n ? cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, st) : cudaSuccess; };
+    CK(up(d.qn, qn.data(), sizeof(float4) * 3 * N));
+    CK(up(d.vel, vel.data(), sizeof(float4) * N));
+    CK(up(d.omg, omg.data(), sizeof(float4) * N));
+    CK(up(d.quat, quat.data(), sizeof(float4) * N));
+    CK(up(d.mass, mass.data(), sizeof(float4) * N));
+    CK(up(d.he, he.data(), sizeof(float4) * N));
+    CK(up(d.bflags, flags.data(), sizeof(int) * N));
+    CK(up(d.group, group.data(), sizeof(int) * N));
+    CK(up(d.group_off, group_off.data(), sizeof(int) * (d.G + 1)));
+    CK(up(d.large_ids, large.data(), sizeof(int) * large.size()));
+    CK(up(d.bmeta, bmeta.data(), sizeof(int4) * Nc));
+    CK(up(d.bxi, bxi.data(), sizeof(float4) * Nc));
+    CK(up(d.bxj, bxj.data(), sizeof(float4) * Nc));
+    CK(up(d.bn, bn.data(), sizeof(float4) * Nc));
+    CK(up(d.drv, drv.data(), sizeof(float4) * 3 * d.Ndrive));
+    CK(up(d.drv_t, drv_t.data(), sizeof(float2) * d.Ndrive));
+    CK(up(d.drv_bond, drv_bond.data(), sizeof(int) * d.Ndrive));
+    if (d.adj_off) {
+        CK(up(d.adj_off, adj_off.data(), sizeof(int) * (N + 1)));
+        CK(up(d.adj_nbr, adj_nbr.data(), sizeof(int) * adj_nbr.size()));
+    }
+    CK(cudaMemsetAsync(d.ctr, 0, sizeof(int) * C_COUNT, st));
+    CK(cudaMemsetAsync(d.step_index, 0, sizeof(long long), st));
+    CK(cudaMemsetAsync(d.resid_body, 0, sizeof(double) * (N ? N : 1), st));
+    CK(cudaMemsetAsync(d.resid_group, 0, sizeof(double) * (d.G ? d.G : 1), st));
+    CK(cudaMemsetAsync(d.end_pos, 0xff, sizeof(int) * d.cap_ends, st));
+    // bonds beyond Nc start counted as zero until the first detection
+    int nb0 = Nc;
+    CK(cudaMemcpyAsync(d.ctr + C_NBONDS, &nb0, sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+
+    // capture one step as a graph
+    long long lc = 0;
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    enqueue_step(s, &lc);
+    cudaError_t ce = cudaStreamEndCapture(st, &s->graph);
+    CK(ce);
+    CK(cudaGraphInstantiate(&s->exec, s->graph, 0));
+    CK(cudaGraphGetNodes(s->graph, nullptr, &s->graph_nodes));
+    s->launches_per_step = lc;
+    CK(cudaMallocHost(&s->h_status, sizeof(int)));
+    *s->h_status = 0;
+    CK(cudaEventCreateWithFlags(&s->ev_status, cudaEventDisableTiming));
+    s->ready = true;
+    return PABD_OK;
+}
+
+pabd_status poll_status(pabd_scene* s, bool wait) {
+    if (!s->status_pending) return status_from_bits(s->latched);
+    cudaError_t q = wait ? cudaEventSynchronize(s->ev_status) : cudaEventQuery(s->ev_status);
+    if (q == cudaErrorNotReady) return PABD_OK;
+    CK(q);
+    s->status_pending = false;
+    s->latched |= *s->h_status;
+    return status_from_bits(s->latched);
+}
+
+pabd_status enqueue_status(pabd_scene* s) {
+    CK(cudaMemcpyAsync(s->h_status, s->d.ctr + C_STATUS, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaEventRecord(s->ev_status, s->st));
+    s->status_pending = true;
+    return PABD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pabd_status_str(pabd_status st) {
+    switch (st) {
+        case PABD_OK: return "ok";
+        case PABD_ERR_ARG: return "invalid argument";
+        case PABD_ERR_OOM: return "device allocation failed";
+        case PABD_ERR_CAPACITY: return "pair or contact capacity exceeded";
+        case PABD_ERR_DIVERGED: return "state became non-finite";
+        case PABD_ERR_TIMEOUT: return "device-side wait timed out";
+        case PABD_ERR_CUDA: return "CUDA runtime error";
+        case PABD_ERR_STATE: return "call not legal in this state";
+    }
+    return "unknown status";
+}
+
+const char* pabd_last_cuda_error(void) { return g_cuda_err; }
+
+pabd_status pabd_create_scene(const pabd_scene_desc* desc, pabd_scene** out) {
+    if (!desc || !out) return PABD_ERR_ARG;
+    if (!(desc->h > 0) || desc->n_iter < 1 || desc->n_iter > 100000) return PABD_ERR_ARG;
+    if ((desc->alloc == nullptr) != (desc->free == nullptr)) return PABD_ERR_ARG;
+    pabd_scene* s = new (std::nothrow) pabd_scene();
+    if (!s) return PABD_ERR_OOM;
+    s->desc = *desc;
+    if (desc->stream) {
+        s->st = (cudaStream_t)desc->stream;
+    } else {
+        if (!cuda_ok(cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking), "cudaStreamCreate")) {
+            delete s;
+            return PABD_ERR_CUDA;
+        }
+        s->own_stream = true;
+    }
+    *out = s;
+    return PABD_OK;
+}
+
+pabd_status pabd_add_body(pabd_scene* s, const pabd_body_desc* b, uint32_t* out_id) {
+    if (!s || !b) return PABD_ERR_ARG;
+    if (s->ready) return PABD_ERR_STATE;
+    for (int k = 0; k < 3; ++k) if (!(b->he[k] > 0) || !std::isfinite(b->he[k])) return PABD_ERR_ARG;
+    if (!(b->mass > 0) || !std::isfinite(b->mass)) return PABD_ERR_ARG;
+    double qn = b->quat[0] * b->quat[0] + b->quat[1] * b->quat[1] + b->quat[2] * b->quat[2] + b->quat[3] * b->quat[3];
+    if (!(qn > 0) || !std::isfinite(qn)) return PABD_ERR_ARG;
+    int last_g = s->bodies.empty() ? 0 : s->bodies.back().group;
+    if (b->group < last_g || b->group < 0 || (s->bodies.empty() && b->group != 0) || b->group > last_g + 1)
+        return PABD_ERR_ARG;
+    if (s->bodies.size() >= 0x7fffffffu / 4) return PABD_ERR_ARG;
+    if (out_id) *out_id = (uint32_t)s->bodies.size();
+    s->bodies.push_back(*b);
+    return PABD_OK;
+}
+
+pabd_status pabd_add_bond(pabd_scene* s, const pabd_bond_desc* b, uint32_t* out_ids, int* n_out) {
+    if (!s || !b) return PABD_ERR_ARG;
+    if (s->ready) return PABD_ERR_STATE;
+    const long nbod = (long)s->bodies.size();
+    if (b->body_i >= (uint32_t)nbod) return PABD_ERR_ARG;
+    if (b->body_j != PABD_WORLD && b->body_j >= (uint32_t)nbod) return PABD_ERR_ARG;
+    if (b->body_j == b->body_i) return PABD_ERR_ARG;
+    if (!(b->kappa >= 0) || !std::isfinite(b->kappa)) return PABD_ERR_ARG;
+    if (b->type == PABD_ELASTIC_NL && !(b->rest_len > 0)) return PABD_ERR_ARG;
+    if (b->type == PABD_SPRING && !(b->rest_len >= 0)) return PABD_ERR_ARG;
+    const int i = (int)b->body_i, j = b->body_j == PABD_WORLD ? -1 : (int)b->body_j;
+    const double h2 = s->desc.h * s->desc.h;
+    HostBond hb{};
+    hb.i = i; hb.j = j;
+    hb.w = h2 * b->kappa;
+    hb.p1 = b->rest_len;
+    for (int k = 0; k < 3; ++k) { hb.xi[k] = b->x_i[k]; hb.xj[k] = b->x_j[k]; }
+    const uint32_t first = (uint32_t)s->bonds.size();
+    if (b->type == PABD_SPHERICAL || b->type == PABD_SPRING || b->type == PABD_ELASTIC_NL) {
+        hb.type = b->type;
+        s->bonds.push_back(hb);
+        if (out_ids) out_ids[0] = first;
+        if (n_out) *n_out = 1;
+        return PABD_OK;
+    }
+    if (b->type != PABD_REVOLUTE && b->type != PABD_DRIVE) return PABD_ERR_ARG;
+    double an = std::sqrt(b->axis[0] * b->axis[0] + b->axis[1] * b->axis[1] + b->axis[2] * b->axis[2]);
+    if (!(an > 0)) return PABD_ERR_ARG;
+    double ui[3] = {b->axis[0] / an, b->axis[1] / an, b->axis[2] / an};
+    // carry directions from body i's frame into body j's frame (world for PABD_WORLD)
+    double Qi[4], Ri[9], Rj[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    normalize_quat(s->bodies[i].quat, Qi);
+    quat_to_mat_d(Qi, Ri);
+    if (j >= 0) { double Qj[4]; normalize_quat(s->bodies[j].quat, Qj); quat_to_mat_d(Qj, Rj); }
+    auto carry = [&](const double* di, double* dj) {
+        double wv[3];
+        for (int r = 0; r < 3; ++r) wv[r] = Ri[3 * r] * di[0] + Ri[3 * r + 1] * di[1] + Ri[3 * r + 2] * di[2];
+        for (int c = 0; c < 3; ++c) dj[c] = Rj[c] * wv[0] + Rj[3 + c] * wv[1] + Rj[6 + c] * wv[2];
+    };
+    double uj[3];
+    carry(ui, uj);
+    if (b->type == PABD_REVOLUTE) {
+        for (int sg = 1; sg >= -1; sg -= 2) {
+            HostBond h = hb;
+            h.type = K_SPHERICAL;
+            for (int k = 0; k < 3; ++k) {
+                h.xi[k] = b->x_i[k] + sg * b->arm * ui[k];
+                h.xj[k] = b->x_j[k] + sg * b->arm * uj[k];
+            }
+            s->bonds.push_back(h);
+        }
+        if (out_ids) { out_ids[0] = first; out_ids[1] = first + 1; }
+        if (n_out) *n_out = 2;
+        return PABD_OK;
+    }
+    // drive: lever r_i orthogonal to u_i (u_i x e_m, e_m the axis least aligned with u_i)
+    if (!(b->drive_period > 0)) return PABD_ERR_ARG;
+    int m = 0;
+    for (int k = 1; k < 3; ++k) if (std::fabs(ui[k]) < std::fabs(ui[m])) m = k;
+    double e[3] = {0, 0, 0};
+    e[m] = 1.0;
+    double ri[3] = {ui[1] * e[2] - ui[2] * e[1], ui[2] * e[0] - ui[0] * e[2], ui[0] * e[1] - ui[1] * e[0]};
+    double rn = std::sqrt(ri[0] * ri[0] + ri[1] * ri[1] + ri[2] * ri[2]);
+    for (int k = 0; k < 3; ++k) ri[k] /= rn;
+    double rj[3];
+    carry(ri, rj);
+    hb.type = K_DRIVE;
+    for (int k = 0; k < 3; ++k) { hb.ui[k] = ui[k]; hb.ri[k] = ri[k]; hb.xj[k] = b->x_j[k] + b->arm * rj[k]; }
+    hb.arm = b->arm; hb.amp = b->drive_amp; hb.period = b->drive_period; hb.phase = b->drive_phase;
+    s->drive_ids.push_back((int)first);
+    s->bonds.push_back(hb);
+    if (out_ids) out_ids[0] = first;
+    if (n_out) *n_out = 1;
+    return PABD_OK;
+}
+
+pabd_status pabd_set_profiling(pabd_scene* s, int on) {
+    if (!s) return PABD_ERR_ARG;
+    pabd_status r = finalize_scene(s);
+    if (r != PABD_OK) return r;
+    if (on && !s->prof_exec) {
+        const int ne = 5 + 2 * s->d.p.n_iter;
+        s->prof_ev.resize(ne);
+        for (int k = 0; k < ne; ++k) CK(cudaEventCreate(&s->prof_ev[k]));
+        long long lc = 0;
+        CK(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
+        enqueue_step(s, &lc, s->prof_ev.data());
+        CK(cudaStreamEndCapture(s->st, &s->prof_graph));
+        CK(cudaGraphInstantiate(&s->prof_exec, s->prof_graph, 0));
+    }
+    s->profiling = on != 0;
+    return PABD_OK;
+}
+
+pabd_status pabd_read_profile(pabd_scene* s, double* out, size_t n, int reset) {
+    if (!s || !out || n > PABD_PROFILE_SLOTS) return PABD_ERR_ARG;
+    for (size_t k = 0; k < n; ++k) out[k] = s->prof_acc[k];
+    if (reset) for (double& v : s->prof_acc) v = 0.0;
+    return PABD_OK;
+}
+
+namespace {
+// one profiled step: launch the graph with event nodes, wait, accumulate stage times
+pabd_status profiled_step(pabd_scene* s) {
+    CK(cudaGraphLaunch(s->prof_exec, s->st));
+    s->launches += s->launches_per_step;
+    const std::vector<cudaEvent_t>& e = s->prof_ev;
+    CK(cudaEventSynchronize(e.back()));
+    auto ms = [&](int a, int b) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e[a], e[b]);
+        return (double)t;
+    };
+    const int n_it = s->d.p.n_iter;
+    double* acc = s->prof_acc;
+    acc[0] += 1.0;
+    acc[1] += ms(0, 1);
+    acc[2] += ms(1, 2);
+    acc[3] += ms(2, 3);
+    for (int k = 0; k < n_it; ++k) {
+        acc[4] += ms(3 + 2 * k, 4 + 2 * k);
+        acc[5] += ms(4 + 2 * k, 5 + 2 * k);
+    }
+    acc[6] += ms(3 + 2 * n_it, 4 + 2 * n_it);
+    acc[7] += n_it;
+    acc[8] += n_it;
+    acc[9] += ms(0, 4 + 2 * n_it);
+    int nb = 0;
+    CK(cudaMemcpy(&nb, s->d.ctr + C_NBONDS, sizeof(int), cudaMemcpyDeviceToHost));
+    acc[10] += nb;
+    return PABD_OK;
+}
+}  // namespace
+
+pabd_status pabd_step(pabd_scene* s, int nsteps) {
+    if (!s || nsteps < 0) return PABD_ERR_ARG;
+    pabd_status r = finalize_scene(s);
+    if (r != PABD_OK) return r;
+    r = poll_status(s, false);
+    if (r != PABD_OK) return r;
+    for (int k = 0; k < nsteps; ++k) {
+        if (s->profiling) {
+            r = profiled_step(s);
+            if (r != PABD_OK) return r;
+            continue;
+        }
+        CK(cudaGraphLaunch(s->exec, s->st));
+        s->launches += s->launches_per_step;
+    }
+    return enqueue_status(s);
+}
+
+pabd_status pabd_step_eager(pabd_scene* s, int nsteps) {
+    if (!s || nsteps < 0) return PABD_ERR_ARG;
+    pabd_status r = finalize_scene(s);
+    if (r != PABD_OK) return r;
+    r = poll_status(s, false);
+    if (r != PABD_OK) return r;
+    for (int k = 0; k < nsteps; ++k) enqueue_step(s, &s->launches);
+    CK(cudaGetLastError());
+    return enqueue_status(s);
+}
+
+pabd_status pabd_detect(pabd_scene* s) {
+    if (!s) return PABD_ERR_ARG;
+    pabd_status r = finalize_scene(s);
+    if (r != PABD_OK) return r;
+    launch_drive_update(s->d, s->st, &s->launches);
+    launch_collision(s->d, s->st, &s->launches);
+    CK(cudaGetLastError());
+    return enqueue_status(s);
+}
+
+pabd_status pabd_sync(pabd_scene* s) {
+    if (!s) return PABD_ERR_ARG;
+    CK(cudaStreamSynchronize(s->st));
+    if (!s->ready) return PABD_OK;
+    pabd_status r = poll_status(s, true);
+    if (r != PABD_OK) return r;
+    int bits = 0;
+    CK(cudaMemcpy(&bits, s->d.ctr + C_STATUS, sizeof(int), cudaMemcpyDeviceToHost));
+    s->latched |= bits;
+    return status_from_bits(s->latched);
+}
+
+pabd_status pabd_read_state(pabd_scene* s, double* rows, size_t n) {
+    if (!s || !rows) return PABD_ERR_ARG;
+    pabd_status r = finalize_scene(s);
+    if (r != PABD_OK) return r;
+    const int N = s->d.N;
+    if (n != (size_t)N) return PABD_ERR_ARG;
+    std::vector<float4> q(3 * N), v(N), w(N), Q(N);
+    CK(cudaMemcpyAsync(q.data(), s->d.qn, sizeof(float4) * 3 * N, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(v.data(), s->d.vel, sizeof(float4) * N, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(w.data(), s->d.omg, sizeof(float4) * N, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(Q.data(), s->d.quat, sizeof(float4) * N, cudaMemcpyDeviceToHost, s->st));
+    r = pabd_sync(s);
+    for (int b = 0; b < N; ++b) {
+        double* o = rows + (size_t)PABD_STATE_COLS * b;
+        const float* qf = reinterpret_cast<const float*>(&q[3 * b]);
+        for (int k = 0; k < 12; ++k) o[k] = qf[k];
+        o[12] = Q[b].x; o[13] = Q[b].y; o[14] = Q[b].z; o[15] = Q[b].w;
+        o[16] = v[b].x; o[17] = v[b].y; o[18] = v[b].z;
+        o[19] = w[b].x; o[20] = w[b].y; o[21] = w[b].z;
+    }
+    return r;
+}
+
+pabd_status pabd_write_state(pabd_scene* s, const double* rows, size_t n) {
+    if (!s || !rows) return PABD_ERR_ARG;
+    pabd_status r = finalize_scene(s);
+    if (r != PABD_OK) return r;
+    const int N = s->d.N;
+    if (n != (size_t)N) return PABD_ERR_ARG;
+    std::vector<float4> q(3 * N), v(N), w(N), Q(N);
+    for (int b = 0; b < N; ++b) {
+        const double* o = rows + (size_t)PABD_STATE_COLS * b;
+        for (int k = 0; k < PABD_STATE_COLS; ++k) if (!std::isfinite(o[k])) return PABD_ERR_ARG;
+        float* qf = reinterpret_cast<float*>(&q[3 * b]);
+        for (int k = 0; k < 12; ++k) qf[k] = (float)o[k];
+        Q[b] = make_float4((float)o[12], (float)o[13], (float)o[14], (float)o[15]);
+        bool pin = s->bodies[b].pinned != 0;
+        v[b] = pin ? make_float4(0, 0, 0, 0) : make_float4((float)o[16], (float)o[17], (float)o[18], 0.f);
+        w[b] = pin ? make_float4(0, 0, 0, 0) : make_float4((float)o[19], (float)o[20], (float)o[21], 0.f);
+    }
+    CK(cudaMemcpyAsync(s->d.qn, q.data(), sizeof(float4) * 3 * N, cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(s->d.vel, v.data(), sizeof(float4) * N, cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(s->d.omg, w.data(), sizeof(float4) * N, cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(s->d.quat, Q.data(), sizeof(float4) * N, cudaMemcpyHostToDevice, s->st));
+    CK(cudaStreamSynchronize(s->st));  // the staging vectors go out of scope
+    return PABD_OK;
+}
+
+pabd_status pabd_set_step_index(pabd_scene* s, int64_t step_index) {
+    if (!s || step_index < 0) return PABD_ERR_ARG;
+    pabd_status r = finalize_scene(s);
+    if (r != PABD_OK) return r;
+    long long v = step_index;
+    CK(cudaMemcpyAsync(s->d.step_index, &v, sizeof v, cudaMemcpyHostToDevice, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return PABD_OK;
+}
+
+pabd_status pabd_read_pairs(pabd_scene* s, int32_t* out, size_t cap, size_t* n) {
+    if (!s || !n) return PABD_ERR_ARG;
+    pabd_status r = finalize_scene(s);
+    if (r != PABD_OK) return r;
+    int np = 0;
+    CK(cudaMemcpyAsync(&np, s->d.ctr + C_NPAIRS, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+    r = pabd_sync(s);
+    *n = (size_t)np;
+    size_t m = (size_t)np < cap ? (size_t)np : cap;
+    if (m && out) {
+        CK(cudaMemcpy(out, s->d.pairs, sizeof(int2) * m, cudaMemcpyDeviceToHost));
+    }
+    return r;
+}
+
+pabd_status pabd_read_contacts(pabd_scene* s, int32_t* meta, float* data, size_t cap, size_t* n) {
+    if (!s || !n) return PABD_ERR_ARG;
+    pabd_status r = finalize_scene(s);
+    if (r != PABD_OK) return r;
+    int c[C_COUNT];
+    CK(cudaMemcpyAsync(c, s->d.ctr, sizeof c, cudaMemcpyDeviceToHost, s->st));
+    r = pabd_sync(s);
+    const int nk = c[C_NPC] + c[C_NGC];
+    *n = (size_t)nk;
+    size_t m = (size_t)nk < cap ? (size_t)nk : cap;
+    if (!m || !meta || !data) return r;
+    std::vector<int4> bm(m);
+    std::vector<float4> xi(m), xj(m), bn(m);
+    const int o = s->d.Nc;
+    CK(cudaMemcpy(bm.data(), s->d.bmeta + o, sizeof(int4) * m, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(xi.data(), s->d.bxi + o, sizeof(float4) * m, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(xj.data(), s->d.bxj + o, sizeof(float4) * m, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(bn.data(), s->d.bn + o, sizeof(float4) * m, cudaMemcpyDeviceToHost));
+    for (size_t k = 0; k < m; ++k) {
+        meta[3 * k] = bm[k].z; meta[3 * k + 1] = bm[k].x; meta[3 * k + 2] = bm[k].y;
+        float* dd = data + 11 * k;
+        dd[0] = xi[k].x; dd[1] = xi[k].y; dd[2] = xi[k].z;
+        dd[3] = xj[k].x; dd[4] = xj[k].y; dd[5] = xj[k].z;
+        dd[6] = bn[k].x; dd[7] = bn[k].y; dd[8] = bn[k].z;
+        dd[9] = xj[k].w; dd[10] = xi[k].w;
+    }
+    return r;
+}
+
+pabd_status pabd_read_residual(pabd_scene* s, double* out, size_t n_groups) {
+    if (!s || !out) return PABD_ERR_ARG;
+    pabd_status r = finalize_scene(s);
+    if (r != PABD_OK) return r;
+    if (n_groups != (size_t)s->d.G) return PABD_ERR_ARG;
+    r = pabd_sync(s);
+    if (n_groups) CK(cudaMemcpy(out, s->d.resid_group, sizeof(double) * n_groups, cudaMemcpyDeviceToHost));
+    return r;
+}
+
+pabd_status pabd_get_info(pabd_scene* s, pabd_info* info) {
+    if (!s || !info) return PABD_ERR_ARG;
+    std::memset(info, 0, sizeof *info);
+    info->n_bodies = (int64_t)s->bodies.size();
+    info->n_groups = s->bodies.empty() ? 0 : s->bodies.back().group + 1;
+    info->n_static_bonds = (int64_t)s->bonds.size();
+    info->launches = s->launches;
+    if (!s->ready) return PABD_OK;
+    int c[C_COUNT];
+    long long step = 0;
+    CK(cudaMemcpyAsync(c, s->d.ctr, sizeof c, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(&step, s->d.step_index, sizeof step, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    info->n_bonds = c[C_NBONDS];
+    info->n_pairs = c[C_NPAIRS];
+    info->n_contacts = c[C_NPC] + c[C_NGC];
+    info->step_index = step;
+    info->max_pairs = s->d.cap_pairs;
+    info->max_contacts = s->d.cap_contacts;
+    info->graph_nodes = (int64_t)s->graph_nodes;
+    info->fp64_bodies = s->fp64_bodies;
+    info->device_bytes = (int64_t)s->bytes;
+    return PABD_OK;
+}
+
+pabd_status pabd_destroy_scene(pabd_scene* s) {
+    if (!s) return PABD_ERR_ARG;
+    cudaStreamSynchronize(s->st);
+    if (s->exec) cudaGraphExecDestroy(s->exec);
+    if (s->prof_exec) cudaGraphExecDestroy(s->prof_exec);
+    if (s->prof_graph) cudaGraphDestroy(s->prof_graph);
+    for (cudaEvent_t e : s->prof_ev) cudaEventDestroy(e);
+    if (s->graph) cudaGraphDestroy(s->graph);
+    if (s->ev_status) cudaEventDestroy(s->ev_status);
+    if (s->h_status) cudaFreeHost(s->h_status);
+    for (void* p : s->allocs) {
+        if (s->desc.free) s->desc.free(p, s->desc.alloc_ctx);
+        else cudaFree(p);
+    }
+    if (s->own_stream) cudaStreamDestroy(s->st);
+    delete s;
+    return PABD_OK;
+}
+
+}  // extern "C"

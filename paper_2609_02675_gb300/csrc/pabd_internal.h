@@ -1,0 +1,94 @@
+// Internal layout of a scene on the device and the launchers of every kernel.
+//
+// Memory layout (structure of arrays; one slot per body / bond / bond end):
+//   q (12 floats per body) as 3 float4: (c0 c1 c2 A00) (A01 A02 A10 A11) (A12 A20 A21 A22),
+//   i.e. the generalised coordinates q = (c, a1, a2, a3) of Eq. 1 in order, 48 contiguous
+//   bytes per body so a gather of one body is three 16-byte loads of one 64-byte segment.
+//   Bonds: meta int4 (i, j, type, aux), xi float4 (x_i, w0), xj float4 (x_j, p1),
+//   bn float4 (N, mu) -- static bonds first, then this step's contact bonds.
+//   Bond ends: a CSR over bodies sorted by (body, 2*bond + side); per end the bond kernel
+//   writes one float4 (w, f') at its CSR slot and the solve reads its body's slice.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pabd {
+
+enum BondKind { K_SPHERICAL = 0, K_SPRING = 1, K_ELASTIC_NL = 2, K_DRIVE = 4, K_CONTACT = 5, K_GROUND = 6 };
+
+enum StatusBits { ST_CAPACITY = 1, ST_DIVERGED = 2, ST_TIMEOUT = 4 };
+
+enum BodyFlags { BF_PINNED = 1, BF_FP64 = 2, BF_LARGE = 4 };
+
+// device counters (ints) -- one small array so that one memset resets them
+enum Counter {
+    C_NPAIRS = 0,      // broad-phase pairs (clamped to capacity)
+    C_NPC,             // body-body contacts
+    C_NGC,             // ground contacts
+    C_NBONDS,          // static + contact bonds this step
+    C_STATUS,          // latched StatusBits (never reset by a step)
+    C_CELLBITS,        // float bits of the grid cell size
+    C_FP64DYN,         // bodies that switched to FP64 by the pivot test (last sweep)
+    C_COUNT
+};
+
+struct Params {
+    float h, h2, inv_h;
+    float g[3];
+    float gn[3], gd;
+    float mu, c_kappa, d_hat_rel, margin;
+    int n_iter, has_ground, project, body_contacts, precision_policy;
+    double h_d;
+};
+
+struct Dev {
+    Params p;
+    int N, Nc, Ndrive, G, Nlarge;
+    int cap_pairs, cap_contacts, cap_bonds, cap_ends;
+    int table_bits;             // grid hash table has 1 << table_bits buckets
+    // bodies
+    float4 *qn, *qa, *qb, *sq;  // 3 float4 per body each
+    float4 *vel, *omg, *quat, *qstar;
+    float4 *mass;               // (m, Pi_xx, Pi_yy, Pi_zz)
+    float4 *he;                 // (hx, hy, hz, dhat)
+    int *bflags, *group, *group_off, *large_ids;
+    int *adj_off, *adj_nbr;     // sorted partners joined by user bonds (no contact), or null
+    double *resid_body, *resid_group;
+    // bonds
+    int4 *bmeta;
+    float4 *bxi, *bxj, *bn;
+    float4 *drv;                // 3 float4 per drive: (x_i0, arm) (r, amp) (u x r, 0); period/phase in drv_t
+    float2 *drv_t;              // (period, phase)
+    int *drv_bond;              // bond index of each drive
+    // CSR of bond ends
+    int *end_cnt, *end_cur, *end_off, *end_id, *end_pos;
+    float4 *ends, *end_x;
+    // collision
+    float4 *lo, *hi;            // inflated AABB; lo.w = inflation
+    int4 *cell;                 // cell coords (.w = bucket)
+    int *bucket_cnt, *bucket_cur, *bucket_off, *bucket_items;
+    int *pair_cnt, *pair_off;
+    int2 *pairs;
+    int *npc, *npc_off, *gnd_cnt, *gnd_off;
+    // misc
+    int *ctr;                   // Counter array
+    long long *step_index;
+    int *scan_scratch;          // block sums of the scans
+};
+
+// ---- launchers (all asynchronous on `st`) ----
+// scan: out[0..n] exclusive prefix sums of in[0..n-1], n read from *n_dev (or n_cap if
+// n_dev is null), out[n] = total; grid sized for n_cap.
+void scan_exclusive(const int* in, int* out, const int* n_dev, int n_cap, int* scratch, cudaStream_t st,
+                    long long* launches);
+int scan_scratch_ints(int n_cap);
+
+void launch_collision(const Dev& d, cudaStream_t st, long long* launches);
+void launch_csr(const Dev& d, cudaStream_t st, long long* launches);
+void launch_predict(const Dev& d, cudaStream_t st, long long* launches);
+void launch_bond(const Dev& d, const float4* q, cudaStream_t st, long long* launches);
+void launch_solve(const Dev& d, const float4* q_in, float4* q_out, int last, cudaStream_t st, long long* launches);
+void launch_finalize(const Dev& d, const float4* q_fin, cudaStream_t st, long long* launches);
+void launch_drive_update(const Dev& d, cudaStream_t st, long long* launches);
+
+}  // namespace pabd

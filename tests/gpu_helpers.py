@@ -1,0 +1,51 @@
+"""Helpers shared by the GPU parity tests: the per-step error measure and teacher forcing."""
+from __future__ import annotations
+
+import numpy as np
+
+SIGNS = np.array([[sx, sy, sz] for sz in (-1, 1) for sy in (-1, 1) for sx in (-1, 1)], dtype=np.float64)
+
+# relative per-step position tolerance of the FP32 path against the FP64 oracle
+REL_TOL = 1e-5
+
+
+def corners(st: np.ndarray, he: np.ndarray) -> np.ndarray:
+    """World positions y = A x + c of the 8 box corners of every body (N, 8, 3)."""
+    x = SIGNS[None, :, :] * he[:, None, :]
+    A = st[:, 3:12].reshape(-1, 3, 3)
+    return st[:, None, 0:3] + np.einsum("nij,nkj->nki", A, x)
+
+
+def scene_scale(st_ref: np.ndarray, he: np.ndarray) -> float:
+    """Diagonal of the scene's bounding box (at least 1)."""
+    y = corners(st_ref, he).reshape(-1, 3)
+    return max(float(np.linalg.norm(y.max(0) - y.min(0))), 1.0)
+
+
+def rel_err(st_gpu: np.ndarray, st_ref: np.ndarray, he: np.ndarray) -> float:
+    """max over bodies and corners |y_gpu - y_ref| / scene diagonal."""
+    if st_ref.shape[0] == 0:
+        return 0.0
+    d = np.linalg.norm(corners(st_gpu, he) - corners(st_ref, he), axis=-1)
+    return float(d.max()) / scene_scale(st_ref, he)
+
+
+def teacher_forced_step(gpu, ref, n: int = 1):
+    """Start the GPU from the oracle's state (rounded to FP32 on upload), step both n steps."""
+    st0 = ref.state()
+    gpu.set_state(st0)
+    gpu.set_step_index(ref.step_index)
+    ref.step(n)
+    gpu.step(n)
+    return gpu.state(), ref.state()
+
+
+def same_contacts(gpu_c, ref_c):
+    """Bit-exact contact lists: same (type, i, j) rows in the same order and the same
+    single-precision geometry; dhat and w agree to single-precision rounding."""
+    gm, gd = gpu_c
+    rm, rd = ref_c
+    assert gm.shape == rm.shape, f"contact count {gm.shape[0]} vs {rm.shape[0]}"
+    assert np.array_equal(gm, rm)
+    assert np.array_equal(gd[:, :9], rd[:, :9].astype(np.float32))
+    np.testing.assert_allclose(gd[:, 9:11], rd[:, 9:11], rtol=2e-7, atol=0)

@@ -1,0 +1,266 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 oracle on the same seeded
+inputs.  Integer work (pairs, contact lists) is compared bit for bit; positions per step,
+teacher-forced from the oracle's state, within 1e-5 of the scene diagonal."""
+import numpy as np
+import pytest
+
+import oracle as O
+import scenes as S
+from tests.gpu_helpers import REL_TOL, rel_err, same_contacts, teacher_forced_step
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2609_02675_gb300 as mod
+    return mod
+
+
+def _he(sc):
+    return np.ascontiguousarray(sc.bodies["he"], dtype=np.float64)
+
+
+# --------------------------------------------------------------------------------------
+# closed forms on the device
+# --------------------------------------------------------------------------------------
+
+def test_gpu_ballistic_and_spin(P):
+    h = 1.0 / 60.0
+    v0 = np.array([1.3, 4.0, -0.7])
+    sc = S.single_body(c=(0.2, 5.0, -1.0), v=v0, omega=(0, 0, 3.0), has_ground=0)
+    g = P.Scene(sc)
+    n = 30
+    g.step(n)
+    st = g.state()[0]
+    gv = np.array([0, -9.81, 0])
+    # v = (c^{n+1} - c^n)/h in FP32: each step adds the rounding of |c| (<= 2^-24 |c|) over h
+    tol_v = 4 * n * 2.0 ** -24 * 6.0 / h
+    np.testing.assert_allclose(st[16:19], v0 + n * h * gv, atol=tol_v)
+    np.testing.assert_allclose(st[0:3], np.array([0.2, 5.0, -1.0]) + n * h * v0 + h * h * gv * n * (n + 1) / 2,
+                               atol=1e-5)
+    w = 3.0
+    for _ in range(n):
+        w = w / (1 + h * h * w * w / 4)
+    np.testing.assert_allclose(st[19:22], [0, 0, w], atol=4 * n * 2.0 ** -24 * 3.0 / h)
+    g.close()
+
+
+# --------------------------------------------------------------------------------------
+# chain pendulum (8 bodies, 7 stiff spherical joints, FP64-flagged solves, ground)
+# --------------------------------------------------------------------------------------
+
+def test_chain_pendulum_teacher_forced_every_step(P):
+    sc = S.chain_pendulum()
+    ref = O.OracleScene(sc)
+    g = P.Scene(sc)
+    assert g.info()["fp64_bodies"] == 7
+    worst = 0.0
+    for k in range(sc.n_steps):
+        a, b = teacher_forced_step(g, ref)
+        worst = max(worst, rel_err(a, b, _he(sc)))
+    assert worst < REL_TOL, worst
+    g.close()
+
+
+def test_chain_pendulum_trajectory(P):
+    """Free-running: the FP32 trajectory stays within the tolerance for the first steps and
+    bounded over the whole run."""
+    sc = S.chain_pendulum()
+    ref = O.OracleScene(sc)
+    g = P.Scene(sc)
+    errs = []
+    for k in range(sc.n_steps):
+        ref.step(1)
+        g.step(1)
+        errs.append(rel_err(g.state(), ref.state(), _he(sc)))
+    assert max(errs[:10]) < REL_TOL, errs[:10]
+    assert max(errs) < 1e-2, max(errs)
+    g.close()
+
+
+def test_fp32_only_policy_is_worse_on_stiff_chain(P):
+    """The FP64 fallback matters: with the FP32-only policy the stiff chain is further off."""
+    sc = S.chain_pendulum()
+    ref = O.OracleScene(sc)
+    ref.step(20)
+    g64 = P.Scene(sc, precision_policy=1)
+    g32 = P.Scene(sc, precision_policy=0)
+    a64, b = teacher_forced_step(g64, ref)
+    ref2 = O.OracleScene(sc)
+    ref2.step(20)
+    a32, b2 = teacher_forced_step(g32, ref2)
+    e64, e32 = rel_err(a64, b, _he(sc)), rel_err(a32, b2, _he(sc))
+    assert e64 < REL_TOL
+    assert e32 >= e64
+    g64.close()
+    g32.close()
+
+
+# --------------------------------------------------------------------------------------
+# box pile: pairs and contacts bit-exact, steps within tolerance
+# --------------------------------------------------------------------------------------
+
+def _pile_small():
+    return S.box_pile(nx=6, ny=6, nz=6, spacing=2.3, n_steps=150)
+
+
+def test_pile_pairs_and_contacts_bit_exact(P):
+    sc = _pile_small()
+    ref = O.OracleScene(sc)
+    g = P.Scene(sc)
+    checked = 0
+    for k in range(sc.n_steps):
+        if k % 10 == 0:
+            g.set_state(ref.state())
+            g.detect()
+            ref.detect()
+            rp, gp = ref.pairs(), g.pairs()
+            assert np.array_equal(gp, rp), f"step {k}: pairs differ ({len(gp)} vs {len(rp)})"
+            same_contacts(g.contacts(), ref.contacts())
+            checked += len(rp)
+        ref.step(1)
+    assert checked > 100
+    g.close()
+
+
+def test_pile_teacher_forced_steps(P):
+    sc = _pile_small()
+    ref = O.OracleScene(sc)
+    g = P.Scene(sc)
+    worst = 0.0
+    n_cont = 0
+    for k in range(sc.n_steps):
+        if k % 5 == 4:
+            a, b = teacher_forced_step(g, ref)
+            worst = max(worst, rel_err(a, b, _he(sc)))
+            n_cont += len(ref.contacts()[0])
+        else:
+            ref.step(1)
+    assert n_cont > 500
+    assert worst < REL_TOL, worst
+    g.close()
+
+
+def test_pile_full_size_sampled(P):
+    """The 4096-box pile (16^3 grid, spacing 3.5): after the first layers land, pairs and
+    contacts are bit-exact and one teacher-forced step is within tolerance."""
+    sc = S.box_pile()
+    ref = O.OracleScene(sc)
+    ref.step(45)
+    g = P.Scene(sc)
+    g.set_state(ref.state())
+    g.detect()
+    ref.detect()
+    assert np.array_equal(g.pairs(), ref.pairs())
+    same_contacts(g.contacts(), ref.contacts())
+    assert len(ref.contacts()[0]) > 500
+    a, b = teacher_forced_step(g, ref)
+    assert rel_err(a, b, _he(sc)) < REL_TOL
+    g.close()
+
+
+def test_graph_and_eager_paths_identical_and_deterministic(P):
+    sc = _pile_small()
+    outs = []
+    for mode in ("graph", "graph", "eager"):
+        g = P.Scene(sc)
+        for _ in range(60):
+            g.step(1) if mode == "graph" else g.step_eager(1)
+        outs.append(g.state())
+        g.close()
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[2])
+
+
+# --------------------------------------------------------------------------------------
+# batched independent scenes (groups), articulated + flexible scenes
+# --------------------------------------------------------------------------------------
+
+def test_batched_trees_parity_and_alone_vs_in_mix(P):
+    sc = S.batched_trees(n_scenes=24, n_steps=40)
+    ref = O.OracleScene(sc)
+    g = P.Scene(sc)
+    worst = 0.0
+    for k in range(sc.n_steps):
+        a, b = teacher_forced_step(g, ref)
+        worst = max(worst, rel_err(a, b, _he(sc)))
+    assert worst < REL_TOL, worst
+    # each scene alone gives bit-identical results to the same scene inside the batch
+    full = P.Scene(sc)
+    full.step(20)
+    st_full = full.state()
+    sizes = sc.meta["sizes"]
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    for gi in (0, 7, 23):
+        sl = slice(off[gi], off[gi + 1])
+        sub = S.Scene("one", dict(sc.params), sc.bodies[sl].copy(), sc.bonds.copy(), 1)
+        sub.bodies["group"] = 0
+        m = (sc.bonds["i"] >= off[gi]) & (sc.bonds["i"] < off[gi + 1])
+        sub.bonds = sc.bonds[m].copy()
+        sub.bonds["i"] -= off[gi]
+        sub.bonds["j"] = np.where(sub.bonds["j"] >= 0, sub.bonds["j"] - off[gi], -1)
+        one = P.Scene(sub)
+        one.step(20)
+        assert np.array_equal(one.state(), st_full[sl])
+        one.close()
+    full.close()
+    g.close()
+
+
+def test_quadruped_bed_rod_small_teacher_forced(P):
+    """Revolute joints, sinusoidal drives, nonlinear elastic rod, granular bed (reduced)."""
+    sc = S.quadruped_bed_rod(bed=(12, 2, 12), n_rod=16, n_steps=40)
+    ref = O.OracleScene(sc)
+    g = P.Scene(sc)
+    worst = 0.0
+    for k in range(sc.n_steps):
+        if k % 4 == 3:
+            a, b = teacher_forced_step(g, ref)
+            worst = max(worst, rel_err(a, b, _he(sc)))
+            g.set_state(ref.state())
+        else:
+            ref.step(1)
+    assert worst < REL_TOL, worst
+    g.close()
+
+
+# --------------------------------------------------------------------------------------
+# edge cases
+# --------------------------------------------------------------------------------------
+
+def test_edge_cases(P):
+    # all bodies pinned: nothing moves
+    sc = S.box_pile(nx=2, ny=2, nz=2)
+    sc.bodies["pinned"] = 1
+    g = P.Scene(sc)
+    st0 = g.state()
+    g.step(3)
+    assert np.array_equal(g.state(), st0)
+    g.close()
+    # a single body on the ground matches the oracle
+    sc = S.single_body(c=(0, 0.52, 0), v=(0.5, -1, 0), n_iter=10)
+    ref = O.OracleScene(sc)
+    g = P.Scene(sc)
+    for _ in range(30):
+        a, b = teacher_forced_step(g, ref)
+        assert rel_err(a, b, _he(sc)) < REL_TOL
+    g.close()
+
+
+def test_capacity_overflow_is_reported(P):
+    sc = _pile_small()
+    ref = O.OracleScene(sc)
+    ref.step(60)
+    g = P.Scene(sc, max_contacts=8)
+    g.set_state(ref.state())
+    g.step(1)
+    with pytest.raises(P.PabdError) as e:
+        g.sync()
+    assert e.value.code == P.ERR_CAPACITY
+    g.close()
