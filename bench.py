@@ -96,20 +96,28 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+ARGS = None
+
+
 def workload():
-    return S.box_pile()
+    n = ARGS.bodies if ARGS is not None else 4096
+    if n == 4096 and not (ARGS is not None and ARGS.stacked):
+        return S.box_pile()
+    return S.box_pile_n(n, stacked=bool(ARGS is not None and ARGS.stacked))
 
 
 def config_of(sc, K):
-    return {"workload": f"box pile {sc.n_bodies} (16^3 jittered grid, spacing 3.5), {sc.params['n_iter']} sweeps, "
-                        f"h=1/60, steps 0..{K - 1} of the trajectory",
+    start = ARGS.start_step if ARGS is not None else 0
+    kind = "stacked columns" if (ARGS is not None and ARGS.stacked) else "jittered grid, spacing 3.5"
+    return {"workload": f"box pile {sc.n_bodies} ({kind}), {sc.params['n_iter']} sweeps, "
+                        f"h=1/60, steps {start}..{start + K - 1} of the trajectory",
             "n_bodies": sc.n_bodies, "n_iter": sc.params["n_iter"], "l2": "flushed between timed steps (256 MB write)",
             "parallelism": "replicas"}
 
 
 def _kernel_hash():
     h = hashlib.sha256()
-    for f in ("k_sweep.cu", "pabd_internal.h"):
+    for f in ("k_sweep.cu", "k_persist.cu", "sweep_math.cuh", "pabd_internal.h"):
         with open(os.path.join(ROOT, "paper_2609_02675_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -177,13 +185,13 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream(dev)
     sc = workload()
     K, W = args.steps, args.warmup
-    g = P.Scene(sc, device=dev, stream=stream)
+    g = P.Scene(sc, device=dev, stream=stream, sweep_mode=args.sweep_mode, sweep_lanes=args.lanes)
     st0 = g.state()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
 
     def reset():
         g.set_state(st0)
-        g.set_step_index(0)
+        g.set_step_index(args.start_step)
 
     def l2_flush():
         with torch.cuda.stream(stream):
@@ -194,7 +202,12 @@ def run_ours(args, rank, world, local_rank):
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
 
-    # warm-up, then restore the initial state
+    # optional untimed lead-in (part of preparing the input state), then warm-up and restore
+    if args.start_step:
+        g.step(args.start_step)
+        g.sync()
+        st0 = g.state()
+    g.set_step_index(args.start_step)
     g.step(W)
     g.sync()
     reset()
@@ -268,14 +281,21 @@ def run_ours(args, rank, world, local_rank):
     n_it = sc.params["n_iter"]
     bonds_avg = prof["bonds_sum"] / steps
     N = sc.n_bodies
-    per_kernel = {
-        # bytes per launch, each array element moved once: bond = static bond records (64 B)
-        # + CSR slot pair (8 B) + two end records written (32 B) per bond + q read (48 B) per body;
-        # solve = q in/out, predictor, mass, flags, CSR offset, residual (176 B) per body
-        # + two end records and two material points read (64 B) per bond
-        "k_bond": (104.0 * bonds_avg + 48.0 * N, prof["bond_ms"] / max(prof["bond_launches"], 1)),
-        "k_solve": (176.0 * N + 64.0 * bonds_avg, prof["solve_ms"] / max(prof["solve_launches"], 1)),
-    }
+    fused = info1["sweep_mode"] == 0
+    if fused:
+        # one launch runs n_it sweeps; per sweep each body moves q in/out, s, mass, flags, CSR
+        # offset and residual (176 B) and each bond's two end records (2 x 48 B) plus, for a
+        # contact, its normal twice (2 x 16 B)
+        per_sweep = 176.0 * N + 128.0 * bonds_avg
+        per_kernel = {"k_sweep_fused": (n_it * per_sweep, prof["bond_ms"] / steps)}
+    else:
+        per_kernel = {
+            # bond = static bond records (64 B) + CSR slot pair (8 B) + two end records written
+            # (32 B) per bond + q read (48 B) per body; solve = q in/out, predictor, mass, flags,
+            # CSR offset, residual (176 B) per body + two end records and material points (64 B)
+            "k_bond": (104.0 * bonds_avg + 48.0 * N, prof["bond_ms"] / max(prof["bond_launches"], 1)),
+            "k_solve": (176.0 * N + 64.0 * bonds_avg, prof["solve_ms"] / max(prof["solve_launches"], 1)),
+        }
     dom = max(per_kernel, key=lambda k: per_kernel[k][1])
     bytes_launch, ms_launch = per_kernel[dom]
     achieved = bytes_launch / (ms_launch * 1e-3) / 1e9
@@ -284,13 +304,15 @@ def run_ours(args, rank, world, local_rank):
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
             "traffic": tr["bytes_per_launch"] if tr else None,
-            "bytes_per_launch": bytes_launch, "us_per_launch": ms_launch * 1e3,
+            "bytes_per_launch": bytes_launch, "us_per_launch": ms_launch * 1e3, "bonds_per_step": bonds_avg,
             "stage_ms_per_step": {k: prof[k] / steps for k in ("collision_ms", "csr_ms", "predict_ms", "bond_ms",
                                                                  "solve_ms", "finalize_ms", "step_ms")}}
+    cfg = config_of(sc, K)
+    cfg["sweep"] = {k: info1[k] for k in ("sweep_mode", "sweep_lanes", "sweep_block", "sweep_grid")}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic", "config": config_of(sc, K),
+        "dtype": "f32", "data": "synthetic", "config": cfg,
         "steps_per_s": world * K / (t_ms * 1e-3),
         "plain_path": {"value": total_body_iter / (t_plain * 1e-3), "unit": UNIT, "ms_per_step": t_plain / K},
         "e2e": {"value": total_body_iter / (t_e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -311,7 +333,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--bodies", type=int, default=4096, help="pile size (4096 = the 16^3 pile)")
+    ap.add_argument("--stacked", action="store_true", help="pile as touching columns (contacts from step 0)")
+    ap.add_argument("--start-step", type=int, default=0, help="untimed lead-in steps before the timed window")
+    ap.add_argument("--sweep-mode", type=int, default=0, help="0: fused persistent sweep, 1: two launches per sweep")
+    ap.add_argument("--lanes", type=int, default=0, help="lanes per body in the fused sweep (0: library default)")
     args = ap.parse_args()
+    global ARGS
+    ARGS = args
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -86,6 +86,11 @@ typedef struct {
     int body_contacts;        /* 0: only ground contacts */
     double large_he;          /* bodies with a half extent above this skip the grid */
     int precision_policy;     /* 0: FP32 solves; 1: FP64 per-body solve where ill-conditioned */
+    int sweep_mode;           /* 0: fused persistent sweep (one cooperative launch runs all
+                                 n_iter iterations); 1: a bond launch + a solve launch per sweep */
+    int sweep_lanes;          /* lanes per body in the fused sweep: 1, 2, 4, 8 or 16; 0 = 4.
+                                 Fixes the summation order (results depend on it, not on the
+                                 block / grid sizes, which the library autotunes) */
     size_t max_pairs;         /* capacities; 0 = 16 per body */
     size_t max_contacts;      /* 0 = 24 per body */
     void* stream;             /* cudaStream_t on which all work is enqueued (NULL: default) */
@@ -129,6 +134,7 @@ typedef struct {
     int64_t launches;         /* kernels launched by this scene so far */
     int64_t fp64_bodies;      /* bodies whose solve is statically flagged for FP64 */
     int64_t device_bytes;     /* device memory held by the scene */
+    int64_t sweep_mode, sweep_lanes, sweep_block, sweep_grid;  /* fused sweep launch shape */
 } pabd_info;
 
 /* Create an empty scene on the current CUDA device.  *out receives the handle. */

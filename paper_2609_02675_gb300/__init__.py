@@ -41,7 +41,7 @@ class pabd_scene_desc(ctypes.Structure):
         ("mu", ctypes.c_double), ("c_kappa", ctypes.c_double), ("d_hat_rel", ctypes.c_double),
         ("margin", ctypes.c_double), ("project", ctypes.c_int), ("body_contacts", ctypes.c_int),
         ("large_he", ctypes.c_double), ("precision_policy", ctypes.c_int),
-        ("max_pairs", ctypes.c_size_t), ("max_contacts", ctypes.c_size_t),
+        ("sweep_mode", ctypes.c_int), ("sweep_lanes", ctypes.c_int), ("max_pairs", ctypes.c_size_t), ("max_contacts", ctypes.c_size_t),
         ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
     ]
 
@@ -65,7 +65,8 @@ class pabd_bond_desc(ctypes.Structure):
 class pabd_info(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
         "n_bodies", "n_groups", "n_static_bonds", "n_bonds", "n_pairs", "n_contacts", "step_index",
-        "max_pairs", "max_contacts", "graph_nodes", "launches", "fp64_bodies", "device_bytes")]
+        "max_pairs", "max_contacts", "graph_nodes", "launches", "fp64_bodies", "device_bytes",
+        "sweep_mode", "sweep_lanes", "sweep_block", "sweep_grid")]
 
 
 _P = ctypes.c_void_p
@@ -249,7 +250,7 @@ class _TorchAllocator:
 
 
 def scene_desc(params: dict, stream=0, allocator: _TorchAllocator | None = None, precision_policy=1,
-               max_pairs=0, max_contacts=0) -> pabd_scene_desc:
+               max_pairs=0, max_contacts=0, sweep_mode=0, sweep_lanes=0) -> pabd_scene_desc:
     d = pabd_scene_desc()
     d.h = params["h"]
     d.gravity = D3(*params["gravity"])
@@ -265,6 +266,8 @@ def scene_desc(params: dict, stream=0, allocator: _TorchAllocator | None = None,
     d.body_contacts = int(params["body_contacts"])
     d.large_he = params["large_he"]
     d.precision_policy = int(precision_policy)
+    d.sweep_mode = int(sweep_mode)
+    d.sweep_lanes = int(sweep_lanes)
     d.max_pairs = int(max_pairs)
     d.max_contacts = int(max_contacts)
     d.stream = stream or None
@@ -281,7 +284,7 @@ class Scene:
     """A library scene built from a ``scenes.Scene`` (bodies and user bonds)."""
 
     def __init__(self, scene, device: int = 0, stream=None, torch_memory: bool = True, precision_policy: int = 1,
-                 max_pairs: int = 0, max_contacts: int = 0):
+                 max_pairs: int = 0, max_contacts: int = 0, sweep_mode: int = 0, sweep_lanes: int = 0):
         import torch
         torch.cuda.set_device(device)
         if stream is None:
@@ -289,7 +292,7 @@ class Scene:
         self.torch_stream = stream
         self._alloc = _TorchAllocator(device, stream.cuda_stream) if torch_memory else None
         self.desc = scene_desc(scene.params, stream.cuda_stream, self._alloc, precision_policy, max_pairs,
-                               max_contacts)
+                               max_contacts, sweep_mode, sweep_lanes)
         self.h = pabd_create_scene(self.desc)
         self.n = scene.n_bodies
         self.n_groups = scene.n_groups

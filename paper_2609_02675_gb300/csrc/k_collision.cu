@@ -141,63 +141,107 @@ __device__ __forceinline__ bool pair_ok(const Dev& d, int i, int j, int gi, int 
     return true;
 }
 
-// Visit the partners j > i of body i in a fixed order; F(j) is called for each accepted j.
+// Pair finding, one warp per body i.  A grid body: lane c < 27 scans neighbour cell c
+// (dx, dy, dz = c % 3 - 1, c / 3 % 3 - 1, c / 9 - 1), then the lanes stride over the large
+// bodies; the partners are written at per-lane offsets and the body's slice is sorted.  A
+// large body: the warp sweeps j = i+1 .. N-1 in chunks of 32 and compacts with a ballot,
+// which keeps j ascending.  Accepted partners: j > i, same group, not both pinned, inflated
+// boxes overlap, not joined by a user bond.
 template <class F>
-__device__ __forceinline__ void for_partners(const Dev& d, int i, F&& f) {
+__device__ __forceinline__ int lane_partners(const Dev& d, int i, int lane, F&& f) {
     const int gi = d.group[i], fi = d.bflags[i];
-    if (fi & BF_LARGE) {
-        for (int j = i + 1; j < d.N; ++j)
-            if (pair_ok(d, i, j, gi, fi)) f(j);
-        return;
+    int n = 0;
+    if (lane < 27) {
+        const int4 ci = d.cell[i];
+        const int x = ci.x + lane % 3 - 1, y = ci.y + (lane / 3) % 3 - 1, z = ci.z + lane / 9 - 1;
+        const int hb = cell_hash(x, y, z, d.table_bits);
+        const int s = d.bucket_off[hb], e = d.bucket_off[hb + 1];
+        for (int k = s; k < e; ++k) {
+            const int j = d.bucket_items[k];
+            if (j <= i) continue;
+            const int4 cj = d.cell[j];
+            if (cj.x != x || cj.y != y || cj.z != z) continue;
+            if (pair_ok(d, i, j, gi, fi)) { f(j, n); ++n; }
+        }
     }
-    const int4 ci = d.cell[i];
-    for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-                int x = ci.x + dx, y = ci.y + dy, z = ci.z + dz;
-                int hb = cell_hash(x, y, z, d.table_bits);
-                int s = d.bucket_off[hb], e = d.bucket_off[hb + 1];
-                for (int k = s; k < e; ++k) {
-                    int j = d.bucket_items[k];
-                    if (j <= i) continue;
-                    int4 cj = d.cell[j];
-                    if (cj.x != x || cj.y != y || cj.z != z) continue;
-                    if (pair_ok(d, i, j, gi, fi)) f(j);
-                }
-            }
-    for (int k = 0; k < d.Nlarge; ++k) {
-        int j = d.large_ids[k];
-        if (j > i && pair_ok(d, i, j, gi, fi)) f(j);
+    for (int k = lane; k < d.Nlarge; k += 32) {
+        const int j = d.large_ids[k];
+        if (j > i && pair_ok(d, i, j, gi, fi)) { f(j, n); ++n; }
     }
+    return n;
+}
+
+__device__ __forceinline__ int warp_sum(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int warp_excl(int v, int lane) {
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    return inc - v;
 }
 
 __global__ void k_pair_count(Dev d) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (i >= d.N) return;
     int n = 0;
-    if (d.p.body_contacts) for_partners(d, i, [&](int) { ++n; });
-    d.pair_cnt[i] = n;
+    if (d.p.body_contacts) {
+        const int gi = d.group[i], fi = d.bflags[i];
+        if (fi & BF_LARGE) {
+            for (int j0 = i + 1; j0 < d.N; j0 += 32) {
+                const int j = j0 + lane;
+                n += (j < d.N && pair_ok(d, i, j, gi, fi)) ? 1 : 0;
+            }
+        } else {
+            n = lane_partners(d, i, lane, [](int, int) {});
+        }
+    }
+    n = warp_sum(n);
+    if (lane == 0) d.pair_cnt[i] = n;
 }
 
 __global__ void k_pair_write(Dev d) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (i >= d.N) return;
     const int s = d.pair_off[i];
     const int cap = d.cap_pairs;
-    int n = 0;
-    if (d.p.body_contacts) for_partners(d, i, [&](int j) {
-        if (s + n < cap) d.pairs[s + n] = make_int2(i, j);
-        ++n;
-    });
-    int e = min(s + n, cap);
-    // insertion sort of the partner list (ascending j)
-    for (int a = s + 1; a < e; ++a) {
-        int2 v = d.pairs[a];
-        int b = a - 1;
-        while (b >= s && d.pairs[b].y > v.y) { d.pairs[b + 1] = d.pairs[b]; --b; }
-        d.pairs[b + 1] = v;
+    if (d.p.body_contacts) {
+        const int gi = d.group[i], fi = d.bflags[i];
+        if (fi & BF_LARGE) {
+            int pos = s;
+            for (int j0 = i + 1; j0 < d.N; j0 += 32) {
+                const int j = j0 + lane;
+                const bool ok = j < d.N && pair_ok(d, i, j, gi, fi);
+                const unsigned bal = __ballot_sync(0xffffffffu, ok);
+                const int at = pos + __popc(bal & ((1u << lane) - 1u));
+                if (ok && at < cap) d.pairs[at] = make_int2(i, j);
+                pos += __popc(bal);
+            }
+        } else {
+            const int mine = lane_partners(d, i, lane, [](int, int) {});
+            const int base = s + warp_excl(mine, lane);
+            lane_partners(d, i, lane, [&](int j, int k) {
+                if (base + k < cap) d.pairs[base + k] = make_int2(i, j);
+            });
+            __syncwarp();
+            if (lane == 0) {
+                const int e = min(d.pair_off[i + 1], cap);
+                for (int a = s + 1; a < e; ++a) {  // insertion sort of the slice by j
+                    int2 v = d.pairs[a];
+                    int b = a - 1;
+                    while (b >= s && d.pairs[b].y > v.y) { d.pairs[b + 1] = d.pairs[b]; --b; }
+                    d.pairs[b + 1] = v;
+                }
+            }
+        }
     }
-    if (i == d.N - 1) {
+    if (i == d.N - 1 && lane == 0) {
         int tot = d.pair_off[d.N];
         if (tot > cap) atomicOr(&d.ctr[C_STATUS], ST_CAPACITY);
         d.ctr[C_NPAIRS] = min(tot, cap);
@@ -423,9 +467,10 @@ void launch_collision(const Dev& d, cudaStream_t st, long long* launches) {
     k_cells<<<nblk(d.N), CT, 0, st>>>(d);
     scan_exclusive(d.bucket_cnt, d.bucket_off, nullptr, T, d.scan_scratch, st, launches);
     k_bucket_fill<<<nblk(d.N), CT, 0, st>>>(d);
-    k_pair_count<<<nblk(d.N), CT, 0, st>>>(d);
+    const int wblk = (d.N * 32 + CT - 1) / CT > 0 ? (d.N * 32 + CT - 1) / CT : 1;  // one warp per body
+    k_pair_count<<<wblk, CT, 0, st>>>(d);
     scan_exclusive(d.pair_cnt, d.pair_off, nullptr, d.N, d.scan_scratch, st, launches);
-    k_pair_write<<<nblk(d.N), CT, 0, st>>>(d);
+    k_pair_write<<<wblk, CT, 0, st>>>(d);
     const int nt = d.cap_pairs > d.N ? d.cap_pairs : d.N;
     k_narrow_count<<<nblk(nt), CT, 0, st>>>(d);
     scan_exclusive(d.npc, d.npc_off, d.ctr + C_NPAIRS, d.cap_pairs, d.scan_scratch, st, launches);

@@ -172,17 +172,26 @@ __global__ void k_csr_sort(Dev d) {
     }
 }
 
-// per-group residual sqrt(sum over the group's bodies of |q^{k+1} - q^k|^2): one warp per
-// group, fixed lane order and shuffle tree (deterministic)
-__global__ void k_group_resid(Dev d) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (warp >= d.G) return;
-    const int s = d.group_off[warp], e = d.group_off[warp + 1];
+// per-group residual sqrt(sum over the group's bodies of |q^{k+1} - q^k|^2): one block of
+// RES_T threads per group, fixed per-thread strides, warp shuffle tree, warps summed in
+// order by thread 0 (deterministic)
+constexpr int RES_T = 128;
+__global__ void __launch_bounds__(RES_T) k_group_resid(Dev d) {
+    __shared__ double part[RES_T / 32];
+    const int g = blockIdx.x;
+    if (g >= d.G) return;
+    const int s = d.group_off[g], e = d.group_off[g + 1];
     double acc = 0.0;
-    for (int b = s + lane; b < e; b += 32) acc += d.resid_body[b];
+    for (int b = s + threadIdx.x; b < e; b += RES_T) acc += d.resid_body[b];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) d.resid_group[warp] = sqrt(acc);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < RES_T / 32; ++w) t += part[w];
+        d.resid_group[g] = sqrt(t);
+    }
 }
 
 void launch_predict(const Dev& d, cudaStream_t st, long long* launches) {
@@ -208,7 +217,7 @@ void launch_csr(const Dev& d, cudaStream_t st, long long* launches) {
 
 void launch_finalize(const Dev& d, const float4* q_fin, cudaStream_t st, long long* launches) {
     k_finalize<<<nblk(d.N), ST_T, 0, st>>>(d, q_fin);
-    k_group_resid<<<(d.G * 32 + ST_T - 1) / ST_T > 0 ? (d.G * 32 + ST_T - 1) / ST_T : 1, ST_T, 0, st>>>(d);
+    k_group_resid<<<d.G > 0 ? d.G : 1, RES_T, 0, st>>>(d);
     *launches += 2;
 }
 

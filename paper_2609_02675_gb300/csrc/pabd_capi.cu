@@ -77,6 +77,8 @@ struct pabd_scene {
     cudaGraph_t prof_graph = nullptr;
     cudaGraphExec_t prof_exec = nullptr;
     double prof_acc[PABD_PROFILE_SLOTS] = {0};
+    // fused sweep launch shape
+    int fused = 0, lanes = 4, sw_block = 128, sw_grid = 1;
 
     void* dalloc(size_t n) {
         if (n == 0) n = 16;
@@ -123,15 +125,74 @@ void enqueue_step(pabd_scene* s, long long* launches, const cudaEvent_t* ev = nu
     mark();
     float4* cur = d.qa;
     float4* nxt = d.qb;
-    for (int it = 0; it < d.p.n_iter; ++it) {
-        launch_bond(d, cur, s->st, launches);
-        mark();
-        launch_solve(d, cur, nxt, it == d.p.n_iter - 1, s->st, launches);
-        mark();
-        float4* t = cur; cur = nxt; nxt = t;
+    if (s->fused) {
+        // events: [4] = the whole fused sweep, [5 .. 3 + 2 n_iter] unused (recorded together)
+        cudaMemsetAsync(d.ctr + C_FP64DYN, 0, sizeof(int), s->st);
+        launch_fused_sweep(d, s->lanes, s->sw_block, s->sw_grid, s->st, launches);
+        for (int it = 0; it < d.p.n_iter; ++it) {
+            mark();
+            mark();
+            float4* t = cur; cur = nxt; nxt = t;
+        }
+    } else {
+        for (int it = 0; it < d.p.n_iter; ++it) {
+            launch_bond(d, cur, s->st, launches);
+            mark();
+            launch_solve(d, cur, nxt, it == d.p.n_iter - 1, s->st, launches);
+            mark();
+            float4* t = cur; cur = nxt; nxt = t;
+        }
     }
     launch_finalize(d, cur, s->st, launches);
     mark();
+}
+
+// Launch-shape autotuner for the fused sweep: with the scene's step-0 collision, CSR and
+// predictor in place (none of them changes q^n), time the sweep for each block size at the
+// largest co-resident grid the work can use; keep the fastest.  The shape never changes the
+// results (each body's arithmetic does not depend on which block runs it).
+pabd_status autotune_sweep(pabd_scene* s) {
+    Dev& d = s->d;
+    long long lc = 0;
+    launch_drive_update(d, s->st, &lc);
+    launch_collision(d, s->st, &lc);
+    launch_csr(d, s->st, &lc);
+    launch_predict(d, s->st, &lc);
+    CK(cudaGetLastError());
+    const int blocks[] = {64, 128, 256, 512};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int bs : blocks) {
+        int maxg = fused_max_blocks(s->lanes, bs);
+        if (maxg <= 0) continue;
+        long long need = ((long long)d.N * s->lanes + bs - 1) / bs;
+        int grid = (int)std::min<long long>(need, maxg);
+        if (grid < 1) grid = 1;
+        float tot = 0.f;
+        bool ok = true;
+        for (int r = 0; r < 4 && ok; ++r) {
+            CK(cudaEventRecord(e0, s->st));
+            ok = launch_fused_sweep(d, s->lanes, bs, grid, s->st, &lc) == cudaSuccess;
+            CK(cudaEventRecord(e1, s->st));
+            CK(cudaEventSynchronize(e1));
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, e0, e1));
+            if (r > 0) tot += t;  // first launch warms caches
+        }
+        if (ok && tot < best) { best = tot; s->sw_block = bs; s->sw_grid = grid; }
+    }
+    cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best >= 1e30f) s->fused = 0;
+    // leave the counters as a fresh scene has them
+    CK(cudaMemsetAsync(d.ctr, 0, sizeof(int) * C_COUNT, s->st));
+    int nb0 = d.Nc;
+    CK(cudaMemcpyAsync(d.ctr + C_NBONDS, &nb0, sizeof(int), cudaMemcpyHostToDevice, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return PABD_OK;
 }
 
 pabd_status finalize_scene(pabd_scene* s) {
@@ -260,6 +321,8 @@ pabd_status finalize_scene(pabd_scene* s) {
     ok &= alloc_arr(s, d.end_cnt, N) && alloc_arr(s, d.end_cur, N) && alloc_arr(s, d.end_off, N + 1);
     ok &= alloc_arr(s, d.end_id, d.cap_ends) && alloc_arr(s, d.end_pos, d.cap_ends);
     ok &= alloc_arr(s, d.ends, d.cap_ends) && alloc_arr(s, d.end_x, d.cap_ends);
+    ok &= alloc_arr(s, d.rec_m, d.cap_ends) && alloc_arr(s, d.rec_a, d.cap_ends) && alloc_arr(s, d.rec_b, d.cap_ends);
+    ok &= alloc_arr(s, d.gbar, 2);
     ok &= alloc_arr(s, d.lo, N) && alloc_arr(s, d.hi, N) && alloc_arr(s, d.cell, N);
     ok &= alloc_arr(s, d.bucket_cnt, T) && alloc_arr(s, d.bucket_cur, T) && alloc_arr(s, d.bucket_off, T + 1) &&
           alloc_arr(s, d.bucket_items, N);
@@ -304,10 +367,27 @@ pabd_status finalize_scene(pabd_scene* s) {
     CK(cudaMemsetAsync(d.resid_body, 0, sizeof(double) * (N ? N : 1), st));
     CK(cudaMemsetAsync(d.resid_group, 0, sizeof(double) * (d.G ? d.G : 1), st));
     CK(cudaMemsetAsync(d.end_pos, 0xff, sizeof(int) * d.cap_ends, st));
+    CK(cudaMemsetAsync(d.gbar, 0, 2 * sizeof(unsigned), st));
     // bonds beyond Nc start counted as zero until the first detection
     int nb0 = Nc;
     CK(cudaMemcpyAsync(d.ctr + C_NBONDS, &nb0, sizeof(int), cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
+
+    // fused sweep: lanes per body from the descriptor, block / grid from a timing sweep
+    s->fused = (ds.sweep_mode == 0) && N > 0;
+    if (s->fused) {
+        int coop = 0, dev = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        if (!coop) s->fused = 0;
+    }
+    if (s->fused) {
+        const int L = ds.sweep_lanes ? ds.sweep_lanes : 4;
+        if (L != 1 && L != 2 && L != 4 && L != 8 && L != 16) return PABD_ERR_ARG;
+        s->lanes = L;
+        pabd_status tr = autotune_sweep(s);
+        if (tr != PABD_OK) return tr;
+    }
 
     // capture one step as a graph
     long long lc = 0;
@@ -697,6 +777,8 @@ pabd_status pabd_read_residual(pabd_scene* s, double* out, size_t n_groups) {
 
 pabd_status pabd_get_info(pabd_scene* s, pabd_info* info) {
     if (!s || !info) return PABD_ERR_ARG;
+    pabd_status fr = finalize_scene(s);
+    if (fr != PABD_OK) return fr;
     std::memset(info, 0, sizeof *info);
     info->n_bodies = (int64_t)s->bodies.size();
     info->n_groups = s->bodies.empty() ? 0 : s->bodies.back().group + 1;
@@ -717,6 +799,10 @@ pabd_status pabd_get_info(pabd_scene* s, pabd_info* info) {
     info->graph_nodes = (int64_t)s->graph_nodes;
     info->fp64_bodies = s->fp64_bodies;
     info->device_bytes = (int64_t)s->bytes;
+    info->sweep_mode = s->fused ? 0 : 1;
+    info->sweep_lanes = s->lanes;
+    info->sweep_block = s->sw_block;
+    info->sweep_grid = s->sw_grid;
     return PABD_OK;
 }
 

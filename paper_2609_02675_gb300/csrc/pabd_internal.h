@@ -63,6 +63,10 @@ struct Dev {
     // CSR of bond ends
     int *end_cnt, *end_cur, *end_off, *end_id, *end_pos;
     float4 *ends, *end_x;
+    // bond-end records in CSR order for the fused sweep: (i, j, type, bond), x_i (+w0), x_j (+p1)
+    int4 *rec_m;
+    float4 *rec_a, *rec_b;
+    unsigned *gbar;             // grid barrier: arrival counter, generation
     // collision
     float4 *lo, *hi;            // inflated AABB; lo.w = inflation
     int4 *cell;                 // cell coords (.w = bucket)
@@ -90,5 +94,8 @@ void launch_bond(const Dev& d, const float4* q, cudaStream_t st, long long* laun
 void launch_solve(const Dev& d, const float4* q_in, float4* q_out, int last, cudaStream_t st, long long* launches);
 void launch_finalize(const Dev& d, const float4* q_fin, cudaStream_t st, long long* launches);
 void launch_drive_update(const Dev& d, cudaStream_t st, long long* launches);
+// fused persistent sweep (all n_iter iterations, cooperative launch); L lanes per body
+cudaError_t launch_fused_sweep(const Dev& d, int L, int block, int grid, cudaStream_t st, long long* launches);
+int fused_max_blocks(int L, int block);
 
 }  // namespace pabd

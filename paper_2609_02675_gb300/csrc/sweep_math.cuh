@@ -1,0 +1,247 @@
+// Device arithmetic shared by the sweep kernels (k_sweep.cu: bond + solve launches,
+// k_persist.cu: the fused persistent sweep): bond split forces, the per-body 4x4 system
+// and the rotation of the local solve.  One copy, so both paths compute identical bonds.
+#pragma once
+#include "pabd_internal.h"
+
+namespace pabd {
+
+__device__ __forceinline__ void ld_q(const float4* __restrict__ q, int b, float* c, float* A) {
+    float4 a = q[3 * b], bb = q[3 * b + 1], cc = q[3 * b + 2];
+    c[0] = a.x; c[1] = a.y; c[2] = a.z;
+    A[0] = a.w; A[1] = bb.x; A[2] = bb.y; A[3] = bb.z; A[4] = bb.w;
+    A[5] = cc.x; A[6] = cc.y; A[7] = cc.z; A[8] = cc.w;
+}
+
+__device__ __forceinline__ void world_pt(const float* c, const float* A, float4 x, float* y) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) y[k] = c[k] + A[3 * k] * x.x + A[3 * k + 1] * x.y + A[3 * k + 2] * x.z;
+}
+
+// Split force of one bond from the iterate (Eq. 15-17): returns w = h^2 phi+(d)/d and the
+// delta-form record f' of end i (end j gets -f'), see the file comment of k_sweep.cu.
+__device__ __forceinline__ float bond_force(int type, float4 xi, float4 xj, float4 nm, const float* yi,
+                                            const float* yj, float* f) {
+    float w = xi.w;
+    if (type == K_CONTACT || type == K_GROUND) {
+        const float dhat = xj.w;
+        float rr[3] = {yi[0] - yj[0], yi[1] - yj[1], yi[2] - yj[2]};
+        float g = nm.x * rr[0] + nm.y * rr[1] + nm.z * rr[2];
+        if (g < dhat) {
+            float t[3] = {rr[0] - g * nm.x, rr[1] - g * nm.y, rr[2] - g * nm.z};
+            float tn = sqrtf(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+            float tau = nm.w * (dhat - g);
+            float keep = tn > tau ? 1.f - tau / tn : 0.f;  // t - t_c = keep * t
+            const float N[3] = {nm.x, nm.y, nm.z};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) f[k] = w * ((dhat * N[k] + keep * t[k]) - rr[k]);
+        } else {
+            w = 0.f;
+            f[0] = f[1] = f[2] = 0.f;
+        }
+        return w;
+    }
+    float r[3] = {yj[0] - yi[0], yj[1] - yi[1], yj[2] - yi[2]};
+    if (type == K_SPHERICAL || type == K_DRIVE) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) f[k] = w * r[k];
+        return w;
+    }
+    float dd = sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    float n[3];
+    if (dd > 0.f) { float id = 1.f / dd; n[0] = r[0] * id; n[1] = r[1] * id; n[2] = r[2] * id; }
+    else { n[0] = 0.f; n[1] = 1.f; n[2] = 0.f; }
+    const float l = xj.w;
+    float s;
+    if (type == K_SPRING) {
+        s = w * (dd - l);                       // h^2 phi(d)
+    } else {                                    // nonlinear elastic, tangent split
+        const float il2 = 1.f / (l * l);
+        s = (w * (1.f / 3.f)) * (dd * dd * dd * il2 - l);
+        w = w * dd * dd * il2;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) f[k] = s * n[k];
+    return w;
+}
+
+// ---- 4x4 SPD system with three right-hand sides ----
+// G packed as g[10] = (00 01 02 03 11 12 13 22 23 33); R[4][3]
+template <class T>
+struct Sys {
+    T g[10];
+    T r[4][3];
+};
+
+template <class T>
+__device__ __forceinline__ void sys_init(Sys<T>& s, float4 mass, const float* dc, const float* dA) {
+    s.g[0] = mass.x; s.g[1] = 0; s.g[2] = 0; s.g[3] = 0;
+    s.g[4] = mass.y; s.g[5] = 0; s.g[6] = 0;
+    s.g[7] = mass.z; s.g[8] = 0;
+    s.g[9] = mass.w;
+    const T pm[4] = {(T)mass.x, (T)mass.y, (T)mass.z, (T)mass.w};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        s.r[0][k] = pm[0] * (T)dc[k];
+#pragma unroll
+        for (int l = 0; l < 3; ++l) s.r[1 + l][k] = pm[1 + l] * (T)dA[3 * k + l];
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void sys_add(Sys<T>& s, float4 e, float4 x) {
+    const T w = e.x;
+    const T z1 = x.x, z2 = x.y, z3 = x.z;
+    const T wz1 = w * z1, wz2 = w * z2, wz3 = w * z3;
+    s.g[0] += w;   s.g[1] += wz1;      s.g[2] += wz2;      s.g[3] += wz3;
+    s.g[4] += wz1 * z1; s.g[5] += wz1 * z2; s.g[6] += wz1 * z3;
+    s.g[7] += wz2 * z2; s.g[8] += wz2 * z3;
+    s.g[9] += wz3 * z3;
+    const T f[3] = {(T)e.y, (T)e.z, (T)e.w};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        s.r[0][k] += f[k];
+        s.r[1][k] += z1 * f[k];
+        s.r[2][k] += z2 * f[k];
+        s.r[3][k] += z3 * f[k];
+    }
+}
+
+// Cholesky G = L L^T and solve; returns the smallest pivot / diagonal ratio (<= 0: failed)
+template <class T>
+__device__ __forceinline__ T sys_solve(const Sys<T>& s, T out[4][3]) {
+    const T* g = s.g;
+    T d0 = g[0];
+    T l00 = sqrt(d0), i0 = T(1) / l00;
+    T l10 = g[1] * i0, l20 = g[2] * i0, l30 = g[3] * i0;
+    T d1 = g[4] - l10 * l10;
+    T l11 = sqrt(d1), i1 = T(1) / l11;
+    T l21 = (g[5] - l20 * l10) * i1, l31 = (g[6] - l30 * l10) * i1;
+    T d2 = g[7] - l20 * l20 - l21 * l21;
+    T l22 = sqrt(d2), i2 = T(1) / l22;
+    T l32 = (g[8] - l30 * l20 - l31 * l21) * i2;
+    T d3 = g[9] - l30 * l30 - l31 * l31 - l32 * l32;
+    T l33 = sqrt(d3), i3 = T(1) / l33;
+    T ratio = d0 > 0 ? T(1) : T(-1);
+    ratio = fmin(ratio, d1 / g[4]);
+    ratio = fmin(ratio, d2 / g[7]);
+    ratio = fmin(ratio, d3 / g[9]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        T y0 = s.r[0][k] * i0;
+        T y1 = (s.r[1][k] - l10 * y0) * i1;
+        T y2 = (s.r[2][k] - l20 * y0 - l21 * y1) * i2;
+        T y3 = (s.r[3][k] - l30 * y0 - l31 * y1 - l32 * y2) * i3;
+        T x3 = y3 * i3;
+        T x2 = (y2 - l32 * x3) * i2;
+        T x1 = (y1 - l21 * x2 - l31 * x3) * i1;
+        T x0 = (y0 - l10 * x1 - l20 * x2 - l30 * x3) * i0;
+        out[0][k] = x0; out[1][k] = x1; out[2][k] = x2; out[3][k] = x3;
+    }
+    return ratio;
+}
+
+// ---- local solve: rotation of A ----
+
+__device__ __forceinline__ void cofactor(const float* X, float* C) {
+    C[0] = X[4] * X[8] - X[5] * X[7]; C[1] = X[5] * X[6] - X[3] * X[8]; C[2] = X[3] * X[7] - X[4] * X[6];
+    C[3] = X[2] * X[7] - X[1] * X[8]; C[4] = X[0] * X[8] - X[2] * X[6]; C[5] = X[1] * X[6] - X[0] * X[7];
+    C[6] = X[1] * X[5] - X[2] * X[4]; C[7] = X[2] * X[3] - X[0] * X[5]; C[8] = X[0] * X[4] - X[1] * X[3];
+}
+
+// Fallback: eigen-decomposition of S = A^T A by cyclic Jacobi rotations; R = U V^T with
+// u1 = A v1 / |A v1|, u2 = normalised (A v2 - (u1 . A v2) u1), u3 = u1 x u2, det V = +1.
+__device__ __noinline__ static void polar_eigen(float* X) {
+    float S[9], V[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) S[3 * r + c] = X[r] * X[c] + X[3 + r] * X[3 + c] + X[6 + r] * X[6 + c];
+    for (int sweep = 0; sweep < 12; ++sweep) {
+        float off = fabsf(S[1]) + fabsf(S[2]) + fabsf(S[5]);
+        float sc = fabsf(S[0]) + fabsf(S[4]) + fabsf(S[8]);
+        if (off <= 1e-9f * sc) break;
+        for (int pq = 0; pq < 3; ++pq) {
+            const int p = pq == 2 ? 1 : 0, qd = pq == 0 ? 1 : 2;
+            float apq = S[3 * p + qd];
+            if (fabsf(apq) <= 1e-30f) continue;
+            float tau = (S[3 * qd + qd] - S[3 * p + p]) / (2.f * apq);
+            float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+            float cc = rsqrtf(1.f + t * t), ss = t * cc;
+            for (int k = 0; k < 3; ++k) {  // S <- S J
+                float skp = S[3 * k + p], skq = S[3 * k + qd];
+                S[3 * k + p] = cc * skp - ss * skq;
+                S[3 * k + qd] = ss * skp + cc * skq;
+            }
+            for (int k = 0; k < 3; ++k) {  // S <- J^T S
+                float spk = S[3 * p + k], sqk = S[3 * qd + k];
+                S[3 * p + k] = cc * spk - ss * sqk;
+                S[3 * qd + k] = ss * spk + cc * sqk;
+            }
+            for (int k = 0; k < 3; ++k) {
+                float vkp = V[3 * k + p], vkq = V[3 * k + qd];
+                V[3 * k + p] = cc * vkp - ss * vkq;
+                V[3 * k + qd] = ss * vkp + cc * vkq;
+            }
+        }
+    }
+    int o[3] = {0, 1, 2};
+    float lam[3] = {S[0], S[4], S[8]};
+    for (int a = 0; a < 3; ++a)
+        for (int b = a + 1; b < 3; ++b)
+            if (lam[o[b]] > lam[o[a]]) { int t = o[a]; o[a] = o[b]; o[b] = t; }
+    float v[3][3], u[3][3];
+    for (int c = 0; c < 3; ++c)
+        for (int r = 0; r < 3; ++r) v[c][r] = V[3 * r + o[c]];
+    // det V = +1
+    float dv = v[0][0] * (v[1][1] * v[2][2] - v[1][2] * v[2][1]) - v[0][1] * (v[1][0] * v[2][2] - v[1][2] * v[2][0]) +
+               v[0][2] * (v[1][0] * v[2][1] - v[1][1] * v[2][0]);
+    if (dv < 0.f) for (int r = 0; r < 3; ++r) v[2][r] = -v[2][r];
+    float av[3][3];
+    for (int c = 0; c < 2; ++c)
+        for (int r = 0; r < 3; ++r) av[c][r] = X[3 * r] * v[c][0] + X[3 * r + 1] * v[c][1] + X[3 * r + 2] * v[c][2];
+    float n0 = sqrtf(av[0][0] * av[0][0] + av[0][1] * av[0][1] + av[0][2] * av[0][2]);
+    if (n0 > 1e-20f) for (int r = 0; r < 3; ++r) u[0][r] = av[0][r] / n0;
+    else { u[0][0] = v[0][0]; u[0][1] = v[0][1]; u[0][2] = v[0][2]; }
+    float pr = u[0][0] * av[1][0] + u[0][1] * av[1][1] + u[0][2] * av[1][2];
+    for (int r = 0; r < 3; ++r) u[1][r] = av[1][r] - pr * u[0][r];
+    float n1 = sqrtf(u[1][0] * u[1][0] + u[1][1] * u[1][1] + u[1][2] * u[1][2]);
+    if (n1 > 1e-20f) for (int r = 0; r < 3; ++r) u[1][r] /= n1;
+    else {  // any unit vector orthogonal to u0
+        int m = 0;
+        for (int k = 1; k < 3; ++k) if (fabsf(u[0][k]) < fabsf(u[0][m])) m = k;
+        float e[3] = {0.f, 0.f, 0.f};
+        e[m] = 1.f;
+        u[1][0] = u[0][1] * e[2] - u[0][2] * e[1];
+        u[1][1] = u[0][2] * e[0] - u[0][0] * e[2];
+        u[1][2] = u[0][0] * e[1] - u[0][1] * e[0];
+        float nn = rsqrtf(u[1][0] * u[1][0] + u[1][1] * u[1][1] + u[1][2] * u[1][2]);
+        for (int r = 0; r < 3; ++r) u[1][r] *= nn;
+    }
+    u[2][0] = u[0][1] * u[1][2] - u[0][2] * u[1][1];
+    u[2][1] = u[0][2] * u[1][0] - u[0][0] * u[1][2];
+    u[2][2] = u[0][0] * u[1][1] - u[0][1] * u[1][0];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) X[3 * r + c] = u[0][r] * v[0][c] + u[1][r] * v[1][c] + u[2][r] * v[2][c];
+}
+
+__device__ __forceinline__ void polar_rotation(float* X) {
+    float C[9];
+    const float nrm = X[0] * X[0] + X[1] * X[1] + X[2] * X[2] + X[3] * X[3] + X[4] * X[4] + X[5] * X[5] +
+                      X[6] * X[6] + X[7] * X[7] + X[8] * X[8];
+    for (int it = 0; it < 12; ++it) {
+        cofactor(X, C);
+        const float det = X[0] * C[0] + X[1] * C[1] + X[2] * C[2];
+        if (!(det > 1e-6f * nrm * sqrtf(nrm))) { polar_eigen(X); return; }
+        const float z = rcbrtf(det);
+        const float iz = 1.f / (z * det);
+        float diff = 0.f;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            float nx = 0.5f * (z * X[k] + C[k] * iz);
+            diff += (nx - X[k]) * (nx - X[k]);
+            X[k] = nx;
+        }
+        if (diff < 1e-13f) break;
+    }
+}
+
+}  // namespace pabd

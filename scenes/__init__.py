@@ -187,10 +187,11 @@ def chain_pendulum(seed: int = SEED_BASE + 1, n_bodies=8, n_steps=100) -> Scene:
 
 
 def box_pile(seed: int = SEED_BASE + 2, nx=16, ny=16, nz=16, spacing=3.5, jitter=0.1,
-             n_steps=300, n_iter=30) -> Scene:
+             n_steps=300, n_iter=30, stacked=False) -> Scene:
     """Boxes with edges U[0.5, 2] per axis and density U[500, 2000], axis-aligned, on an
     nx*ny*nz grid (spacing 3.5, bottom layer centres at y = 2, jitter +-0.1 per axis),
-    dropped on the ground plane y = 0; mu = 0.5, h = 1/60."""
+    dropped on the ground plane y = 0; mu = 0.5, h = 1/60.  With stacked=True each column
+    starts as a stack: every box rests 2 mm above the one below (contacts from step 0)."""
     rng = np.random.default_rng(seed)
     n = nx * ny * nz
     b = _bodies(n)
@@ -206,6 +207,15 @@ def box_pile(seed: int = SEED_BASE + 2, nx=16, ny=16, nz=16, spacing=3.5, jitter
     b["c"][:, 1] = 2.0 + gy * spacing
     b["c"][:, 2] = (gz - 0.5 * (nz - 1)) * spacing
     b["c"] += rng.uniform(-jitter, jitter, (n, 3))
+    if stacked:
+        for col in range(nx * nz):
+            ks = np.where(gx * nz + gz == col)[0]
+            ks = ks[np.argsort(gy[ks])]
+            y = 0.0
+            for k in ks:
+                y += 0.002
+                b["c"][k, 1] = y + b["he"][k, 1]
+                y += 2.0 * b["he"][k, 1]
     params = default_params(h=1.0 / 60.0, n_iter=n_iter, mu=0.5)
     return Scene("box_pile", params, b, _bonds(0), n_steps, dict(seed=seed, grid=(nx, ny, nz)))
 

@@ -30,6 +30,13 @@ def rel_err(st_gpu: np.ndarray, st_ref: np.ndarray, he: np.ndarray) -> float:
     return float(d.max()) / scene_scale(st_ref, he)
 
 
+def worst_body(st_gpu: np.ndarray, st_ref: np.ndarray, he: np.ndarray):
+    """(body index, its corner error / scene diagonal) of the worst body."""
+    d = np.linalg.norm(corners(st_gpu, he) - corners(st_ref, he), axis=-1).max(axis=1)
+    k = int(np.argmax(d))
+    return k, float(d[k]) / scene_scale(st_ref, he)
+
+
 def teacher_forced_step(gpu, ref, n: int = 1):
     """Start the GPU from the oracle's state (rounded to FP32 on upload), step both n steps."""
     st0 = ref.state()
