@@ -88,7 +88,7 @@ typedef struct {
     int precision_policy;     /* 0: FP32 solves; 1: FP64 per-body solve where ill-conditioned */
     int sweep_mode;           /* 0: fused persistent sweep (one cooperative launch runs all
                                  n_iter iterations); 1: a bond launch + a solve launch per sweep */
-    int sweep_lanes;          /* lanes per body in the fused sweep: 1, 2, 4, 8 or 16; 0 = 4.
+    int sweep_lanes;          /* lanes per body in the per-body solve: 1, 2, 4, 8 or 16; 0 = 8.
                                  Fixes the summation order (results depend on it, not on the
                                  block / grid sizes, which the library autotunes) */
     size_t max_pairs;         /* capacities; 0 = 16 per body */
@@ -135,6 +135,8 @@ typedef struct {
     int64_t fp64_bodies;      /* bodies whose solve is statically flagged for FP64 */
     int64_t device_bytes;     /* device memory held by the scene */
     int64_t sweep_mode, sweep_lanes, sweep_block, sweep_grid;  /* fused sweep launch shape */
+    int64_t coop_fallbacks;   /* steps whose cooperative sweep launch was refused and ran as
+                                 two launches per sweep instead */
 } pabd_info;
 
 /* Create an empty scene on the current CUDA device.  *out receives the handle. */

@@ -48,127 +48,17 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, int* status) {
     return s_ok != 0;
 }
 
-template <class T, int L>
-__device__ __forceinline__ void sys_reduce(Sys<T>& s, unsigned mask) {
-#pragma unroll
-    for (int o = 1; o < L; o <<= 1) {
-#pragma unroll
-        for (int k = 0; k < 10; ++k) s.g[k] += __shfl_xor_sync(mask, s.g[k], o);
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) s.r[r][k] += __shfl_xor_sync(mask, s.r[r][k], o);
-    }
-}
-
-// accumulate the ends lane, lane + L, ... of body b's CSR slice
-template <class T, int L>
+// accumulate the ends lane, lane + L, ... of body b's CSR slice (bond forces in T)
+template <int L, class T>
 __device__ __forceinline__ void gather_ends(const Dev& d, const float4* __restrict__ q, int b, const float* cb,
                                             const float* Ab, int e0, int e1, int lane, Sys<T>& s) {
     for (int p = e0 + lane; p < e1; p += L) {
         const int4 m = d.rec_m[p];
         const float4 xa = d.rec_a[p], xb = d.rec_b[p];
-        const bool side_j = (m.y == b);
-        float c[3], A[9], yi[3], yj[3];
-        if (side_j) {
-            ld_q(q, m.x, c, A);
-            world_pt(c, A, xa, yi);
-            world_pt(cb, Ab, xb, yj);
-        } else {
-            world_pt(cb, Ab, xa, yi);
-            if (m.y >= 0) {
-                ld_q(q, m.y, c, A);
-                world_pt(c, A, xb, yj);
-            } else {
-                yj[0] = xb.x; yj[1] = xb.y; yj[2] = xb.z;
-            }
-        }
-        const float4 nm = (m.z == K_CONTACT || m.z == K_GROUND) ? d.bn[m.w] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float f[3];
-        const float w = bond_force(m.z, xa, xb, nm, yi, yj, f);
-        const float sg = side_j ? -1.f : 1.f;
-        sys_add(s, make_float4(w, sg * f[0], sg * f[1], sg * f[2]), side_j ? xb : xa);
+        T f[3];
+        const T w = end_force<T>(q, d.bn, b, cb, Ab, m, xa, xb, f);
+        sys_add_t(s, w, f, (m.y == b) ? xb : xa);
     }
-}
-
-template <class T>
-__device__ __forceinline__ void sys_zero(Sys<T>& s) {
-#pragma unroll
-    for (int k = 0; k < 10; ++k) s.g[k] = T(0);
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) s.r[r][k] = T(0);
-}
-
-template <int L>
-__device__ __forceinline__ void body_update(const Dev& d, int b, int lane, unsigned mask,
-                                            const float4* __restrict__ qi, float4* __restrict__ qo, int last) {
-    const int fl = d.bflags[b];
-    if (fl & BF_PINNED) {
-        if (lane == 0) {
-            qo[3 * b] = d.qn[3 * b]; qo[3 * b + 1] = d.qn[3 * b + 1]; qo[3 * b + 2] = d.qn[3 * b + 2];
-            d.resid_body[b] = 0.0;
-        }
-        return;
-    }
-    float c[3], A[9], sc[3], sA[9];
-    ld_q(qi, b, c, A);
-    ld_q(d.sq, b, sc, sA);
-    float dc[3], dA[9];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) dc[k] = sc[k] - c[k];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) dA[k] = sA[k] - A[k];
-    const float4 mass = d.mass[b];
-    const int e0 = d.end_off[b], e1 = d.end_off[b + 1];
-    float X[4][3];
-    bool use64 = d.p.precision_policy && (fl & BF_FP64);
-    if (!use64) {
-        Sys<float> s;
-        if (lane == 0) sys_init(s, mass, dc, dA);
-        else sys_zero(s);
-        gather_ends<float, L>(d, qi, b, c, A, e0, e1, lane, s);
-        sys_reduce<float, L>(s, mask);
-        const float ratio = sys_solve(s, X);
-        if (!(ratio >= 1e-4f) && d.p.precision_policy) {
-            use64 = true;
-            if (last && lane == 0) atomicAdd(&d.ctr[C_FP64DYN], 1);
-        }
-    }
-    if (use64) {
-        Sys<double> s;
-        if (lane == 0) sys_init(s, mass, dc, dA);
-        else sys_zero(s);
-        gather_ends<double, L>(d, qi, b, c, A, e0, e1, lane, s);
-        sys_reduce<double, L>(s, mask);
-        double Xd[4][3];
-        sys_solve(s, Xd);
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) X[r][k] = (float)Xd[r][k];
-    }
-    float cn[3], An[9];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        cn[k] = c[k] + X[0][k];
-#pragma unroll
-        for (int l = 0; l < 3; ++l) An[3 * k + l] = A[3 * k + l] + X[1 + l][k];
-    }
-    if (d.p.project) polar_rotation(An);
-    if (lane != 0) return;
-    double r2 = 0.0;
-    bool finite = true;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) { double t = (double)cn[k] - (double)c[k]; r2 += t * t; finite &= isfinite(cn[k]); }
-#pragma unroll
-    for (int k = 0; k < 9; ++k) { double t = (double)An[k] - (double)A[k]; r2 += t * t; finite &= isfinite(An[k]); }
-    if (!finite) atomicOr(&d.ctr[C_STATUS], ST_DIVERGED);
-    d.resid_body[b] = r2;
-    qo[3 * b] = make_float4(cn[0], cn[1], cn[2], An[0]);
-    qo[3 * b + 1] = make_float4(An[1], An[2], An[3], An[4]);
-    qo[3 * b + 2] = make_float4(An[5], An[6], An[7], An[8]);
 }
 
 template <int L>
@@ -177,12 +67,15 @@ __global__ void k_sweep_fused(Dev d) {
     const int lane = threadIdx.x & (L - 1);
     const int grp = tid / L;
     const int ngrp = (gridDim.x * blockDim.x) / L;
-    const unsigned mask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << ((threadIdx.x & 31) & ~(L - 1)));
+    const unsigned mask = lane_mask<L>();
     for (int it = 0; it < d.p.n_iter; ++it) {
         const float4* qi = (it & 1) ? d.qb : d.qa;
         float4* qo = (it & 1) ? d.qa : d.qb;
         const int last = it == d.p.n_iter - 1;
-        for (int b = grp; b < d.N; b += ngrp) body_update<L>(d, b, lane, mask, qi, qo, last);
+        for (int b = grp; b < d.N; b += ngrp)
+            solve_body<L>(d, b, lane, mask, qi, qo, last, [&](auto& s, const float* c, const float* A, int e0, int e1) {
+                gather_ends<L>(d, qi, b, c, A, e0, e1, lane, s);
+            });
         if (it + 1 < d.p.n_iter && !grid_sync(d.gbar, &d.ctr[C_STATUS])) return;
     }
 }

@@ -78,7 +78,8 @@ struct pabd_scene {
     cudaGraphExec_t prof_exec = nullptr;
     double prof_acc[PABD_PROFILE_SLOTS] = {0};
     // fused sweep launch shape
-    int fused = 0, lanes = 4, sw_block = 128, sw_grid = 1;
+    int fused = 0, lanes = 8, sw_block = 128, sw_grid = 1;
+    long long coop_fallbacks = 0;
 
     void* dalloc(size_t n) {
         if (n == 0) n = 16;
@@ -128,17 +129,29 @@ void enqueue_step(pabd_scene* s, long long* launches, const cudaEvent_t* ev = nu
     if (s->fused) {
         // events: [4] = the whole fused sweep, [5 .. 3 + 2 n_iter] unused (recorded together)
         cudaMemsetAsync(d.ctr + C_FP64DYN, 0, sizeof(int), s->st);
-        launch_fused_sweep(d, s->lanes, s->sw_block, s->sw_grid, s->st, launches);
-        for (int it = 0; it < d.p.n_iter; ++it) {
-            mark();
-            mark();
-            float4* t = cur; cur = nxt; nxt = t;
+        if (launch_fused_sweep(d, s->lanes, s->sw_block, s->sw_grid, s->st, launches) != cudaSuccess) {
+            // the cooperative launch was refused (e.g. co-residency not available): run the
+            // same sweeps as two launches each and count the fallback
+            cudaGetLastError();
+            s->coop_fallbacks++;
+            for (int it = 0; it < d.p.n_iter; ++it) {
+                launch_bond(d, cur, s->st, launches);
+                launch_solve(d, cur, nxt, it == d.p.n_iter - 1, s->lanes, s->st, launches);
+                float4* t = cur; cur = nxt; nxt = t;
+            }
+            for (int it = 0; it < 2 * d.p.n_iter; ++it) mark();
+        } else {
+            for (int it = 0; it < d.p.n_iter; ++it) {
+                mark();
+                mark();
+                float4* t = cur; cur = nxt; nxt = t;
+            }
         }
     } else {
         for (int it = 0; it < d.p.n_iter; ++it) {
             launch_bond(d, cur, s->st, launches);
             mark();
-            launch_solve(d, cur, nxt, it == d.p.n_iter - 1, s->st, launches);
+            launch_solve(d, cur, nxt, it == d.p.n_iter - 1, s->lanes, s->st, launches);
             mark();
             float4* t = cur; cur = nxt; nxt = t;
         }
@@ -373,7 +386,10 @@ pabd_status finalize_scene(pabd_scene* s) {
     CK(cudaMemcpyAsync(d.ctr + C_NBONDS, &nb0, sizeof(int), cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
 
-    // fused sweep: lanes per body from the descriptor, block / grid from a timing sweep
+    // lanes per body from the descriptor; fused sweep block / grid from a timing sweep
+    const int L = ds.sweep_lanes ? ds.sweep_lanes : 8;
+    if (L != 1 && L != 2 && L != 4 && L != 8 && L != 16) return PABD_ERR_ARG;
+    s->lanes = L;
     s->fused = (ds.sweep_mode == 0) && N > 0;
     if (s->fused) {
         int coop = 0, dev = 0;
@@ -382,20 +398,27 @@ pabd_status finalize_scene(pabd_scene* s) {
         if (!coop) s->fused = 0;
     }
     if (s->fused) {
-        const int L = ds.sweep_lanes ? ds.sweep_lanes : 4;
-        if (L != 1 && L != 2 && L != 4 && L != 8 && L != 16) return PABD_ERR_ARG;
         s->lanes = L;
         pabd_status tr = autotune_sweep(s);
         if (tr != PABD_OK) return tr;
     }
 
-    // capture one step as a graph
+    // capture one step as a graph (if the cooperative sweep cannot be captured, capture the
+    // two-launch sweep instead)
     long long lc = 0;
-    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    enqueue_step(s, &lc);
-    cudaError_t ce = cudaStreamEndCapture(st, &s->graph);
-    CK(ce);
-    CK(cudaGraphInstantiate(&s->exec, s->graph, 0));
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        lc = 0;
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        enqueue_step(s, &lc);
+        cudaError_t ce = cudaStreamEndCapture(st, &s->graph);
+        if (ce == cudaSuccess) ce = cudaGraphInstantiate(&s->exec, s->graph, 0);
+        if (ce == cudaSuccess) break;
+        cudaGetLastError();
+        if (s->graph) { cudaGraphDestroy(s->graph); s->graph = nullptr; }
+        if (!s->fused || attempt == 1) { cuda_ok(ce, "capture of the step graph"); return PABD_ERR_CUDA; }
+        s->fused = 0;
+        s->coop_fallbacks = 0;
+    }
     CK(cudaGraphGetNodes(s->graph, nullptr, &s->graph_nodes));
     s->launches_per_step = lc;
     CK(cudaMallocHost(&s->h_status, sizeof(int)));
@@ -803,6 +826,7 @@ pabd_status pabd_get_info(pabd_scene* s, pabd_info* info) {
     info->sweep_lanes = s->lanes;
     info->sweep_block = s->sw_block;
     info->sweep_grid = s->sw_grid;
+    info->coop_fallbacks = s->coop_fallbacks;
     return PABD_OK;
 }
 

@@ -91,7 +91,8 @@ void launch_collision(const Dev& d, cudaStream_t st, long long* launches);
 void launch_csr(const Dev& d, cudaStream_t st, long long* launches);
 void launch_predict(const Dev& d, cudaStream_t st, long long* launches);
 void launch_bond(const Dev& d, const float4* q, cudaStream_t st, long long* launches);
-void launch_solve(const Dev& d, const float4* q_in, float4* q_out, int last, cudaStream_t st, long long* launches);
+void launch_solve(const Dev& d, const float4* q_in, float4* q_out, int last, int lanes, cudaStream_t st,
+                  long long* launches);
 void launch_finalize(const Dev& d, const float4* q_fin, cudaStream_t st, long long* launches);
 void launch_drive_update(const Dev& d, cudaStream_t st, long long* launches);
 // fused persistent sweep (all n_iter iterations, cooperative launch); L lanes per body

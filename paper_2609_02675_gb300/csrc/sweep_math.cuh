@@ -20,48 +20,84 @@ __device__ __forceinline__ void world_pt(const float* c, const float* A, float4 
 
 // Split force of one bond from the iterate (Eq. 15-17): returns w = h^2 phi+(d)/d and the
 // delta-form record f' of end i (end j gets -f'), see the file comment of k_sweep.cu.
-__device__ __forceinline__ float bond_force(int type, float4 xi, float4 xj, float4 nm, const float* yi,
-                                            const float* yj, float* f) {
-    float w = xi.w;
+// T = float for the FP32 path; T = double for bodies on the FP64 path (the end points y
+// are then formed in double from the FP32 state, so no rounding of |y| enters f').
+template <class T>
+__device__ __forceinline__ T bond_force(int type, float4 xi, float4 xj, float4 nm, const T* yi, const T* yj, T* f) {
+    T w = (T)xi.w;
     if (type == K_CONTACT || type == K_GROUND) {
-        const float dhat = xj.w;
-        float rr[3] = {yi[0] - yj[0], yi[1] - yj[1], yi[2] - yj[2]};
-        float g = nm.x * rr[0] + nm.y * rr[1] + nm.z * rr[2];
+        const T dhat = (T)xj.w;
+        const T N[3] = {(T)nm.x, (T)nm.y, (T)nm.z};
+        T rr[3] = {yi[0] - yj[0], yi[1] - yj[1], yi[2] - yj[2]};
+        T g = N[0] * rr[0] + N[1] * rr[1] + N[2] * rr[2];
         if (g < dhat) {
-            float t[3] = {rr[0] - g * nm.x, rr[1] - g * nm.y, rr[2] - g * nm.z};
-            float tn = sqrtf(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
-            float tau = nm.w * (dhat - g);
-            float keep = tn > tau ? 1.f - tau / tn : 0.f;  // t - t_c = keep * t
-            const float N[3] = {nm.x, nm.y, nm.z};
+            T t[3] = {rr[0] - g * N[0], rr[1] - g * N[1], rr[2] - g * N[2]};
+            T tn = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+            T tau = (T)nm.w * (dhat - g);
+            T keep = tn > tau ? T(1) - tau / tn : T(0);  // t - t_c = keep * t
 #pragma unroll
             for (int k = 0; k < 3; ++k) f[k] = w * ((dhat * N[k] + keep * t[k]) - rr[k]);
         } else {
-            w = 0.f;
-            f[0] = f[1] = f[2] = 0.f;
+            w = T(0);
+            f[0] = f[1] = f[2] = T(0);
         }
         return w;
     }
-    float r[3] = {yj[0] - yi[0], yj[1] - yi[1], yj[2] - yi[2]};
+    T r[3] = {yj[0] - yi[0], yj[1] - yi[1], yj[2] - yi[2]};
     if (type == K_SPHERICAL || type == K_DRIVE) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) f[k] = w * r[k];
         return w;
     }
-    float dd = sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-    float n[3];
-    if (dd > 0.f) { float id = 1.f / dd; n[0] = r[0] * id; n[1] = r[1] * id; n[2] = r[2] * id; }
-    else { n[0] = 0.f; n[1] = 1.f; n[2] = 0.f; }
-    const float l = xj.w;
-    float s;
+    T dd = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    T n[3];
+    if (dd > T(0)) { T id = T(1) / dd; n[0] = r[0] * id; n[1] = r[1] * id; n[2] = r[2] * id; }
+    else { n[0] = T(0); n[1] = T(1); n[2] = T(0); }
+    const T l = (T)xj.w;
+    T sc;
     if (type == K_SPRING) {
-        s = w * (dd - l);                       // h^2 phi(d)
+        sc = w * (dd - l);                      // h^2 phi(d)
     } else {                                    // nonlinear elastic, tangent split
-        const float il2 = 1.f / (l * l);
-        s = (w * (1.f / 3.f)) * (dd * dd * dd * il2 - l);
+        const T il2 = T(1) / (l * l);
+        sc = (w * (T(1) / T(3))) * (dd * dd * dd * il2 - l);
         w = w * dd * dd * il2;
     }
 #pragma unroll
-    for (int k = 0; k < 3; ++k) f[k] = s * n[k];
+    for (int k = 0; k < 3; ++k) f[k] = sc * n[k];
+    return w;
+}
+
+template <class T>
+__device__ __forceinline__ void world_pt_t(const float* c, const float* A, float4 x, T* y) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        y[k] = (T)c[k] + (T)A[3 * k] * (T)x.x + (T)A[3 * k + 1] * (T)x.y + (T)A[3 * k + 2] * (T)x.z;
+}
+
+// Force of the bond seen from body `self`: loads the other body from q, forms both end
+// points in T, evaluates the split force; returns w and writes the record of self's end.
+template <class T>
+__device__ __forceinline__ T end_force(const float4* __restrict__ q, const float4* __restrict__ bn, int self,
+                                       const float* cs, const float* As, int4 m, float4 xa, float4 xb, T* f) {
+    const bool side_j = (m.y == self);
+    float c[3], A[9];
+    T yi[3], yj[3];
+    if (side_j) {
+        ld_q(q, m.x, c, A);
+        world_pt_t(c, A, xa, yi);
+        world_pt_t(cs, As, xb, yj);
+    } else {
+        world_pt_t(cs, As, xa, yi);
+        if (m.y >= 0) {
+            ld_q(q, m.y, c, A);
+            world_pt_t(c, A, xb, yj);
+        } else {
+            yj[0] = (T)xb.x; yj[1] = (T)xb.y; yj[2] = (T)xb.z;
+        }
+    }
+    const float4 nm = (m.z == K_CONTACT || m.z == K_GROUND) ? bn[m.w] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const T w = bond_force<T>(m.z, xa, xb, nm, yi, yj, f);
+    if (side_j) { f[0] = -f[0]; f[1] = -f[1]; f[2] = -f[2]; }
     return w;
 }
 
@@ -98,6 +134,23 @@ __device__ __forceinline__ void sys_add(Sys<T>& s, float4 e, float4 x) {
     s.g[7] += wz2 * z2; s.g[8] += wz2 * z3;
     s.g[9] += wz3 * z3;
     const T f[3] = {(T)e.y, (T)e.z, (T)e.w};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        s.r[0][k] += f[k];
+        s.r[1][k] += z1 * f[k];
+        s.r[2][k] += z2 * f[k];
+        s.r[3][k] += z3 * f[k];
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void sys_add_t(Sys<T>& s, T w, const T* f, float4 x) {
+    const T z1 = x.x, z2 = x.y, z3 = x.z;
+    const T wz1 = w * z1, wz2 = w * z2, wz3 = w * z3;
+    s.g[0] += w;   s.g[1] += wz1;      s.g[2] += wz2;      s.g[3] += wz3;
+    s.g[4] += wz1 * z1; s.g[5] += wz1 * z2; s.g[6] += wz1 * z3;
+    s.g[7] += wz2 * z2; s.g[8] += wz2 * z3;
+    s.g[9] += wz3 * z3;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         s.r[0][k] += f[k];
@@ -242,6 +295,111 @@ __device__ __forceinline__ void polar_rotation(float* X) {
         }
         if (diff < 1e-13f) break;
     }
+}
+
+template <class T>
+__device__ __forceinline__ void sys_zero(Sys<T>& s) {
+#pragma unroll
+    for (int k = 0; k < 10; ++k) s.g[k] = T(0);
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) s.r[r][k] = T(0);
+}
+
+// combine the L lanes' partial systems with a fixed xor butterfly (deterministic given L)
+template <int L, class T>
+__device__ __forceinline__ void sys_reduce(Sys<T>& s, unsigned mask) {
+#pragma unroll
+    for (int o = 1; o < L; o <<= 1) {
+#pragma unroll
+        for (int k = 0; k < 10; ++k) s.g[k] += __shfl_xor_sync(mask, s.g[k], o);
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) s.r[r][k] += __shfl_xor_sync(mask, s.r[r][k], o);
+    }
+}
+
+template <int L>
+__device__ __forceinline__ unsigned lane_mask() {
+    return (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << ((threadIdx.x & 31) & ~(L - 1)));
+}
+
+// Global + local solve of body b by L cooperating lanes (Eq. 19-24, Sec. 4.3):
+// G dX = M (s - q^k) + sum_ends [1; x] f'^T, X^{k+1/2} = q^k + dX, A^{k+1} = rotation of
+// A^{k+1/2}; lane 0 stores q^{k+1} and the body's squared update.  gather(sys, c, A, e0, e1)
+// adds this lane's share of the body's bond ends (FP32 first; FP64 for flagged bodies or
+// when a Cholesky pivot falls below 1e-4 of its diagonal).
+template <int L, class Gather>
+__device__ __forceinline__ void solve_body(const Dev& d, int b, int lane, unsigned mask,
+                                           const float4* __restrict__ qi, float4* __restrict__ qo, int last,
+                                           Gather&& gather) {
+    const int fl = d.bflags[b];
+    if (fl & BF_PINNED) {
+        if (lane == 0) {
+            qo[3 * b] = d.qn[3 * b]; qo[3 * b + 1] = d.qn[3 * b + 1]; qo[3 * b + 2] = d.qn[3 * b + 2];
+            d.resid_body[b] = 0.0;
+        }
+        return;
+    }
+    float c[3], A[9], sc[3], sA[9];
+    ld_q(qi, b, c, A);
+    ld_q(d.sq, b, sc, sA);
+    float dc[3], dA[9];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) dc[k] = sc[k] - c[k];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) dA[k] = sA[k] - A[k];
+    const float4 mass = d.mass[b];
+    const int e0 = d.end_off[b], e1 = d.end_off[b + 1];
+    float X[4][3];
+    bool use64 = d.p.precision_policy && (fl & BF_FP64);
+    if (!use64) {
+        Sys<float> s;
+        if (lane == 0) sys_init(s, mass, dc, dA);
+        else sys_zero(s);
+        gather(s, c, A, e0, e1);
+        sys_reduce<L>(s, mask);
+        const float ratio = sys_solve(s, X);
+        if (!(ratio >= 1e-4f) && d.p.precision_policy) {
+            use64 = true;
+            if (last && lane == 0) atomicAdd(&d.ctr[C_FP64DYN], 1);
+        }
+    }
+    if (use64) {
+        Sys<double> s;
+        if (lane == 0) sys_init(s, mass, dc, dA);
+        else sys_zero(s);
+        gather(s, c, A, e0, e1);
+        sys_reduce<L>(s, mask);
+        double Xd[4][3];
+        sys_solve(s, Xd);
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) X[r][k] = (float)Xd[r][k];
+    }
+    float cn[3], An[9];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        cn[k] = c[k] + X[0][k];
+#pragma unroll
+        for (int l = 0; l < 3; ++l) An[3 * k + l] = A[3 * k + l] + X[1 + l][k];
+    }
+    if (d.p.project) polar_rotation(An);
+    if (lane != 0) return;
+    double r2 = 0.0;
+    bool finite = true;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { double t = (double)cn[k] - (double)c[k]; r2 += t * t; finite &= isfinite(cn[k]); }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) { double t = (double)An[k] - (double)A[k]; r2 += t * t; finite &= isfinite(An[k]); }
+    if (!finite) atomicOr(&d.ctr[C_STATUS], ST_DIVERGED);
+    d.resid_body[b] = r2;
+    qo[3 * b] = make_float4(cn[0], cn[1], cn[2], An[0]);
+    qo[3 * b + 1] = make_float4(An[1], An[2], An[3], An[4]);
+    qo[3 * b + 2] = make_float4(An[5], An[6], An[7], An[8]);
 }
 
 }  // namespace pabd
