@@ -198,6 +198,35 @@ pabd_status pabd_get_info(pabd_scene* s, pabd_info* info);
 /* Release all device memory of the scene (synchronises its stream). */
 pabd_status pabd_destroy_scene(pabd_scene* s);
 
+/* Broad phase for callers that cannot allocate device memory.  Some callers must not
+ * call cudaMalloc: code running while a CUDA graph is being captured on its stream (an
+ * allocation there is illegal), real-time loops with a fixed memory budget, and hosts whose
+ * device memory is handed out by someone else.  This call allocates nothing: its scratch
+ * (hash buckets, per-body counts and offsets, the scan's block sums) is a static device
+ * array inside the library, sized for PABD_NOALLOC_MAX_BODIES bodies and held by every
+ * GPU that loads the library until the process exits.  The paper has no counterpart of
+ * this entry point; it returns the same sorted pair list as pabd_detect / pabd_read_pairs
+ * for a scene with these bodies and no user bonds.
+ *
+ * Inputs (device pointers, n_bodies rows each): q 12 floats per body (c, then A row-major),
+ * vel 4 floats per body (v, unused), he 4 floats per body (half extents, unused), group and
+ * flags one int32 per body (flags bit 0 = pinned; no other bit may be set).  h, margin and
+ * d_hat_rel are the scene parameters of pabd_scene_desc.  Outputs (device): pairs_out
+ * receives up to max_pairs (i, j) int32 pairs, i < j, sorted; *n_pairs_out the number of
+ * overlapping pairs found (more than max_pairs means the list was cut).
+ * Asynchronous on `stream` (NULL: the legacy default stream).  Returns PABD_ERR_ARG for
+ * null pointers, n_bodies < 0 or n_bodies > PABD_NOALLOC_MAX_BODIES.  The first call on a
+ * device looks up the device address of the static array (with that device current) and so
+ * should happen before any stream capture; later calls only enqueue memsets and kernels.
+ * Every call reuses the same array and keeps nothing from the previous call: it clears the
+ * buckets and counters it needs first.  Calls that overlap on the GPU (on different streams,
+ * or from several threads) race on that array and must be serialised by the caller. */
+#define PABD_NOALLOC_MAX_BODIES 16384
+pabd_status pabd_broadphase_noalloc(const float* q, const float* vel, const float* he, const int32_t* group,
+                                    const int32_t* flags, int32_t n_bodies, double h, double margin,
+                                    double d_hat_rel, int32_t* pairs_out, int32_t max_pairs,
+                                    int32_t* n_pairs_out, void* stream);
+
 const char* pabd_status_str(pabd_status st);
 
 /* Text of the last CUDA runtime error seen by the library in this thread. */

@@ -94,6 +94,8 @@ _SIGS = {
     "pabd_read_residual": [_P, _PD, ctypes.c_size_t],
     "pabd_get_info": [_P, ctypes.POINTER(pabd_info)],
     "pabd_destroy_scene": [_P],
+    "pabd_broadphase_noalloc": [_P, _P, _P, _P, _P, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_double, _P, ctypes.c_int32, _P, _P],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -224,6 +226,18 @@ def pabd_get_info(s) -> dict:
 
 def pabd_destroy_scene(s):
     return _check(_lib.pabd_destroy_scene(s), "pabd_destroy_scene")
+
+
+NOALLOC_MAX_BODIES = 16384
+
+
+def pabd_broadphase_noalloc(q: int, vel: int, he: int, group: int, flags: int, n_bodies: int, h: float,
+                            margin: float, d_hat_rel: float, pairs_out: int, max_pairs: int, n_pairs_out: int,
+                            stream: int = 0):
+    """Allocation-free broad phase on device pointers (see include/pabd.h)."""
+    return _check(_lib.pabd_broadphase_noalloc(q, vel, he, group, flags, n_bodies, h, margin, d_hat_rel,
+                                                pairs_out, max_pairs, n_pairs_out, stream or None),
+                  "pabd_broadphase_noalloc")
 
 
 # ---- torch plumbing: device memory and stream ----

@@ -458,6 +458,24 @@ __global__ void k_narrow_write(Dev d) {
 
 static inline int nblk(int n) { return (n + CT - 1) / CT > 0 ? (n + CT - 1) / CT : 1; }
 
+// The broad phase alone (bucket / counter resets, AABBs, grid, sorted pair list), on whatever
+// buffers `d` points at; used by the allocation-free entry point.
+void launch_broadphase(const Dev& d, cudaStream_t st, long long* launches) {
+    const int T = 1 << d.table_bits;
+    cudaMemsetAsync(d.bucket_cnt, 0, sizeof(int) * T, st);
+    cudaMemsetAsync(d.bucket_cur, 0, sizeof(int) * T, st);
+    cudaMemsetAsync(d.ctr, 0, sizeof(int) * C_COUNT, st);
+    k_aabb<<<nblk(d.N), CT, 0, st>>>(d);
+    k_cells<<<nblk(d.N), CT, 0, st>>>(d);
+    scan_exclusive(d.bucket_cnt, d.bucket_off, nullptr, T, d.scan_scratch, st, launches);
+    k_bucket_fill<<<nblk(d.N), CT, 0, st>>>(d);
+    const int wblk = (d.N * 32 + CT - 1) / CT > 0 ? (d.N * 32 + CT - 1) / CT : 1;
+    k_pair_count<<<wblk, CT, 0, st>>>(d);
+    scan_exclusive(d.pair_cnt, d.pair_off, nullptr, d.N, d.scan_scratch, st, launches);
+    k_pair_write<<<wblk, CT, 0, st>>>(d);
+    *launches += 5;
+}
+
 void launch_collision(const Dev& d, cudaStream_t st, long long* launches) {
     const int T = 1 << d.table_bits;
     cudaMemsetAsync(d.bucket_cnt, 0, sizeof(int) * T, st);

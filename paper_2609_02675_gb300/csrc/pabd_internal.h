@@ -88,6 +88,7 @@ void scan_exclusive(const int* in, int* out, const int* n_dev, int n_cap, int* s
 int scan_scratch_ints(int n_cap);
 
 void launch_collision(const Dev& d, cudaStream_t st, long long* launches);
+void launch_broadphase(const Dev& d, cudaStream_t st, long long* launches);
 void launch_csr(const Dev& d, cudaStream_t st, long long* launches);
 void launch_predict(const Dev& d, cudaStream_t st, long long* launches);
 void launch_bond(const Dev& d, const float4* q, cudaStream_t st, long long* launches);
