@@ -100,6 +100,10 @@ ARGS = None
 
 
 def workload():
+    if ARGS is not None and ARGS.workload == "trees":
+        return S.batched_trees()
+    if ARGS is not None and ARGS.workload == "quadruped":
+        return S.quadruped_bed_rod()
     n = ARGS.bodies if ARGS is not None else 4096
     if n == 4096 and not (ARGS is not None and ARGS.stacked):
         return S.box_pile()
@@ -108,6 +112,16 @@ def workload():
 
 def config_of(sc, K):
     start = ARGS.start_step if ARGS is not None else 0
+    if ARGS is not None and ARGS.workload in ("trees", "quadruped"):
+        if ARGS.workload == "trees":
+            desc = (f"{sc.n_groups} independent trees of 4-64 boxes ({sc.n_bodies} bodies), ground contact, "
+                    f"{sc.params['n_iter']} sweeps, h=1/120, one batched scene")
+        else:
+            desc = (f"driven 13-body quadruped on a bed of {sc.meta['n_bed']} cubes + {sc.meta['n_rod']}-segment "
+                    f"elastic rod ({sc.n_bodies} bodies), {sc.params['n_iter']} sweeps, h=1/60")
+        return {"workload": desc + f", steps {start}..{start + K - 1}", "n_bodies": sc.n_bodies,
+                "n_iter": sc.params["n_iter"], "l2": "flushed between timed steps (256 MB write)",
+                "parallelism": "replicas"}
     kind = "stacked columns" if (ARGS is not None and ARGS.stacked) else "jittered grid, spacing 3.5"
     return {"workload": f"box pile {sc.n_bodies} ({kind}), {sc.params['n_iter']} sweeps, "
                         f"h=1/60, steps {start}..{start + K - 1} of the trajectory",
@@ -138,6 +152,38 @@ def _ncu_traffic(kernel: str):
         return None
 
 
+def max_over_ranks(values, world: int, device=None):
+    """Element-wise max of per-rank timings (the slowest rank defines the job's time)."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_throughput(units_per_rank: float, world: int, t_max_ms: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return units_per_rank * world / (t_max_ms * 1e-3)
+
+
+def host_cpu() -> str:
+    """CPU model and logical core count of this host."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model", "hardware")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return f"{model} ({os.cpu_count()} logical cores)"
+
+
 def cpu_baseline(budget_s: float = 15.0, max_steps: int = 300):
     """The FP64 oracle (as it stands) on the same pile, steps 0..M-1 within the time budget."""
     import oracle as O
@@ -150,7 +196,8 @@ def cpu_baseline(budget_s: float = 15.0, max_steps: int = 300):
         m += 1
     dt = time.perf_counter() - t0
     return {"value": sc.n_bodies * sc.params["n_iter"] * m / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle steps 0..{m - 1} of the {sc.n_bodies}-box pile ({m} steps, {dt:.1f} s, single thread)"}
+            "sample": f"oracle steps 0..{m - 1} of the {sc.n_bodies}-box pile ({m} steps, {dt:.1f} s, single thread)",
+            "host": host_cpu()}
 
 
 def run_reference(args, rank, world):
@@ -171,7 +218,8 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_of(sc, args.steps),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"oracle steps 0..{args.steps - 1} of the pile, single thread"},
+                             "sample": f"oracle steps 0..{args.steps - 1} of the pile, single thread",
+                             "host": host_cpu()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -251,6 +299,35 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     t_plain = sum(a.elapsed_time(b) for a, b in evp)
 
+    # batched scenes: the same scenes each run alone on the plain path (a sample, eager launches)
+    alone = None
+    if args.workload == "trees":
+        sizes = sc.meta["sizes"]
+        off = np.concatenate([[0], np.cumsum(sizes)])
+        pick = np.linspace(0, len(sizes) - 1, 32).astype(int)
+        t_alone, body_iter = 0.0, 0
+        for gi in pick:
+            sl = slice(off[gi], off[gi + 1])
+            sub = S.Scene("one", dict(sc.params), sc.bodies[sl].copy(), sc.bonds.copy(), 1)
+            sub.bodies["group"] = 0
+            m = (sc.bonds["i"] >= off[gi]) & (sc.bonds["i"] < off[gi + 1])
+            sub.bonds = sc.bonds[m].copy()
+            sub.bonds["i"] -= off[gi]
+            sub.bonds["j"] = np.where(sub.bonds["j"] >= 0, sub.bonds["j"] - off[gi], -1)
+            one = P.Scene(sub, device=dev, stream=stream)
+            one.step_eager(2)
+            one.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            one.step_eager(min(K, 20))
+            e1.record(stream)
+            e1.synchronize()
+            t_alone += e0.elapsed_time(e1)
+            body_iter += int(sizes[gi]) * sc.params["n_iter"] * min(K, 20)
+            one.close()
+        alone = {"value": body_iter / (t_alone * 1e-3), "unit": UNIT,
+                 "sample": "32 of the scenes, each alone on the plain path (eager launches), 20 steps each"}
+
     # end to end through the C-ABI with host buffers: write state (H2D), step, read state (D2H)
     reset()
     rows = g.state()
@@ -266,47 +343,44 @@ def run_ours(args, rank, world, local_rank):
     t_e2e = time.perf_counter() - t0
 
     # max over ranks
-    vals = torch.tensor([t_ms, t_plain, t_e2e * 1e3], dtype=torch.float64, device=f"cuda:{dev}")
-    if world > 1:
-        torch.distributed.all_reduce(vals, op=torch.distributed.ReduceOp.MAX)
-    t_ms, t_plain, t_e2e_ms = vals.tolist()
+    t_ms, t_plain, t_e2e_ms = max_over_ranks([t_ms, t_plain, t_e2e * 1e3], world, f"cuda:{dev}")
     g.close()
     if rank != 0:
         return
     total_body_iter = n_body_iter * K * world
-    value = total_body_iter / (t_ms * 1e-3)
+    value = job_throughput(n_body_iter * K, world, t_ms)
 
-    # roofline of the dominant sweep kernel
+    # roofline of the sweep: per launch of the sweep kernel, algorithmic bytes / average
+    # duration (the sweep stage's events bracket all its launches of a step)
     steps = max(prof["steps"], 1)
     n_it = sc.params["n_iter"]
     bonds_avg = prof["bonds_sum"] / steps
     N = sc.n_bodies
-    fused = info1["sweep_mode"] == 0
-    if fused:
-        # one launch runs n_it sweeps; per sweep each body moves q in/out, s, mass, flags, CSR
-        # offset and residual (176 B) and each bond's two end records (2 x 48 B) plus, for a
-        # contact, its normal twice (2 x 16 B)
-        per_sweep = 176.0 * N + 128.0 * bonds_avg
-        per_kernel = {"k_sweep_fused": (n_it * per_sweep, prof["bond_ms"] / steps)}
+    mode = info1["sweep_mode"]
+    # per sweep: each body moves q in / out, s, mass, flags, CSR offsets and its residual
+    # (176 B); each bond its two CSR-ordered end records (2 x 48 B) and, for a contact, its
+    # normal twice (2 x 16 B); the two-launch mode also writes and re-reads the end records
+    per_sweep = 176.0 * N + 128.0 * bonds_avg
+    if mode == 3:
+        kernel, per_launch_bytes = "k_sweep_fused", n_it * per_sweep
+    elif mode == 2:
+        kernel, per_launch_bytes = "k_sweep_one", per_sweep
     else:
-        per_kernel = {
-            # bond = static bond records (64 B) + CSR slot pair (8 B) + two end records written
-            # (32 B) per bond + q read (48 B) per body; solve = q in/out, predictor, mass, flags,
-            # CSR offset, residual (176 B) per body + two end records and material points (64 B)
-            "k_bond": (104.0 * bonds_avg + 48.0 * N, prof["bond_ms"] / max(prof["bond_launches"], 1)),
-            "k_solve": (176.0 * N + 64.0 * bonds_avg, prof["solve_ms"] / max(prof["solve_launches"], 1)),
-        }
-    dom = max(per_kernel, key=lambda k: per_kernel[k][1])
-    bytes_launch, ms_launch = per_kernel[dom]
-    achieved = bytes_launch / (ms_launch * 1e-3) / 1e9
+        kernel, per_launch_bytes = "k_bond+k_solve", per_sweep + 64.0 * bonds_avg
+    launches_per_step = prof["sweep_launches"] / steps
+    ms_launch = prof["sweep_ms"] / max(prof["sweep_launches"], 1)
+    if mode == 1:
+        ms_launch *= 2.0  # one bond + one solve launch per sweep
+    achieved = per_launch_bytes / (ms_launch * 1e-3) / 1e9
     peak, peak_kind = _peaks()
-    tr = _ncu_traffic(dom)
-    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+    tr = _ncu_traffic(kernel)
+    roof = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
             "traffic": tr["bytes_per_launch"] if tr else None,
-            "bytes_per_launch": bytes_launch, "us_per_launch": ms_launch * 1e3, "bonds_per_step": bonds_avg,
-            "stage_ms_per_step": {k: prof[k] / steps for k in ("collision_ms", "csr_ms", "predict_ms", "bond_ms",
-                                                                 "solve_ms", "finalize_ms", "step_ms")}}
+            "bytes_per_launch": per_launch_bytes, "us_per_launch": ms_launch * 1e3, "bonds_per_step": bonds_avg,
+            "launches_per_step": launches_per_step,
+            "stage_ms_per_step": {k: prof[k] / steps for k in ("collision_ms", "csr_ms", "predict_ms", "sweep_ms",
+                                                                 "finalize_ms", "step_ms")}}
     cfg = config_of(sc, K)
     cfg["sweep"] = {k: info1[k] for k in ("sweep_mode", "sweep_lanes", "sweep_block", "sweep_grid")}
     line = {
@@ -314,15 +388,60 @@ def run_ours(args, rank, world, local_rank):
         "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic", "config": cfg,
         "steps_per_s": world * K / (t_ms * 1e-3),
-        "plain_path": {"value": total_body_iter / (t_plain * 1e-3), "unit": UNIT, "ms_per_step": t_plain / K},
-        "e2e": {"value": total_body_iter / (t_e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "plain_path": {"value": job_throughput(n_body_iter * K, world, t_plain), "unit": UNIT, "ms_per_step": t_plain / K},
+        "e2e": {"value": job_throughput(n_body_iter * K, world, t_e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
+        **({"scenes_alone_plain_path": alone} if alone else {}),
         "clocks": clk.summary(),
         "roofline": roof,
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+
+
+def run_served(args, dev):
+    """Poisson stream of step requests over resident pile scenes of 10 to 1e5 bodies (one
+    line per rate), against each scene's step alone on the plain path."""
+    import torch
+    import paper_2609_02675_gb300 as P
+    from paper_2609_02675_gb300.serve import Server, replay
+    torch.cuda.set_device(dev)
+
+    def make(n):
+        return S.box_pile_n(int(n), seed=S.SEED_BASE + 5, stacked=True, n_iter=30)
+
+    out = []
+    for rate in [float(x) for x in args.rates.split(",")]:
+        reqs, sizes = S.request_stream(rate=rate, duration=args.duration, max_scenes=64)
+        srv = Server(lambda sid: make(sizes[sid]), hbm_budget=32 << 30, device=dev)
+        t0, t1 = replay(srv, reqs, duration=args.duration, drain_timeout=20.0)
+        st = srv.stats(t0, t1)
+        # plain path: each distinct scene size stepped alone (sampled), mean step time
+        pick = sorted(set(sizes))[:: max(1, len(set(sizes)) // 8)]
+        alone_ms = []
+        for n in pick:
+            g = P.Scene(make(n), device=dev)
+            g.step_eager(1)
+            g.sync()
+            t = time.perf_counter()
+            g.step_eager(3)
+            g.sync()
+            alone_ms.append((time.perf_counter() - t) / 3 * 1e3)
+            g.close()
+        srv.close()
+        st.update({"rate": rate, "scenes": len(sizes), "plain_path_step_ms_mean": float(np.mean(alone_ms)),
+                   "plain_path_sizes": [int(n) for n in pick]})
+        out.append(st)
+        torch.cuda.empty_cache()
+    line = {"metric": "served step latency", "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+            "data": "synthetic", "dtype": "f32",
+            "config": {"workload": f"Poisson step requests (1-60 steps) over at most 64 pile scenes of 10-1e5 "
+                                   f"bodies, {args.duration:.0f} s of arrivals per rate (then up to 20 s to drain), "
+                                   f"HBM budget 32 GB",
+                       "parallelism": "one scene per stream, continuous batching"},
+            "rates": out}
     print(json.dumps(line), flush=True)
 
 
@@ -333,10 +452,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="pile", choices=["pile", "trees", "quadruped", "served"])
+    ap.add_argument("--rates", default="100,300,1000,3000,10000", help="served: request rates (req/s)")
+    ap.add_argument("--duration", type=float, default=3.0, help="served: seconds of arrivals per rate")
     ap.add_argument("--bodies", type=int, default=4096, help="pile size (4096 = the 16^3 pile)")
     ap.add_argument("--stacked", action="store_true", help="pile as touching columns (contacts from step 0)")
     ap.add_argument("--start-step", type=int, default=0, help="untimed lead-in steps before the timed window")
-    ap.add_argument("--sweep-mode", type=int, default=0, help="0: fused persistent sweep, 1: two launches per sweep")
+    ap.add_argument("--sweep-mode", type=int, default=0,
+                    help="1: two launches per sweep, 2: one launch per sweep, 3: fused persistent, 0: library choice")
     ap.add_argument("--lanes", type=int, default=0, help="lanes per body in the fused sweep (0: library default)")
     args = ap.parse_args()
     global ARGS
@@ -346,6 +469,10 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "served":
+        if rank == 0:
+            run_served(args, local_rank)
         return
     if world > 1:
         import torch

@@ -57,6 +57,12 @@ typedef enum {
  *               point pivot_i + arm * Rot(axis, theta(t)) r_i, theta(t) = drive_amp *
  *               sin(2 pi t / drive_period + drive_phase), t the end time of the step;
  *               r_i is a fixed unit vector orthogonal to the axis.
+ *   AL_DISTANCE augmented Lagrangian distance constraint (Eq. 27-29): Psi = kappa C^2/2 +
+ *               lambda C, C = d - rest_len; phi+ = kappa d + max(lambda - kappa l, 0),
+ *               phi- = min(lambda - kappa l, 0).  After every sweep, from the new iterate:
+ *               lambda <- kappa C + lambda, kappa <- kappa + al_beta |C|; at the start of every
+ *               step kappa <- max(al_gamma kappa, kappa_start), lambda <- al_alpha al_gamma
+ *               lambda.  `kappa` is kappa_start; kappa starts there and lambda at 0.
  * Directions given in body_i's frame are carried into body_j's frame through the bodies'
  * orientations at the time the bond is added. */
 typedef enum {
@@ -64,7 +70,8 @@ typedef enum {
     PABD_SPRING = 1,
     PABD_ELASTIC_NL = 2,
     PABD_REVOLUTE = 3,
-    PABD_DRIVE = 4
+    PABD_DRIVE = 4,
+    PABD_AL_DISTANCE = 5
 } pabd_bond_type;
 
 typedef struct pabd_scene pabd_scene; /* opaque, owned by the library */
@@ -86,13 +93,16 @@ typedef struct {
     int body_contacts;        /* 0: only ground contacts */
     double large_he;          /* bodies with a half extent above this skip the grid */
     int precision_policy;     /* 0: FP32 solves; 1: FP64 per-body solve where ill-conditioned */
-    int sweep_mode;           /* 0: fused persistent sweep (one cooperative launch runs all
-                                 n_iter iterations); 1: a bond launch + a solve launch per sweep */
+    int sweep_mode;           /* 1: a bond launch + a solve launch per sweep; 2: one launch per
+                                 sweep (the solve evaluates its bonds); 3: one cooperative launch
+                                 runs all n_iter sweeps; 0: the library's choice (2).  All modes
+                                 give the same results for the same sweep_lanes */
     int sweep_lanes;          /* lanes per body in the per-body solve: 1, 2, 4, 8 or 16; 0 = 8.
                                  Fixes the summation order (results depend on it, not on the
                                  block / grid sizes, which the library autotunes) */
-    size_t max_pairs;         /* capacities; 0 = 16 per body */
-    size_t max_contacts;      /* 0 = 24 per body */
+    size_t max_pairs;         /* capacities: at most 16 M pairs, 0 = 16 per body (clamped to 16 M) */
+    size_t max_contacts;      /* at most 60 M, 0 = 32 per body (clamped to 60 M); at most 8 M bodies.
+                                 Exceeding one in a step latches PABD_ERR_CAPACITY. */
     void* stream;             /* cudaStream_t on which all work is enqueued (NULL: default) */
     /* optional device allocator (e.g. a framework's caching allocator); NULL: cudaMalloc */
     void* (*alloc)(size_t bytes, void* ctx);
@@ -120,6 +130,7 @@ typedef struct {
     double axis[3];           /* REVOLUTE / DRIVE axis in body_i's frame */
     double kappa, rest_len, arm;
     double drive_amp, drive_period, drive_phase;
+    double al_beta, al_alpha, al_gamma;  /* AL_DISTANCE parameters */
 } pabd_bond_desc;
 
 /* State rows exchanged with the host: 22 doubles per body,
@@ -134,7 +145,8 @@ typedef struct {
     int64_t launches;         /* kernels launched by this scene so far */
     int64_t fp64_bodies;      /* bodies whose solve is statically flagged for FP64 */
     int64_t device_bytes;     /* device memory held by the scene */
-    int64_t sweep_mode, sweep_lanes, sweep_block, sweep_grid;  /* fused sweep launch shape */
+    int64_t sweep_mode, sweep_lanes, sweep_block, sweep_grid;  /* sweep mode (1, 2, 3) and the
+                                 fused sweep's launch shape */
     int64_t coop_fallbacks;   /* steps whose cooperative sweep launch was refused and ran as
                                  two launches per sweep instead */
 } pabd_info;
@@ -149,6 +161,13 @@ pabd_status pabd_add_body(pabd_scene* s, const pabd_body_desc* b, uint32_t* out_
  * ids it expands to; *n_out (may be NULL) their number (REVOLUTE: 2, others: 1). */
 pabd_status pabd_add_bond(pabd_scene* s, const pabd_bond_desc* b, uint32_t* out_ids, int* n_out);
 
+/* Bulk forms of pabd_add_body / pabd_add_bond for n descriptors in an array; out_ids (may be
+ * NULL) receives the n body ids, or the internal bond ids (2 per REVOLUTE) up to out_cap.
+ * Stops at the first invalid descriptor and returns its error; *n_done (may be NULL) is the
+ * number of descriptors added before it. */
+pabd_status pabd_add_bodies(pabd_scene* s, const pabd_body_desc* b, size_t n, uint32_t* out_ids, size_t* n_done);
+pabd_status pabd_add_bonds(pabd_scene* s, const pabd_bond_desc* b, size_t n, size_t* n_done);
+
 /* Advance nsteps time steps (asynchronous on desc.stream; one CUDA graph launch each). */
 pabd_status pabd_step(pabd_scene* s, int nsteps);
 
@@ -156,11 +175,12 @@ pabd_status pabd_step(pabd_scene* s, int nsteps);
 pabd_status pabd_step_eager(pabd_scene* s, int nsteps);
 
 /* Stage timing.  With profiling on, pabd_step launches a second captured graph that also
- * records CUDA events between the stages, waits for each step and accumulates the times
- * (milliseconds) read back by pabd_read_profile into PABD_PROFILE_SLOTS doubles:
+ * records CUDA events at the stage boundaries, waits for each step and accumulates the
+ * times (milliseconds) read back by pabd_read_profile into PABD_PROFILE_SLOTS doubles:
  *   [0] steps, [1] drives + collision detection, [2] CSR build, [3] predictor,
- *   [4] bond kernels, [5] solve kernels, [6] finalize + residual, [7] bond launches,
- *   [8] solve launches, [9] whole steps, [10] sum over steps of the bond count.
+ *   [4] all sweeps (bond + solve of every iteration), [5] unused (0), [6] finalize +
+ *   residual, [7] sweep-kernel launches, [8] sweeps, [9] whole steps, [10] sum over steps
+ *   of the bond count.
  * reset != 0 clears the accumulators after reading. */
 #define PABD_PROFILE_SLOTS 11
 pabd_status pabd_set_profiling(pabd_scene* s, int on);
@@ -180,6 +200,15 @@ pabd_status pabd_write_state(pabd_scene* s, const double* host_rows, size_t n_bo
 /* Set the index n of the next step (its end time is (n + 1) h, used by DRIVE bonds);
  * ordered on the stream like a state write. */
 pabd_status pabd_set_step_index(pabd_scene* s, int64_t step_index);
+
+/* Augmented Lagrangian state of the static bonds (internal ids, as pabd_add_bond returns
+ * them; n_bonds must equal pabd_info.n_static_bonds, else PABD_ERR_ARG): (kappa, lambda) per
+ * bond, 2 doubles each, zeros for other bond types -- the values the last step ended with,
+ * which the next step warm-starts from (Eq. 29).  Held on the device in FP32.  Both calls
+ * finalize the scene if needed and synchronise its stream; a write ignores the entries of
+ * other bond types and rejects non-finite values (PABD_ERR_ARG, nothing written). */
+pabd_status pabd_read_bond_state(pabd_scene* s, double* host_out, size_t n_bonds);
+pabd_status pabd_write_bond_state(pabd_scene* s, const double* host_in, size_t n_bonds);
 
 /* Broad-phase pairs of the last detection: *n receives the count; up to cap (i, j)
  * int32 pairs (i < j, sorted) are written to host_pairs. */

@@ -75,6 +75,10 @@ def lib():
         L.po_cholesky_solve.argtypes = [ctypes.c_int, D, D, D]
         L.po_cholesky_solve.restype = ctypes.c_int
         L.po_contact_rule.argtypes = [D, ctypes.c_double, ctypes.c_double, ctypes.c_double, D, D, D, D, D]
+        L.po_get_al_state.argtypes = [P, D]
+        L.po_get_activation_margin.argtypes = [P, D]
+        L.po_set_activation_shift.argtypes = [P, ctypes.c_double]
+        L.po_set_al_state.argtypes = [P, D]
         _lib = L
     return _lib
 
@@ -109,8 +113,8 @@ class OracleScene:
             self.L.po_add_body(self.h, _dp(row))
         for bo in scene.bonds:
             row = np.array([bo["type"], bo["i"], bo["j"], *bo["xi"], *bo["xj"], *bo["axis"],
-                            bo["kappa"], bo["rest"], bo["arm"], bo["amp"], bo["period"], bo["phase"]],
-                           dtype=np.float64)
+                            bo["kappa"], bo["rest"], bo["arm"], bo["amp"], bo["period"], bo["phase"],
+                            bo["beta"], bo["alpha"], bo["gamma"]], dtype=np.float64)
             if self.L.po_add_bond(self.h, _dp(row)) < 0:
                 raise ValueError("oracle rejected bond")
         self.n = scene.n_bodies
@@ -162,6 +166,27 @@ class OracleScene:
         out = np.zeros(max(n, 1))
         self.L.po_get_residual(self.h, _dp(out), n)
         return out[:n]
+
+    def al_state(self) -> np.ndarray:
+        """(kappa, lambda) of every static bond after expansion (zeros for non-AL bonds)."""
+        n = self.L.po_n_static_bonds(self.h)
+        out = np.zeros((max(n, 1), 2))
+        self.L.po_get_al_state(self.h, _dp(out))
+        return out[:n]
+
+    def activation_margin(self) -> np.ndarray:
+        """Per body, min over the last step's sweeps of |g - dhat| over its contacts (inf if none)."""
+        out = np.zeros(max(self.n, 1))
+        self.L.po_get_activation_margin(self.h, _dp(out))
+        return out[:self.n]
+
+    def set_activation_shift(self, shift: float):
+        """Test probe: contacts switch on at g < dhat + shift in the following steps (0 = the method)."""
+        self.L.po_set_activation_shift(self.h, float(shift))
+
+    def set_al_state(self, st: np.ndarray):
+        st = np.ascontiguousarray(st, dtype=np.float64)
+        self.L.po_set_al_state(self.h, _dp(st))
 
     def body_system(self, body: int):
         H = np.zeros((12, 12))

@@ -35,7 +35,7 @@
 #define PO_WORLD (-1)
 
 enum { PO_SPHERICAL = 0, PO_SPRING = 1, PO_ELASTIC_NL = 2, PO_REVOLUTE = 3, PO_DRIVE = 4,
-       PO_CONTACT = 5, PO_GROUND = 6 };
+       PO_CONTACT = 5, PO_GROUND = 6, PO_AL = 7 };
 
 typedef struct {
     double he[3];
@@ -56,6 +56,8 @@ typedef struct {
     double ui[3], ri[3], arm, amp, period, phase;
     /* contact */
     double N[3], dhat, w, mu;
+    /* augmented Lagrangian distance bond (Eq. 27-29): stiffness and multiplier, parameters */
+    double al_k, al_lam, al_kstart, al_beta, al_alpha, al_gamma;
 } po_bond;
 
 typedef struct {
@@ -82,6 +84,8 @@ typedef struct {
     int64_t step;
     int n_groups;
     double* resid;          /* per group, last iteration of the last step */
+    double* amargin;        /* per body: min over the last step's sweeps of |g - dhat| of its contacts */
+    double act_shift;       /* test probe of the contact activation threshold, 0 in the method */
     /* adjacency of static bonds (pairs excluded from contact) */
     int n_excl, cap_excl;
     int* excl;              /* sorted (min, max) pairs */
@@ -307,7 +311,7 @@ void* po_create(const double* pr) {
 void po_destroy(void* h) {
     po_scene* s = (po_scene*)h;
     if (!s) return;
-    free(s->bs); free(s->st); free(s->cb); free(s->kb); free(s->pairs); free(s->resid); free(s->excl);
+    free(s->bs); free(s->st); free(s->cb); free(s->kb); free(s->pairs); free(s->resid); free(s->amargin); free(s->excl);
     free(s);
 }
 
@@ -382,6 +386,7 @@ static void carry_dir(const po_scene* s, int i, int j, const double* di, double*
 }
 
 /* bond: type, i, j, xi[3], xj[3], axis[3], kappa, rest, arm, amp, period, phase
+   [, beta, alpha, gamma for the augmented Lagrangian distance bond, user type 5]
    Returns the number of internal bonds created (REVOLUTE expands to two). */
 int po_add_bond(void* h, const double* d) {
     po_scene* s = (po_scene*)h;
@@ -396,6 +401,14 @@ int po_add_bond(void* h, const double* d) {
     if (type == PO_SPHERICAL || type == PO_SPRING || type == PO_ELASTIC_NL) {
         b.type = type;
         memcpy(b.xi, xi, sizeof xi); memcpy(b.xj, xj, sizeof xj);
+        push_static(s, &b);
+        return 1;
+    }
+    if (type == 5) {  /* augmented Lagrangian distance bond: kappa = kappa_start */
+        b.type = PO_AL;
+        memcpy(b.xi, xi, sizeof xi); memcpy(b.xj, xj, sizeof xj);
+        b.al_kstart = kappa; b.al_beta = d[18]; b.al_alpha = d[19]; b.al_gamma = d[20];
+        b.al_k = kappa; b.al_lam = 0.0;
         push_static(s, &b);
         return 1;
     }
@@ -675,12 +688,15 @@ void po_detect(void* h) {
 /* Contact + Coulomb friction bond rule (reading) for end points yi (body i) and yj (body j
    or the world anchor), frozen normal N, contact distance dhat, weight w = h^2 kappa_c and
    friction coefficient mu. Writes w (0 when inactive) and the two ends' f. */
-void po_contact_rule(const double* N, double dhat, double w, double mu, const double* yi,
-                     const double* yj, double* wout, double* fi, double* fj) {
+/* `shift` moves only the activation threshold (active iff g < dhat + shift); it is 0 in the
+   method and set only by tests that probe how a step depends on a contact sitting at the
+   threshold (a decision the single-precision path may take the other way). */
+static void contact_rule_at(const double* N, double dhat, double shift, double w, double mu, const double* yi,
+                            const double* yj, double* wout, double* fi, double* fj) {
     double rr[3], t[3];
     for (int k = 0; k < 3; ++k) rr[k] = yi[k] - yj[k];
     double g = dot3(N, rr);
-    if (!(g < dhat)) {
+    if (!(g < dhat + shift)) {
         *wout = 0;
         memset(fi, 0, 3 * sizeof(double));
         memset(fj, 0, 3 * sizeof(double));
@@ -695,6 +711,11 @@ void po_contact_rule(const double* N, double dhat, double w, double mu, const do
         fi[k] = w * (yj[k] + rs);
         fj[k] = w * (yi[k] - rs);
     }
+}
+
+void po_contact_rule(const double* N, double dhat, double w, double mu, const double* yi,
+                     const double* yj, double* wout, double* fi, double* fj) {
+    contact_rule_at(N, dhat, 0.0, w, mu, yi, yj, wout, fi, fj);
 }
 
 /* Evaluate bond b from the iterate q (12 per body).  Outputs for end i (wi, fi) and end j
@@ -728,7 +749,7 @@ static void eval_bond(const po_scene* s, const po_bond* b, const double* q, doub
     else world_point(q + 12 * b->j, b->xj, yj);
 
     if (b->type == PO_CONTACT || b->type == PO_GROUND) {
-        po_contact_rule(b->N, b->dhat, b->w, b->mu, yi, yj, wi, fi, fj);
+        contact_rule_at(b->N, b->dhat, s->act_shift, b->w, b->mu, yi, yj, wi, fi, fj);
         *wj = *wi;
         return;
     }
@@ -741,6 +762,15 @@ static void eval_bond(const po_scene* s, const po_bond* b, const double* q, doub
     switch (b->type) {
         case PO_SPRING:
             w = h2 * b->kappa; phim = -b->kappa * b->rest; break;
+        case PO_AL: {
+            /* phi = kappa C + lambda, C = d - l (Eq. 27): phi+ = kappa d + max(lambda - kappa l, 0),
+               phi- = min(lambda - kappa l, 0); d clamped away from 0 for the implicit part */
+            double cst = b->al_lam - b->al_k * b->rest;
+            double dd = d > 1e-9 ? d : 1e-9;
+            w = h2 * (b->al_k + (cst > 0 ? cst / dd : 0.0));
+            phim = cst < 0 ? cst : 0.0;
+            break;
+        }
         case PO_ELASTIC_NL:
             /* tangent split of phi(d) = (kappa/3)(d^3/l^2 - l): phi+ = phi'(d) d = kappa d^3/l^2,
                phi- = phi(d) - phi'(d) d = -(2 kappa d^3)/(3 l^2) - kappa l/3 <= 0 */
@@ -788,9 +818,36 @@ static void mass_terms(const po_scene* s, int bi, const double* sq, double* H, d
     }
 }
 
+/* Augmented Lagrangian update of one bond after a sweep (Eq. 28), from the constraint of
+   the new iterate q^{k+1} (the primal result of that sweep): lambda <- kappa C + lambda,
+   kappa <- kappa + beta |C|, C = d - l, lambda taking the old kappa. */
+static void al_update(po_bond* b, const double* q) {
+    double yi[3], yj[3];
+    world_point(q + 12 * b->i, b->xi, yi);
+    if (b->j == PO_WORLD) memcpy(yj, b->xj, sizeof yj);
+    else world_point(q + 12 * b->j, b->xj, yj);
+    double r[3] = {yj[0] - yi[0], yj[1] - yi[1], yj[2] - yi[2]};
+    double c = norm3(r) - b->rest;
+    b->al_lam = b->al_k * c + b->al_lam;
+    b->al_k = b->al_k + b->al_beta * fabs(c);
+}
+
 /* Assemble every dynamic body's H and rhs for the iterate q and predictor sq. */
+/* Diagnostic, not part of the step: distance |g - dhat| of a contact from its activation
+   threshold at iterate q, folded into the per-body minimum `margin`. */
+static void note_margin(const po_bond* b, const double* q, double* margin) {
+    double yi[3], yj[3];
+    world_point(q + 12 * b->i, b->xi, yi);
+    if (b->j == PO_WORLD) memcpy(yj, b->xj, sizeof yj);
+    else world_point(q + 12 * b->j, b->xj, yj);
+    double rr[3] = {yi[0] - yj[0], yi[1] - yj[1], yi[2] - yj[2]};
+    double m = fabs(dot3(b->N, rr) - b->dhat);
+    if (m < margin[b->i]) margin[b->i] = m;
+    if (b->j != PO_WORLD && m < margin[b->j]) margin[b->j] = m;
+}
+
 static void assemble_all(const po_scene* s, const double* q, const double* sq, double t_next,
-                         double* H, double* rhs) {
+                         double* H, double* rhs, double* margin) {
     for (int b = 0; b < s->nb; ++b) mass_terms(s, b, sq + 12 * b, H + 144 * b, rhs + 12 * b);
     for (int pass = 0; pass < 2; ++pass) {
         int n = pass ? s->nk : s->nc;
@@ -798,6 +855,7 @@ static void assemble_all(const po_scene* s, const double* q, const double* sq, d
         for (int e = 0; e < n; ++e) {
             const po_bond* b = &arr[e];
             double wi, wj, fi[3], fj[3];
+            if (margin && (b->type == PO_CONTACT || b->type == PO_GROUND)) note_margin(b, q, margin);
             eval_bond(s, b, q, t_next, &wi, fi, &wj, fj);
             double xi[3];
             bond_xi(b, t_next, xi);
@@ -850,9 +908,20 @@ static int step_once(po_scene* s) {
     }
     memcpy(q, sq, sizeof(double) * 12 * nb);
     double t_next = (double)(s->step + 1) * h;
+    /* augmented Lagrangian warm start (Eq. 29): kappa^0 = max(gamma kappa^n, kappa_start),
+       lambda^0 = alpha gamma lambda^n */
+    for (int e = 0; e < s->nc; ++e) {
+        po_bond* b = &s->cb[e];
+        if (b->type != PO_AL) continue;
+        double k = b->al_gamma * b->al_k;
+        b->al_k = k > b->al_kstart ? k : b->al_kstart;
+        b->al_lam = b->al_alpha * b->al_gamma * b->al_lam;
+    }
     if (!s->resid) s->resid = (double*)calloc((size_t)(s->n_groups > 0 ? s->n_groups : 1), sizeof(double));
+    if (!s->amargin) s->amargin = (double*)calloc((size_t)(nb > 0 ? nb : 1), sizeof(double));
+    for (int b = 0; b < nb; ++b) s->amargin[b] = INFINITY;
     for (int it = 0; it < s->p.n_iter; ++it) {
-        assemble_all(s, q, sq, t_next, H, rhs);                  /* Jacobi: all read q^k */
+        assemble_all(s, q, sq, t_next, H, rhs, s->amargin);      /* Jacobi: all read q^k */
         for (int g = 0; g < s->n_groups; ++g) s->resid[g] = 0;
         for (int b = 0; b < nb; ++b) {
             double* out = q1 + 12 * b;
@@ -868,6 +937,8 @@ static int step_once(po_scene* s) {
             s->resid[s->bs[b].group] += r2;
         }
         memcpy(q, q1, sizeof(double) * 12 * nb);
+        for (int e = 0; e < s->nc; ++e)
+            if (s->cb[e].type == PO_AL) al_update(&s->cb[e], q);
     }
     for (int g = 0; g < s->n_groups; ++g) s->resid[g] = sqrt(s->resid[g]);
     /* velocity recovery */
@@ -985,10 +1056,35 @@ void po_body_system(void* h, int body, double* H, double* rhs) {
     double* HH = (double*)malloc(sizeof(double) * 144 * nb);
     double* rr = (double*)malloc(sizeof(double) * 12 * nb);
     for (int b = 0; b < nb; ++b) state_to_q(&s->st[b], q + 12 * b);
-    assemble_all(s, q, q, (double)(s->step + 1) * s->p.h, HH, rr);
+    assemble_all(s, q, q, (double)(s->step + 1) * s->p.h, HH, rr, NULL);
     memcpy(H, HH + 144 * body, 144 * sizeof(double));
     memcpy(rhs, rr + 12 * body, 12 * sizeof(double));
     free(q); free(HH); free(rr);
+}
+
+/* Test probe: contacts of the following steps switch on at g < dhat + shift (0 restores the method). */
+void po_set_activation_shift(void* h, double shift) { ((po_scene*)h)->act_shift = shift; }
+
+/* Per body, the smallest |g - dhat| of its contacts over the sweeps of the last step
+   (infinity for a body without contacts): how close a contact came to switching on or off. */
+void po_get_activation_margin(void* h, double* out) {
+    po_scene* s = (po_scene*)h;
+    for (int b = 0; b < s->nb; ++b) out[b] = s->amargin ? s->amargin[b] : INFINITY;
+}
+
+/* Augmented Lagrangian state (kappa, lambda) of every static bond (0, 0 for other types). */
+void po_get_al_state(void* h, double* out) {
+    po_scene* s = (po_scene*)h;
+    for (int e = 0; e < s->nc; ++e) {
+        out[2 * e] = s->cb[e].type == PO_AL ? s->cb[e].al_k : 0.0;
+        out[2 * e + 1] = s->cb[e].type == PO_AL ? s->cb[e].al_lam : 0.0;
+    }
+}
+
+void po_set_al_state(void* h, const double* in) {
+    po_scene* s = (po_scene*)h;
+    for (int e = 0; e < s->nc; ++e)
+        if (s->cb[e].type == PO_AL) { s->cb[e].al_k = in[2 * e]; s->cb[e].al_lam = in[2 * e + 1]; }
 }
 
 /* Static internal bonds after expansion: type, i, j, xi(3), xj(3) (drive: xj child point) */

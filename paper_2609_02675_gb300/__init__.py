@@ -58,7 +58,8 @@ class pabd_bond_desc(ctypes.Structure):
         ("type", ctypes.c_int), ("body_i", ctypes.c_uint32), ("body_j", ctypes.c_uint32),
         ("x_i", D3), ("x_j", D3), ("axis", D3), ("kappa", ctypes.c_double), ("rest_len", ctypes.c_double),
         ("arm", ctypes.c_double), ("drive_amp", ctypes.c_double), ("drive_period", ctypes.c_double),
-        ("drive_phase", ctypes.c_double),
+        ("drive_phase", ctypes.c_double), ("al_beta", ctypes.c_double), ("al_alpha", ctypes.c_double),
+        ("al_gamma", ctypes.c_double),
     ]
 
 
@@ -80,12 +81,16 @@ _SIGS = {
     "pabd_create_scene": [ctypes.POINTER(pabd_scene_desc), ctypes.POINTER(_P)],
     "pabd_add_body": [_P, ctypes.POINTER(pabd_body_desc), _PU32],
     "pabd_add_bond": [_P, ctypes.POINTER(pabd_bond_desc), _PU32, ctypes.POINTER(ctypes.c_int)],
+    "pabd_add_bodies": [_P, _P, ctypes.c_size_t, _PU32, _PSZ],
+    "pabd_add_bonds": [_P, _P, ctypes.c_size_t, _PSZ],
     "pabd_step": [_P, ctypes.c_int],
     "pabd_step_eager": [_P, ctypes.c_int],
     "pabd_detect": [_P],
     "pabd_sync": [_P],
     "pabd_read_state": [_P, _PD, ctypes.c_size_t],
     "pabd_write_state": [_P, _PD, ctypes.c_size_t],
+    "pabd_read_bond_state": [_P, _PD, ctypes.c_size_t],
+    "pabd_write_bond_state": [_P, _PD, ctypes.c_size_t],
     "pabd_set_step_index": [_P, ctypes.c_int64],
     "pabd_set_profiling": [_P, ctypes.c_int],
     "pabd_read_profile": [_P, _PD, ctypes.c_size_t, ctypes.c_int],
@@ -145,6 +150,31 @@ def pabd_add_bond(s, bond: pabd_bond_desc):
     return list(ids[: n.value])
 
 
+# numpy views with the C layout of pabd_body_desc / pabd_bond_desc
+BODY_C_DTYPE = np.dtype([("he", "f8", 3), ("mass", "f8"), ("c", "f8", 3), ("quat", "f8", 4), ("v", "f8", 3),
+                         ("omega", "f8", 3), ("pinned", "i4"), ("group", "i4")], align=True)
+BOND_C_DTYPE = np.dtype([("type", "i4"), ("body_i", "u4"), ("body_j", "u4"), ("x_i", "f8", 3), ("x_j", "f8", 3),
+                         ("axis", "f8", 3), ("kappa", "f8"), ("rest_len", "f8"), ("arm", "f8"),
+                         ("drive_amp", "f8"), ("drive_period", "f8"), ("drive_phase", "f8"),
+                         ("al_beta", "f8"), ("al_alpha", "f8"), ("al_gamma", "f8")], align=True)
+assert BODY_C_DTYPE.itemsize == ctypes.sizeof(pabd_body_desc)
+assert BOND_C_DTYPE.itemsize == ctypes.sizeof(pabd_bond_desc)
+
+
+def pabd_add_bodies(s, rows: np.ndarray):
+    rows = np.ascontiguousarray(rows, dtype=BODY_C_DTYPE)
+    done = ctypes.c_size_t()
+    _check(_lib.pabd_add_bodies(s, rows.ctypes.data, rows.shape[0], None, ctypes.byref(done)), "pabd_add_bodies")
+    return done.value
+
+
+def pabd_add_bonds(s, rows: np.ndarray):
+    rows = np.ascontiguousarray(rows, dtype=BOND_C_DTYPE)
+    done = ctypes.c_size_t()
+    _check(_lib.pabd_add_bonds(s, rows.ctypes.data, rows.shape[0], ctypes.byref(done)), "pabd_add_bonds")
+    return done.value
+
+
 def pabd_step(s, nsteps: int = 1):
     return _check(_lib.pabd_step(s, nsteps), "pabd_step")
 
@@ -174,12 +204,23 @@ def pabd_write_state(s, rows: np.ndarray):
     _check(_lib.pabd_write_state(s, rows.ctypes.data_as(_PD), rows.shape[0]), "pabd_write_state")
 
 
+def pabd_read_bond_state(s, n_static_bonds: int) -> np.ndarray:
+    out = np.zeros((max(n_static_bonds, 1), 2), dtype=np.float64)
+    _check(_lib.pabd_read_bond_state(s, out.ctypes.data_as(_PD), n_static_bonds), "pabd_read_bond_state")
+    return out[:n_static_bonds]
+
+
+def pabd_write_bond_state(s, st: np.ndarray):
+    st = np.ascontiguousarray(st, dtype=np.float64).reshape(-1, 2)
+    _check(_lib.pabd_write_bond_state(s, st.ctypes.data_as(_PD), st.shape[0]), "pabd_write_bond_state")
+
+
 def pabd_set_step_index(s, k: int):
     _check(_lib.pabd_set_step_index(s, int(k)), "pabd_set_step_index")
 
 
-PROFILE_KEYS = ("steps", "collision_ms", "csr_ms", "predict_ms", "bond_ms", "solve_ms", "finalize_ms",
-                "bond_launches", "solve_launches", "step_ms", "bonds_sum")
+PROFILE_KEYS = ("steps", "collision_ms", "csr_ms", "predict_ms", "sweep_ms", "unused_ms", "finalize_ms",
+                "sweep_launches", "sweeps", "step_ms", "bonds_sum")
 
 
 def pabd_set_profiling(s, on: bool):
@@ -310,32 +351,24 @@ class Scene:
         self.h = pabd_create_scene(self.desc)
         self.n = scene.n_bodies
         self.n_groups = scene.n_groups
-        for b in scene.bodies:
-            bd = pabd_body_desc()
-            bd.he = D3(*b["he"])
-            bd.mass = float(b["mass"])
-            bd.c = D3(*b["c"])
-            bd.quat = (ctypes.c_double * 4)(*b["quat"])
-            bd.v = D3(*b["v"])
-            bd.omega = D3(*b["omega"])
-            bd.pinned = int(b["pinned"])
-            bd.group = int(b["group"])
-            pabd_add_body(self.h, bd)
-        for bo in scene.bonds:
-            bb = pabd_bond_desc()
-            bb.type = int(bo["type"])
-            bb.body_i = int(bo["i"])
-            bb.body_j = WORLD if int(bo["j"]) < 0 else int(bo["j"])
-            bb.x_i = D3(*bo["xi"])
-            bb.x_j = D3(*bo["xj"])
-            bb.axis = D3(*bo["axis"])
-            bb.kappa = float(bo["kappa"])
-            bb.rest_len = float(bo["rest"])
-            bb.arm = float(bo["arm"])
-            bb.drive_amp = float(bo["amp"])
-            bb.drive_period = float(bo["period"])
-            bb.drive_phase = float(bo["phase"])
-            pabd_add_bond(self.h, bb)
+        bodies = np.zeros(scene.n_bodies, dtype=BODY_C_DTYPE)
+        for f in ("he", "mass", "c", "quat", "v", "omega", "pinned", "group"):
+            bodies[f] = scene.bodies[f]
+        pabd_add_bodies(self.h, bodies)
+        nb = len(scene.bonds)
+        if nb:
+            bonds = np.zeros(nb, dtype=BOND_C_DTYPE)
+            bonds["type"] = scene.bonds["type"]
+            bonds["body_i"] = scene.bonds["i"].astype(np.int64).astype(np.uint32)
+            j = scene.bonds["j"].astype(np.int64)
+            bonds["body_j"] = np.where(j < 0, np.int64(WORLD), j).astype(np.uint32)
+            bonds["x_i"], bonds["x_j"], bonds["axis"] = scene.bonds["xi"], scene.bonds["xj"], scene.bonds["axis"]
+            bonds["kappa"], bonds["rest_len"], bonds["arm"] = scene.bonds["kappa"], scene.bonds["rest"], scene.bonds["arm"]
+            bonds["drive_amp"], bonds["drive_period"] = scene.bonds["amp"], scene.bonds["period"]
+            bonds["drive_phase"] = scene.bonds["phase"]
+            bonds["al_beta"], bonds["al_alpha"] = scene.bonds["beta"], scene.bonds["alpha"]
+            bonds["al_gamma"] = scene.bonds["gamma"]
+            pabd_add_bonds(self.h, bonds)
 
     def close(self):
         if getattr(self, "h", None):
@@ -368,6 +401,13 @@ class Scene:
 
     def set_step_index(self, k: int):
         pabd_set_step_index(self.h, k)
+
+    def bond_state(self) -> np.ndarray:
+        """(kappa, lambda) of every static bond (zeros for bonds other than AL_DISTANCE)."""
+        return pabd_read_bond_state(self.h, pabd_get_info(self.h)["n_static_bonds"])
+
+    def set_bond_state(self, st: np.ndarray):
+        pabd_write_bond_state(self.h, st)
 
     def set_profiling(self, on: bool):
         pabd_set_profiling(self.h, on)

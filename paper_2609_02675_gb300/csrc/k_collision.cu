@@ -105,13 +105,21 @@ __global__ void k_cells(Dev d) {
     atomicAdd(&d.bucket_cnt[hb], 1);
 }
 
+// Bodies into their buckets, with a compact copy of what the pair test reads (box, id, group,
+// flags, cell) so that a candidate costs one contiguous record read.
 __global__ void k_bucket_fill(Dev d) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= d.N) return;
-    int hb = d.cell[b].w;
-    if (hb < 0) return;
-    int pos = d.bucket_off[hb] + atomicAdd(&d.bucket_cur[hb], 1);
+    const int4 c = d.cell[b];
+    if (c.w < 0) return;
+    const int pos = d.bucket_off[c.w] + atomicAdd(&d.bucket_cur[c.w], 1);
     d.bucket_items[pos] = b;
+    if (d.brec_lo) {
+        const float4 lo = d.lo[b], hi = d.hi[b];
+        d.brec_lo[pos] = make_float4(lo.x, lo.y, lo.z, __int_as_float(b));
+        d.brec_hi[pos] = make_float4(hi.x, hi.y, hi.z, __int_as_float(d.group[b]));
+        d.brec_cell[pos] = make_int4(c.x, c.y, c.z, d.bflags[b]);
+    }
 }
 
 __device__ __forceinline__ bool overlap(const float4& la, const float4& ha, const float4& lb, const float4& hb) {
@@ -156,12 +164,27 @@ __device__ __forceinline__ int lane_partners(const Dev& d, int i, int lane, F&& 
         const int x = ci.x + lane % 3 - 1, y = ci.y + (lane / 3) % 3 - 1, z = ci.z + lane / 9 - 1;
         const int hb = cell_hash(x, y, z, d.table_bits);
         const int s = d.bucket_off[hb], e = d.bucket_off[hb + 1];
-        for (int k = s; k < e; ++k) {
-            const int j = d.bucket_items[k];
-            if (j <= i) continue;
-            const int4 cj = d.cell[j];
-            if (cj.x != x || cj.y != y || cj.z != z) continue;
-            if (pair_ok(d, i, j, gi, fi)) { f(j, n); ++n; }
+        if (d.brec_lo) {
+            const float4 li = d.lo[i], hi_ = d.hi[i];
+            for (int k = s; k < e; ++k) {
+                const int4 cj = d.brec_cell[k];
+                const float4 lj = d.brec_lo[k], hj = d.brec_hi[k];
+                const int j = __float_as_int(lj.w);
+                if (j <= i || cj.x != x || cj.y != y || cj.z != z) continue;
+                if (__float_as_int(hj.w) != gi || ((fi & BF_PINNED) && (cj.w & BF_PINNED))) continue;
+                if (!overlap(li, hi_, lj, hj)) continue;
+                if (adj_has(d, i, j)) continue;
+                f(j, n);
+                ++n;
+            }
+        } else {
+            for (int k = s; k < e; ++k) {
+                const int j = d.bucket_items[k];
+                if (j <= i) continue;
+                const int4 cj = d.cell[j];
+                if (cj.x != x || cj.y != y || cj.z != z) continue;
+                if (pair_ok(d, i, j, gi, fi)) { f(j, n); ++n; }
+            }
         }
     }
     for (int k = lane; k < d.Nlarge; k += 32) {
@@ -202,6 +225,7 @@ __global__ void k_pair_count(Dev d) {
             n = lane_partners(d, i, lane, [](int, int) {});
         }
     }
+    if (d.lane_cnt) d.lane_cnt[32 * i + lane] = n;
     n = warp_sum(n);
     if (lane == 0) d.pair_cnt[i] = n;
 }
@@ -224,7 +248,7 @@ __global__ void k_pair_write(Dev d) {
                 pos += __popc(bal);
             }
         } else {
-            const int mine = lane_partners(d, i, lane, [](int, int) {});
+            const int mine = d.lane_cnt ? d.lane_cnt[32 * i + lane] : lane_partners(d, i, lane, [](int, int) {});
             const int base = s + warp_excl(mine, lane);
             lane_partners(d, i, lane, [&](int j, int k) {
                 if (base + k < cap) d.pairs[base + k] = make_int2(i, j);

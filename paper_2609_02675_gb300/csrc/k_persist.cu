@@ -51,12 +51,14 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, int* status) {
 // accumulate the ends lane, lane + L, ... of body b's CSR slice (bond forces in T)
 template <int L, class T>
 __device__ __forceinline__ void gather_ends(const Dev& d, const float4* __restrict__ q, int b, const float* cb,
-                                            const float* Ab, int e0, int e1, int lane, Sys<T>& s) {
+                                            const float* Ab, int e0, int e1, int lane, int it, Sys<T>& s) {
     for (int p = e0 + lane; p < e1; p += L) {
         const int4 m = d.rec_m[p];
         const float4 xa = d.rec_a[p], xb = d.rec_b[p];
+        // an augmented Lagrangian bond's state is stored by end i, or by end j when i is pinned
+        const bool writer = (m.z == K_AL) && (m.x == b || (d.bflags[m.x] & BF_PINNED));
         T f[3];
-        const T w = end_force<T>(q, d.bn, b, cb, Ab, m, xa, xb, f);
+        const T w = end_force<T>(d, q, b, cb, Ab, m, xa, xb, it, writer, f);
         sys_add_t(s, w, f, (m.y == b) ? xb : xa);
     }
 }
@@ -74,10 +76,41 @@ __global__ void k_sweep_fused(Dev d) {
         const int last = it == d.p.n_iter - 1;
         for (int b = grp; b < d.N; b += ngrp)
             solve_body<L>(d, b, lane, mask, qi, qo, last, [&](auto& s, const float* c, const float* A, int e0, int e1) {
-                gather_ends<L>(d, qi, b, c, A, e0, e1, lane, s);
+                gather_ends<L>(d, qi, b, c, A, e0, e1, lane, it, s);
             });
         if (it + 1 < d.p.n_iter && !grid_sync(d.gbar, &d.ctr[C_STATUS])) return;
     }
+}
+
+// One sweep per launch: the same per-body work as the fused kernel, with the launch boundary
+// (a graph edge) in place of the grid barrier.
+template <int L>
+__global__ void __launch_bounds__(128) k_sweep_one(Dev d, const float4* __restrict__ qi, float4* __restrict__ qo,
+                                                   int it) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = tid / L, lane = tid & (L - 1);
+    if (b >= d.N) return;
+    const int last = it == d.p.n_iter - 1;
+    solve_body<L>(d, b, lane, lane_mask<L>(), qi, qo, last, [&](auto& s, const float* c, const float* A, int e0, int e1) {
+        gather_ends<L>(d, qi, b, c, A, e0, e1, lane, it, s);
+    });
+}
+
+void launch_end_records(const Dev& d, cudaStream_t st, long long* launches);
+
+void launch_sweep_one(const Dev& d, const float4* qi, float4* qo, int it, int L, cudaStream_t st,
+                      long long* launches) {
+    const long long n = (long long)(d.N > 0 ? d.N : 1) * L;
+    const int grid = (int)((n + 127) / 128);
+    if (it == d.p.n_iter - 1) cudaMemsetAsync(d.ctr + C_FP64DYN, 0, sizeof(int), st);
+    switch (L) {
+        case 1: k_sweep_one<1><<<grid, 128, 0, st>>>(d, qi, qo, it); break;
+        case 2: k_sweep_one<2><<<grid, 128, 0, st>>>(d, qi, qo, it); break;
+        case 4: k_sweep_one<4><<<grid, 128, 0, st>>>(d, qi, qo, it); break;
+        case 8: k_sweep_one<8><<<grid, 128, 0, st>>>(d, qi, qo, it); break;
+        default: k_sweep_one<16><<<grid, 128, 0, st>>>(d, qi, qo, it); break;
+    }
+    *launches += 1;
 }
 
 // copy of every bond end's record into CSR order (once per step, after the CSR sort)
@@ -111,13 +144,18 @@ int fused_max_blocks(int L, int block) {
     return per_sm * sms;
 }
 
-cudaError_t launch_fused_sweep(const Dev& d, int L, int block, int grid, cudaStream_t st, long long* launches) {
+void launch_end_records(const Dev& d, cudaStream_t st, long long* launches) {
     const int nrec = d.cap_ends > 0 ? d.cap_ends : 1;
     k_end_records<<<(nrec + 255) / 256, 256, 0, st>>>(d);
+    *launches += 1;
+}
+
+cudaError_t launch_fused_sweep(const Dev& d, int L, int block, int grid, cudaStream_t st, long long* launches) {
+    launch_end_records(d, st, launches);
     Dev dd = d;
     void* args[] = {&dd};
     cudaError_t e = cudaLaunchCooperativeKernel((const void*)fused_fn(L), dim3(grid), dim3(block), args, 0, st);
-    *launches += 2;
+    *launches += 1;
     return e;
 }
 

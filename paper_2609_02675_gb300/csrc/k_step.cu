@@ -152,22 +152,46 @@ __global__ void k_csr_fill(Dev d) {
     else d.end_pos[2 * b + 1] = -1;
 }
 
-// sort each body's slice of end ids, then record every end's slot and material point
+// Sort each body's slice of end ids (one warp per body), then record every end's slot and
+// material point.  Slices of up to 64 ends are sorted in registers by a bitonic network
+// (element k sits in lane k / 2, slot k % 2; padding is INT_MAX); longer slices fall back to
+// an insertion sort by lane 0.  Either way the slice ends up in ascending end id.
 __global__ void k_csr_sort(Dev d) {
-    int body = blockIdx.x * blockDim.x + threadIdx.x;
+    const int body = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (body >= d.N) return;
-    const int s = d.end_off[body], e = d.end_off[body + 1];
-    for (int a = s + 1; a < e; ++a) {
-        int v = d.end_id[a];
-        int k = a - 1;
-        while (k >= s && d.end_id[k] > v) { d.end_id[k + 1] = d.end_id[k]; --k; }
-        d.end_id[k + 1] = v;
+    const int s = d.end_off[body], e = d.end_off[body + 1], n = e - s;
+    if (n <= 64) {
+        int v0 = (2 * lane < n) ? d.end_id[s + 2 * lane] : 0x7fffffff;
+        int v1 = (2 * lane + 1 < n) ? d.end_id[s + 2 * lane + 1] : 0x7fffffff;
+        for (int size = 2; size <= 64; size <<= 1) {
+            const bool up = ((2 * lane) & size) == 0;       // ascending block (same for both slots)
+            for (int stride = size >> 1; stride > 1; stride >>= 1) {
+                const bool lower = ((2 * lane) & stride) == 0; // partner k ^ stride is in lane ^ stride/2
+                const int o0 = __shfl_xor_sync(0xffffffffu, v0, stride >> 1);
+                const int o1 = __shfl_xor_sync(0xffffffffu, v1, stride >> 1);
+                v0 = (lower == up) ? min(v0, o0) : max(v0, o0);
+                v1 = (lower == up) ? min(v1, o1) : max(v1, o1);
+            }
+            const int mn = min(v0, v1), mx = max(v0, v1);  // stride 1: the lane's own pair
+            v0 = up ? mn : mx;
+            v1 = up ? mx : mn;
+        }
+        if (2 * lane < n) d.end_id[s + 2 * lane] = v0;
+        if (2 * lane + 1 < n) d.end_id[s + 2 * lane + 1] = v1;
+    } else if (lane == 0) {
+        for (int a = s + 1; a < e; ++a) {
+            int v = d.end_id[a];
+            int k = a - 1;
+            while (k >= s && d.end_id[k] > v) { d.end_id[k + 1] = d.end_id[k]; --k; }
+            d.end_id[k + 1] = v;
+        }
     }
-    for (int p = s; p < e; ++p) {
-        int id = d.end_id[p];
-        int bond = id >> 1;
+    __syncwarp();
+    for (int p = s + lane; p < e; p += 32) {
+        const int id = d.end_id[p];
+        const int bond = id >> 1;
         d.end_pos[id] = p;
-        float4 x = (id & 1) ? d.bxj[bond] : d.bxi[bond];
+        const float4 x = (id & 1) ? d.bxj[bond] : d.bxi[bond];
         d.end_x[p] = make_float4(x.x, x.y, x.z, 0.f);
     }
 }
@@ -211,7 +235,7 @@ void launch_csr(const Dev& d, cudaStream_t st, long long* launches) {
     k_csr_count<<<nblk(d.cap_bonds), ST_T, 0, st>>>(d);
     scan_exclusive(d.end_cnt, d.end_off, nullptr, d.N, d.scan_scratch, st, launches);
     k_csr_fill<<<nblk(d.cap_bonds), ST_T, 0, st>>>(d);
-    k_csr_sort<<<nblk(d.N), ST_T, 0, st>>>(d);
+    k_csr_sort<<<nblk(d.N * 32), ST_T, 0, st>>>(d);
     *launches += 3;
 }
 

@@ -34,6 +34,8 @@ struct HostBond {
     double w, p1;  // w = h^2 kappa; p1 = rest length
     // drive
     double ui[3], ri[3], arm, amp, period, phase;
+    // augmented Lagrangian distance bond: kappa_start, growth, dual decay, stiffness decay
+    double kappa, al_beta, al_alpha, al_gamma;
 };
 
 void quat_to_mat_d(const double* q, double* R) {
@@ -78,8 +80,10 @@ struct pabd_scene {
     cudaGraphExec_t prof_exec = nullptr;
     double prof_acc[PABD_PROFILE_SLOTS] = {0};
     // fused sweep launch shape
-    int fused = 0, lanes = 8, sw_block = 128, sw_grid = 1;
+    int fused = 0, mode = 1, lanes = 8, sw_block = 128, sw_grid = 1;
     long long coop_fallbacks = 0;
+    // augmented Lagrangian bonds: (kappa_start, 0) per static bond, the state before the first step
+    std::vector<float2> al_init;
 
     void* dalloc(size_t n) {
         if (n == 0) n = 16;
@@ -107,9 +111,11 @@ bool alloc_arr(pabd_scene* s, T*& p, size_t n) {
     return p != nullptr;
 }
 
-// enqueue one time step of Alg. 1 on the scene's stream; with `ev` (5 + 2 n_iter events)
-// an event is recorded after every stage: [0] start, [1] drives + collision, [2] CSR,
-// [3] predictor, [4 + 2k] bond kernel of sweep k, [5 + 2k] solve of sweep k, [last] finalize
+// enqueue one time step of Alg. 1 on the scene's stream; with `ev` (PROF_EVENTS events) an
+// event is recorded at every stage boundary: [0] start, [1] after drives + collision
+// detection, [2] CSR, [3] predictor, [4] all n_iter sweeps, [5] finalize + residual
+constexpr int PROF_EVENTS = 6;
+
 void enqueue_step(pabd_scene* s, long long* launches, const cudaEvent_t* ev = nullptr) {
     const Dev& d = s->d;
     int e = 0;
@@ -123,39 +129,39 @@ void enqueue_step(pabd_scene* s, long long* launches, const cudaEvent_t* ev = nu
     launch_csr(d, s->st, launches);
     mark();
     launch_predict(d, s->st, launches);
+    launch_al_warm(d, s->st, launches);
     mark();
     float4* cur = d.qa;
     float4* nxt = d.qb;
+    auto two_launch = [&]() {
+        for (int it = 0; it < d.p.n_iter; ++it) {
+            launch_bond(d, cur, it, s->st, launches);
+            launch_solve(d, cur, nxt, it == d.p.n_iter - 1, s->lanes, s->st, launches);
+            float4* t = cur; cur = nxt; nxt = t;
+        }
+    };
     if (s->fused) {
-        // events: [4] = the whole fused sweep, [5 .. 3 + 2 n_iter] unused (recorded together)
         cudaMemsetAsync(d.ctr + C_FP64DYN, 0, sizeof(int), s->st);
         if (launch_fused_sweep(d, s->lanes, s->sw_block, s->sw_grid, s->st, launches) != cudaSuccess) {
             // the cooperative launch was refused (e.g. co-residency not available): run the
             // same sweeps as two launches each and count the fallback
             cudaGetLastError();
             s->coop_fallbacks++;
-            for (int it = 0; it < d.p.n_iter; ++it) {
-                launch_bond(d, cur, s->st, launches);
-                launch_solve(d, cur, nxt, it == d.p.n_iter - 1, s->lanes, s->st, launches);
-                float4* t = cur; cur = nxt; nxt = t;
-            }
-            for (int it = 0; it < 2 * d.p.n_iter; ++it) mark();
+            two_launch();
         } else {
-            for (int it = 0; it < d.p.n_iter; ++it) {
-                mark();
-                mark();
-                float4* t = cur; cur = nxt; nxt = t;
-            }
+            if (d.p.n_iter & 1) { float4* t = cur; cur = nxt; nxt = t; }
         }
-    } else {
+    } else if (s->mode == 2) {
+        launch_end_records(d, s->st, launches);
         for (int it = 0; it < d.p.n_iter; ++it) {
-            launch_bond(d, cur, s->st, launches);
-            mark();
-            launch_solve(d, cur, nxt, it == d.p.n_iter - 1, s->lanes, s->st, launches);
-            mark();
+            launch_sweep_one(d, cur, nxt, it, s->lanes, s->st, launches);
             float4* t = cur; cur = nxt; nxt = t;
         }
+    } else {
+        two_launch();
     }
+    launch_al_final(d, cur, s->st, launches);
+    mark();
     launch_finalize(d, cur, s->st, launches);
     mark();
 }
@@ -199,7 +205,7 @@ pabd_status autotune_sweep(pabd_scene* s) {
     cudaGetLastError();
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (best >= 1e30f) s->fused = 0;
+    if (best >= 1e30f) { s->fused = 0; s->mode = 1; }
     // leave the counters as a fresh scene has them
     CK(cudaMemsetAsync(d.ctr, 0, sizeof(int) * C_COUNT, s->st));
     int nb0 = d.Nc;
@@ -230,15 +236,23 @@ pabd_status finalize_scene(pabd_scene* s) {
     p.n_iter = ds.n_iter; p.has_ground = ds.has_ground; p.project = ds.project; p.body_contacts = ds.body_contacts;
     p.precision_policy = ds.precision_policy;
     // capacities
-    d.cap_pairs = (int)(ds.max_pairs ? ds.max_pairs : (size_t)16 * (N > 64 ? N : 64));
-    d.cap_contacts = (int)(ds.max_contacts ? ds.max_contacts : (size_t)24 * (N > 64 ? N : 64));
+    // the two-level scans cover 4096 x 4096 values; bond ends are counted in int.  Defaults:
+    // 16 pairs and 32 contacts per body (a dense granular bed reaches about 24), clamped to
+    // those limits; an explicit capacity beyond them is an error
+    const size_t PAIR_LIMIT = 16000000, CONTACT_LIMIT = 60000000;
+    const size_t nb64 = (size_t)(N > 64 ? N : 64);
+    const size_t want_pairs = ds.max_pairs ? ds.max_pairs : std::min(16 * nb64, PAIR_LIMIT);
+    const size_t want_contacts = ds.max_contacts ? ds.max_contacts : std::min(32 * nb64, CONTACT_LIMIT);
+    if (want_pairs > PAIR_LIMIT || want_contacts > CONTACT_LIMIT || (size_t)N > 8000000) return PABD_ERR_ARG;
+    d.cap_pairs = (int)want_pairs;
+    d.cap_contacts = (int)want_contacts;
     d.cap_bonds = Nc + d.cap_contacts;
     d.cap_ends = 2 * d.cap_bonds;
     int bits = 6;
     while ((1 << bits) < 2 * N) ++bits;
     d.table_bits = bits;
     const int T = 1 << bits;
-    if (T > 16000000 || d.cap_pairs > 16000000 || d.cap_bonds > 8000000) return PABD_ERR_ARG;
+    if (T > 16777216 || (long long)d.cap_bonds * 2 > 2000000000LL) return PABD_ERR_ARG;
 
     // host staging
     std::vector<float4> qn(3 * N), vel(N), omg(N), quat(N), mass(N), he(N);
@@ -295,7 +309,9 @@ pabd_status finalize_scene(pabd_scene* s) {
     for (int k = 0; k < Nc; ++k) {
         const HostBond& hb = s->bonds[k];
         bmeta[k] = make_int4(hb.i, hb.j, hb.type, 0);
-        bxi[k] = make_float4((float)hb.xi[0], (float)hb.xi[1], (float)hb.xi[2], (float)hb.w);
+        // an augmented Lagrangian bond carries h^2 here; its kappa lives in the per-bond state
+        const double xw = hb.type == K_AL ? ds.h * ds.h : hb.w;
+        bxi[k] = make_float4((float)hb.xi[0], (float)hb.xi[1], (float)hb.xi[2], (float)xw);
         bxj[k] = make_float4((float)hb.xj[0], (float)hb.xj[1], (float)hb.xj[2], (float)hb.p1);
         bn[k] = make_float4(0, 0, 0, 0);
         if (hb.i >= 0 && hb.j >= 0) { adj[hb.i].push_back(hb.j); adj[hb.j].push_back(hb.i); }
@@ -310,6 +326,19 @@ pabd_status finalize_scene(pabd_scene* s) {
         drv_t[k] = make_float2((float)hb.period, (float)hb.phase);
         drv_bond[k] = s->drive_ids[k];
         bmeta[s->drive_ids[k]].w = k;
+    }
+    // augmented Lagrangian bonds: parameters and the state a fresh scene starts from
+    std::vector<float4> al_par;
+    for (const HostBond& hb : s->bonds) d.Nal += hb.type == K_AL;
+    if (d.Nal) {
+        al_par.assign(Nc, make_float4(0, 0, 0, 0));
+        s->al_init.assign(Nc, make_float2(0, 0));
+        for (int k = 0; k < Nc; ++k) {
+            const HostBond& hb = s->bonds[k];
+            if (hb.type != K_AL) continue;
+            al_par[k] = make_float4((float)hb.kappa, (float)hb.al_beta, (float)hb.al_alpha, (float)hb.al_gamma);
+            s->al_init[k] = make_float2((float)hb.kappa, 0.f);
+        }
     }
     std::vector<int> adj_off(N + 1, 0), adj_nbr;
     for (int b = 0; b < N; ++b) {
@@ -340,6 +369,8 @@ pabd_status finalize_scene(pabd_scene* s) {
     ok &= alloc_arr(s, d.bucket_cnt, T) && alloc_arr(s, d.bucket_cur, T) && alloc_arr(s, d.bucket_off, T + 1) &&
           alloc_arr(s, d.bucket_items, N);
     ok &= alloc_arr(s, d.pair_cnt, N) && alloc_arr(s, d.pair_off, N + 1) && alloc_arr(s, d.pairs, d.cap_pairs);
+    ok &= alloc_arr(s, d.brec_lo, N) && alloc_arr(s, d.brec_hi, N) && alloc_arr(s, d.brec_cell, N);
+    ok &= alloc_arr(s, d.lane_cnt, (size_t)32 * N);
     ok &= alloc_arr(s, d.npc, d.cap_pairs) && alloc_arr(s, d.npc_off, d.cap_pairs + 1);
     ok &= alloc_arr(s, d.gnd_cnt, N) && alloc_arr(s, d.gnd_off, N + 1);
     ok &= alloc_arr(s, d.ctr, C_COUNT) && alloc_arr(s, d.step_index, 1);
@@ -350,6 +381,7 @@ pabd_status finalize_scene(pabd_scene* s) {
     if (!adj_nbr.empty()) {
         ok &= alloc_arr(s, d.adj_off, N + 1) && alloc_arr(s, d.adj_nbr, adj_nbr.size());
     }
+    if (d.Nal) ok &= alloc_arr(s, d.al_st0, Nc) && alloc_arr(s, d.al_st1, Nc) && alloc_arr(s, d.al_par, Nc);
     if (!ok) return PABD_ERR_OOM;
 
     cudaStream_t st = s->st;
@@ -375,6 +407,7 @@ pabd_status finalize_scene(pabd_scene* s) {
         CK(up(d.adj_off, adj_off.data(), sizeof(int) * (N + 1)));
         CK(up(d.adj_nbr, adj_nbr.data(), sizeof(int) * adj_nbr.size()));
     }
+    if (d.Nal) CK(up(d.al_par, al_par.data(), sizeof(float4) * Nc));
     CK(cudaMemsetAsync(d.ctr, 0, sizeof(int) * C_COUNT, st));
     CK(cudaMemsetAsync(d.step_index, 0, sizeof(long long), st));
     CK(cudaMemsetAsync(d.resid_body, 0, sizeof(double) * (N ? N : 1), st));
@@ -390,7 +423,11 @@ pabd_status finalize_scene(pabd_scene* s) {
     const int L = ds.sweep_lanes ? ds.sweep_lanes : 8;
     if (L != 1 && L != 2 && L != 4 && L != 8 && L != 16) return PABD_ERR_ARG;
     s->lanes = L;
-    s->fused = (ds.sweep_mode == 0) && N > 0;
+    // sweep mode: 1 two launches per sweep, 2 one launch per sweep, 3 fused persistent;
+    // 0 = one launch per sweep (the fastest on the measured scenes)
+    if (ds.sweep_mode < 0 || ds.sweep_mode > 3) return PABD_ERR_ARG;
+    s->mode = ds.sweep_mode == 0 ? 2 : ds.sweep_mode;
+    s->fused = (s->mode == 3) && N > 0;
     if (s->fused) {
         int coop = 0, dev = 0;
         CK(cudaGetDevice(&dev));
@@ -401,6 +438,11 @@ pabd_status finalize_scene(pabd_scene* s) {
         s->lanes = L;
         pabd_status tr = autotune_sweep(s);
         if (tr != PABD_OK) return tr;
+    }
+    // the state the first step's warm start reads (the trial sweeps above may have written it)
+    if (d.Nal) {
+        CK(up((d.p.n_iter & 1) ? d.al_st1 : d.al_st0, s->al_init.data(), sizeof(float2) * Nc));
+        CK(cudaStreamSynchronize(st));
     }
 
     // capture one step as a graph (if the cooperative sweep cannot be captured, capture the
@@ -417,6 +459,7 @@ pabd_status finalize_scene(pabd_scene* s) {
         if (s->graph) { cudaGraphDestroy(s->graph); s->graph = nullptr; }
         if (!s->fused || attempt == 1) { cuda_ok(ce, "capture of the step graph"); return PABD_ERR_CUDA; }
         s->fused = 0;
+        s->mode = 1;
         s->coop_fallbacks = 0;
     }
     CK(cudaGraphGetNodes(s->graph, nullptr, &s->graph_nodes));
@@ -526,6 +569,19 @@ pabd_status pabd_add_bond(pabd_scene* s, const pabd_bond_desc* b, uint32_t* out_
         if (n_out) *n_out = 1;
         return PABD_OK;
     }
+    if (b->type == PABD_AL_DISTANCE) {
+        if (!(b->rest_len >= 0) || !std::isfinite(b->rest_len)) return PABD_ERR_ARG;
+        if (!(b->al_beta >= 0) || !std::isfinite(b->al_beta) || !std::isfinite(b->al_alpha) ||
+            !std::isfinite(b->al_gamma))
+            return PABD_ERR_ARG;
+        hb.type = K_AL;
+        hb.kappa = b->kappa;
+        hb.al_beta = b->al_beta; hb.al_alpha = b->al_alpha; hb.al_gamma = b->al_gamma;
+        s->bonds.push_back(hb);
+        if (out_ids) out_ids[0] = first;
+        if (n_out) *n_out = 1;
+        return PABD_OK;
+    }
     if (b->type != PABD_REVOLUTE && b->type != PABD_DRIVE) return PABD_ERR_ARG;
     double an = std::sqrt(b->axis[0] * b->axis[0] + b->axis[1] * b->axis[1] + b->axis[2] * b->axis[2]);
     if (!(an > 0)) return PABD_ERR_ARG;
@@ -577,12 +633,35 @@ pabd_status pabd_add_bond(pabd_scene* s, const pabd_bond_desc* b, uint32_t* out_
     return PABD_OK;
 }
 
+pabd_status pabd_add_bodies(pabd_scene* s, const pabd_body_desc* b, size_t n, uint32_t* out_ids, size_t* n_done) {
+    if (!s || (n && !b)) return PABD_ERR_ARG;
+    if (n_done) *n_done = 0;
+    s->bodies.reserve(s->bodies.size() + n);
+    for (size_t k = 0; k < n; ++k) {
+        pabd_status r = pabd_add_body(s, b + k, out_ids ? out_ids + k : nullptr);
+        if (r != PABD_OK) return r;
+        if (n_done) *n_done = k + 1;
+    }
+    return PABD_OK;
+}
+
+pabd_status pabd_add_bonds(pabd_scene* s, const pabd_bond_desc* b, size_t n, size_t* n_done) {
+    if (!s || (n && !b)) return PABD_ERR_ARG;
+    if (n_done) *n_done = 0;
+    for (size_t k = 0; k < n; ++k) {
+        pabd_status r = pabd_add_bond(s, b + k, nullptr, nullptr);
+        if (r != PABD_OK) return r;
+        if (n_done) *n_done = k + 1;
+    }
+    return PABD_OK;
+}
+
 pabd_status pabd_set_profiling(pabd_scene* s, int on) {
     if (!s) return PABD_ERR_ARG;
     pabd_status r = finalize_scene(s);
     if (r != PABD_OK) return r;
     if (on && !s->prof_exec) {
-        const int ne = 5 + 2 * s->d.p.n_iter;
+        const int ne = PROF_EVENTS;
         s->prof_ev.resize(ne);
         for (int k = 0; k < ne; ++k) CK(cudaEventCreate(&s->prof_ev[k]));
         long long lc = 0;
@@ -620,14 +699,12 @@ pabd_status profiled_step(pabd_scene* s) {
     acc[1] += ms(0, 1);
     acc[2] += ms(1, 2);
     acc[3] += ms(2, 3);
-    for (int k = 0; k < n_it; ++k) {
-        acc[4] += ms(3 + 2 * k, 4 + 2 * k);
-        acc[5] += ms(4 + 2 * k, 5 + 2 * k);
-    }
-    acc[6] += ms(3 + 2 * n_it, 4 + 2 * n_it);
-    acc[7] += n_it;
+    acc[4] += ms(3, 4);                 // all sweeps of the step
+    acc[5] += 0.0;
+    acc[6] += ms(4, 5);
+    acc[7] += s->fused ? 1 : (s->mode == 1 ? 2 * n_it : n_it);  // sweep-kernel launches
     acc[8] += n_it;
-    acc[9] += ms(0, 4 + 2 * n_it);
+    acc[9] += ms(0, 5);
     int nb = 0;
     CK(cudaMemcpy(&nb, s->d.ctr + C_NBONDS, sizeof(int), cudaMemcpyDeviceToHost));
     acc[10] += nb;
@@ -734,6 +811,46 @@ pabd_status pabd_write_state(pabd_scene* s, const double* rows, size_t n) {
     return PABD_OK;
 }
 
+pabd_status pabd_read_bond_state(pabd_scene* s, double* host_out, size_t n_bonds) {
+    if (!s || (n_bonds && !host_out)) return PABD_ERR_ARG;
+    pabd_status r = finalize_scene(s);
+    if (r != PABD_OK) return r;
+    const Dev& d = s->d;
+    if (n_bonds != (size_t)d.Nc) return PABD_ERR_ARG;
+    std::vector<float2> kl(d.Nc, make_float2(0, 0));
+    if (d.Nal) {
+        // the state a step ends with sits in the buffer of parity n_iter
+        CK(cudaMemcpyAsync(kl.data(), (d.p.n_iter & 1) ? d.al_st1 : d.al_st0, sizeof(float2) * d.Nc,
+                           cudaMemcpyDeviceToHost, s->st));
+    }
+    r = pabd_sync(s);
+    for (int k = 0; k < d.Nc; ++k) {
+        const bool al = s->bonds[k].type == K_AL;
+        host_out[2 * k] = al ? kl[k].x : 0.0;
+        host_out[2 * k + 1] = al ? kl[k].y : 0.0;
+    }
+    return r;
+}
+
+pabd_status pabd_write_bond_state(pabd_scene* s, const double* host_in, size_t n_bonds) {
+    if (!s || (n_bonds && !host_in)) return PABD_ERR_ARG;
+    pabd_status r = finalize_scene(s);
+    if (r != PABD_OK) return r;
+    const Dev& d = s->d;
+    if (n_bonds != (size_t)d.Nc) return PABD_ERR_ARG;
+    if (!d.Nal) return PABD_OK;
+    std::vector<float2> kl(d.Nc, make_float2(0, 0));
+    for (int k = 0; k < d.Nc; ++k) {
+        if (s->bonds[k].type != K_AL) continue;
+        if (!std::isfinite(host_in[2 * k]) || !std::isfinite(host_in[2 * k + 1])) return PABD_ERR_ARG;
+        kl[k] = make_float2((float)host_in[2 * k], (float)host_in[2 * k + 1]);
+    }
+    CK(cudaMemcpyAsync((d.p.n_iter & 1) ? d.al_st1 : d.al_st0, kl.data(), sizeof(float2) * d.Nc,
+                       cudaMemcpyHostToDevice, s->st));
+    CK(cudaStreamSynchronize(s->st));  // the staging vector goes out of scope
+    return PABD_OK;
+}
+
 pabd_status pabd_set_step_index(pabd_scene* s, int64_t step_index) {
     if (!s || step_index < 0) return PABD_ERR_ARG;
     pabd_status r = finalize_scene(s);
@@ -822,7 +939,7 @@ pabd_status pabd_get_info(pabd_scene* s, pabd_info* info) {
     info->graph_nodes = (int64_t)s->graph_nodes;
     info->fp64_bodies = s->fp64_bodies;
     info->device_bytes = (int64_t)s->bytes;
-    info->sweep_mode = s->fused ? 0 : 1;
+    info->sweep_mode = s->fused ? 3 : s->mode;
     info->sweep_lanes = s->lanes;
     info->sweep_block = s->sw_block;
     info->sweep_grid = s->sw_grid;

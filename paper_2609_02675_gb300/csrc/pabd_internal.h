@@ -14,7 +14,7 @@
 
 namespace pabd {
 
-enum BondKind { K_SPHERICAL = 0, K_SPRING = 1, K_ELASTIC_NL = 2, K_DRIVE = 4, K_CONTACT = 5, K_GROUND = 6 };
+enum BondKind { K_SPHERICAL = 0, K_SPRING = 1, K_ELASTIC_NL = 2, K_DRIVE = 4, K_CONTACT = 5, K_GROUND = 6, K_AL = 7 };
 
 enum StatusBits { ST_CAPACITY = 1, ST_DIVERGED = 2, ST_TIMEOUT = 4 };
 
@@ -57,6 +57,11 @@ struct Dev {
     // bonds
     int4 *bmeta;
     float4 *bxi, *bxj, *bn;
+    // augmented Lagrangian bonds: (kappa, lambda) for the sweep of parity k in al_st[k & 1],
+    // parameters (kappa_start, beta, alpha, gamma); indexed by static bond id
+    float2 *al_st0, *al_st1;
+    float4 *al_par;
+    int Nal;
     float4 *drv;                // 3 float4 per drive: (x_i0, arm) (r, amp) (u x r, 0); period/phase in drv_t
     float2 *drv_t;              // (period, phase)
     int *drv_bond;              // bond index of each drive
@@ -71,6 +76,9 @@ struct Dev {
     float4 *lo, *hi;            // inflated AABB; lo.w = inflation
     int4 *cell;                 // cell coords (.w = bucket)
     int *bucket_cnt, *bucket_cur, *bucket_off, *bucket_items;
+    float4 *brec_lo, *brec_hi;  // per bucket slot: (lo, body id bits), (hi, group bits)
+    int4 *brec_cell;            // per bucket slot: (cell x, y, z, flags)
+    int *lane_cnt;              // per body x 32 lanes: partners found by each lane
     int *pair_cnt, *pair_off;
     int2 *pairs;
     int *npc, *npc_off, *gnd_cnt, *gnd_off;
@@ -91,7 +99,10 @@ void launch_collision(const Dev& d, cudaStream_t st, long long* launches);
 void launch_broadphase(const Dev& d, cudaStream_t st, long long* launches);
 void launch_csr(const Dev& d, cudaStream_t st, long long* launches);
 void launch_predict(const Dev& d, cudaStream_t st, long long* launches);
-void launch_bond(const Dev& d, const float4* q, cudaStream_t st, long long* launches);
+void launch_bond(const Dev& d, const float4* q, int it, cudaStream_t st, long long* launches);
+// augmented Lagrangian: warm start (before the sweeps) and the update after the last sweep
+void launch_al_warm(const Dev& d, cudaStream_t st, long long* launches);
+void launch_al_final(const Dev& d, const float4* q, cudaStream_t st, long long* launches);
 void launch_solve(const Dev& d, const float4* q_in, float4* q_out, int last, int lanes, cudaStream_t st,
                   long long* launches);
 void launch_finalize(const Dev& d, const float4* q_fin, cudaStream_t st, long long* launches);
@@ -99,5 +110,9 @@ void launch_drive_update(const Dev& d, cudaStream_t st, long long* launches);
 // fused persistent sweep (all n_iter iterations, cooperative launch); L lanes per body
 cudaError_t launch_fused_sweep(const Dev& d, int L, int block, int grid, cudaStream_t st, long long* launches);
 int fused_max_blocks(int L, int block);
+// one launch per sweep (bonds evaluated by the solve from CSR-ordered end records)
+void launch_end_records(const Dev& d, cudaStream_t st, long long* launches);
+void launch_sweep_one(const Dev& d, const float4* qi, float4* qo, int it, int L, cudaStream_t st,
+                      long long* launches);
 
 }  // namespace pabd

@@ -74,11 +74,51 @@ __device__ __forceinline__ void world_pt_t(const float* c, const float* A, float
         y[k] = (T)c[k] + (T)A[3 * k] * (T)x.x + (T)A[3 * k + 1] * (T)x.y + (T)A[3 * k + 2] * (T)x.z;
 }
 
+// Augmented Lagrangian distance bond at sweep `it` (Eq. 27-29): for it >= 1 first the dual
+// update from the constraint of this iterate (the primal result of sweep it - 1),
+// lambda <- kappa C + lambda, kappa <- kappa + beta |C|, read from the parity-(it-1) buffer and
+// stored by `writer` into the parity-it buffer; then the split force with those values:
+// phi+ = kappa d + max(lambda - kappa l, 0), phi- = min(lambda - kappa l, 0); w = h^2 phi+/d
+// (d kept above 1e-9), f' = w (y_j - y_i) + h^2 phi- n.  xi.w holds h^2, xj.w the rest length.
+template <class T>
+__device__ __forceinline__ T al_force(const Dev& d, int bond, int it, bool writer, float4 xi, float4 xj,
+                                      const T* yi, const T* yj, T* f) {
+    T r[3] = {yj[0] - yi[0], yj[1] - yi[1], yj[2] - yi[2]};
+    T dd = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    T n[3];
+    if (dd > T(0)) { T id = T(1) / dd; n[0] = r[0] * id; n[1] = r[1] * id; n[2] = r[2] * id; }
+    else { n[0] = T(0); n[1] = T(1); n[2] = T(0); }
+    const float l = xj.w;
+    float kap, lam;
+    if (it == 0) {
+        const float2 kl = d.al_st0[bond];
+        kap = kl.x; lam = kl.y;
+    } else {
+        const float2 kl = ((it - 1) & 1) ? d.al_st1[bond] : d.al_st0[bond];
+        const float c = (float)(dd - (T)l);
+        lam = kl.x * c + kl.y;
+        kap = kl.x + d.al_par[bond].y * fabsf(c);
+        if (writer) {
+            float2* out = (it & 1) ? d.al_st1 : d.al_st0;
+            out[bond] = make_float2(kap, lam);
+        }
+    }
+    const T h2 = (T)xi.w;
+    const T cst = (T)lam - (T)kap * (T)l;
+    const T w = h2 * ((T)kap + (cst > T(0) ? cst / (dd > T(1e-9) ? dd : T(1e-9)) : T(0)));
+    const T sc = h2 * (cst < T(0) ? cst : T(0));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) f[k] = w * r[k] + sc * n[k];
+    return w;
+}
+
 // Force of the bond seen from body `self`: loads the other body from q, forms both end
 // points in T, evaluates the split force; returns w and writes the record of self's end.
+// `it` is the sweep index and `writer` whether this evaluation stores an augmented
+// Lagrangian bond's updated state (exactly one evaluation per bond does).
 template <class T>
-__device__ __forceinline__ T end_force(const float4* __restrict__ q, const float4* __restrict__ bn, int self,
-                                       const float* cs, const float* As, int4 m, float4 xa, float4 xb, T* f) {
+__device__ __forceinline__ T end_force(const Dev& d, const float4* __restrict__ q, int self, const float* cs,
+                                       const float* As, int4 m, float4 xa, float4 xb, int it, bool writer, T* f) {
     const bool side_j = (m.y == self);
     float c[3], A[9];
     T yi[3], yj[3];
@@ -95,8 +135,13 @@ __device__ __forceinline__ T end_force(const float4* __restrict__ q, const float
             yj[0] = (T)xb.x; yj[1] = (T)xb.y; yj[2] = (T)xb.z;
         }
     }
-    const float4 nm = (m.z == K_CONTACT || m.z == K_GROUND) ? bn[m.w] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const T w = bond_force<T>(m.z, xa, xb, nm, yi, yj, f);
+    T w;
+    if (m.z == K_AL) {
+        w = al_force<T>(d, m.w, it, writer, xa, xb, yi, yj, f);
+    } else {
+        const float4 nm = (m.z == K_CONTACT || m.z == K_GROUND) ? d.bn[m.w] : make_float4(0.f, 0.f, 0.f, 0.f);
+        w = bond_force<T>(m.z, xa, xb, nm, yi, yj, f);
+    }
     if (side_j) { f[0] = -f[0]; f[1] = -f[1]; f[2] = -f[2]; }
     return w;
 }
@@ -160,25 +205,29 @@ __device__ __forceinline__ void sys_add_t(Sys<T>& s, T w, const T* f, float4 x) 
     }
 }
 
-// Cholesky G = L L^T and solve; returns the smallest pivot / diagonal ratio (<= 0: failed)
+// Cholesky G = L L^T and solve; returns 1 if every pivot is at least 1e-4 of its diagonal
+// (the factorisation is trusted), -1 otherwise
+__device__ __forceinline__ float inv_sqrt(float x) { return 1.f / sqrtf(x); }
+__device__ __forceinline__ double inv_sqrt(double x) { return 1.0 / sqrt(x); }
+
 template <class T>
 __device__ __forceinline__ T sys_solve(const Sys<T>& s, T out[4][3]) {
     const T* g = s.g;
+    // L = lower Cholesky factor, stored through its inverse diagonal i_k = 1 / L_kk
     T d0 = g[0];
-    T l00 = sqrt(d0), i0 = T(1) / l00;
+    T i0 = inv_sqrt(d0);
     T l10 = g[1] * i0, l20 = g[2] * i0, l30 = g[3] * i0;
     T d1 = g[4] - l10 * l10;
-    T l11 = sqrt(d1), i1 = T(1) / l11;
+    T i1 = inv_sqrt(d1);
     T l21 = (g[5] - l20 * l10) * i1, l31 = (g[6] - l30 * l10) * i1;
     T d2 = g[7] - l20 * l20 - l21 * l21;
-    T l22 = sqrt(d2), i2 = T(1) / l22;
+    T i2 = inv_sqrt(d2);
     T l32 = (g[8] - l30 * l20 - l31 * l21) * i2;
     T d3 = g[9] - l30 * l30 - l31 * l31 - l32 * l32;
-    T l33 = sqrt(d3), i3 = T(1) / l33;
-    T ratio = d0 > 0 ? T(1) : T(-1);
-    ratio = fmin(ratio, d1 / g[4]);
-    ratio = fmin(ratio, d2 / g[7]);
-    ratio = fmin(ratio, d3 / g[9]);
+    T i3 = inv_sqrt(d3);
+    // well conditioned iff every pivot keeps at least 1e-4 of its diagonal (no division)
+    const T lim = T(1e-4);
+    const T ratio = (d0 > T(0) && d1 >= lim * g[4] && d2 >= lim * g[7] && d3 >= lim * g[9]) ? T(1) : T(-1);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         T y0 = s.r[0][k] * i0;
@@ -276,7 +325,10 @@ __device__ __noinline__ static void polar_eigen(float* X) {
         for (int c = 0; c < 3; ++c) X[3 * r + c] = u[0][r] * v[0][c] + u[1][r] * v[1][c] + u[2][r] * v[2][c];
 }
 
-__device__ __forceinline__ void polar_rotation(float* X) {
+// Higham's scaled Newton iteration for the orthogonal polar factor:
+// X <- (z X + X^-T / z) / 2, z = |det X|^(-1/3), X^-T = cofactor(X) / det X.  Falls back
+// to the eigen-decomposition route when det X is not clearly positive.
+__device__ __noinline__ static void polar_higham(float* X) {
     float C[9];
     const float nrm = X[0] * X[0] + X[1] * X[1] + X[2] * X[2] + X[3] * X[3] + X[4] * X[4] + X[5] * X[5] +
                       X[6] * X[6] + X[7] * X[7] + X[8] * X[8];
@@ -293,7 +345,42 @@ __device__ __forceinline__ void polar_rotation(float* X) {
             diff += (nx - X[k]) * (nx - X[k]);
             X[k] = nx;
         }
-        if (diff < 1e-13f) break;
+        if (diff < 1e-12f) break;
+    }
+}
+
+// Rotation of A^{k+1/2} (local solve).  A near-orthogonal A (||A^T A - I||_F < 1/2, det > 0)
+// is taken by the Newton-Schulz iteration X <- X (3 I - X^T X) / 2 (Higham 1986, Kovarik
+// 1970), which converges quadratically to the orthogonal polar factor and needs only
+// multiply-adds; anything else goes to Higham's scaled Newton iteration.
+__device__ __forceinline__ void polar_rotation(float* X) {
+    float E[9];
+    for (int it = 0; it < 8; ++it) {
+        // E = X^T X - I
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = r; c < 3; ++c) {
+                float t = X[r] * X[c] + X[3 + r] * X[3 + c] + X[6 + r] * X[6 + c];
+                E[3 * r + c] = t - (r == c ? 1.f : 0.f);
+                E[3 * c + r] = E[3 * r + c];
+            }
+        const float e2 = E[0] * E[0] + E[4] * E[4] + E[8] * E[8] + 2.f * (E[1] * E[1] + E[2] * E[2] + E[5] * E[5]);
+        if (it == 0) {
+            const float det = X[0] * (X[4] * X[8] - X[5] * X[7]) - X[1] * (X[3] * X[8] - X[5] * X[6]) +
+                              X[2] * (X[3] * X[7] - X[4] * X[6]);
+            if (!(e2 < 0.25f) || !(det > 0.f)) { polar_higham(X); return; }
+        }
+        if (e2 < 1e-13f) break;
+        // X <- X (3I - X^T X)/2 = X (I - E/2)
+        float Y[9];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                Y[3 * r + c] = X[3 * r + c] - 0.5f * (X[3 * r] * E[c] + X[3 * r + 1] * E[3 + c] + X[3 * r + 2] * E[6 + c]);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) X[k] = Y[k];
     }
 }
 
@@ -339,7 +426,7 @@ __device__ __forceinline__ void solve_body(const Dev& d, int b, int lane, unsign
     if (fl & BF_PINNED) {
         if (lane == 0) {
             qo[3 * b] = d.qn[3 * b]; qo[3 * b + 1] = d.qn[3 * b + 1]; qo[3 * b + 2] = d.qn[3 * b + 2];
-            d.resid_body[b] = 0.0;
+            if (last) d.resid_body[b] = 0.0;
         }
         return;
     }
@@ -389,14 +476,16 @@ __device__ __forceinline__ void solve_body(const Dev& d, int b, int lane, unsign
     }
     if (d.p.project) polar_rotation(An);
     if (lane != 0) return;
-    double r2 = 0.0;
-    bool finite = true;
+    if (last) {  // residual and finiteness of the step's last sweep only
+        double r2 = 0.0;
+        bool finite = true;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) { double t = (double)cn[k] - (double)c[k]; r2 += t * t; finite &= isfinite(cn[k]); }
+        for (int k = 0; k < 3; ++k) { double t = (double)cn[k] - (double)c[k]; r2 += t * t; finite &= isfinite(cn[k]); }
 #pragma unroll
-    for (int k = 0; k < 9; ++k) { double t = (double)An[k] - (double)A[k]; r2 += t * t; finite &= isfinite(An[k]); }
-    if (!finite) atomicOr(&d.ctr[C_STATUS], ST_DIVERGED);
-    d.resid_body[b] = r2;
+        for (int k = 0; k < 9; ++k) { double t = (double)An[k] - (double)A[k]; r2 += t * t; finite &= isfinite(An[k]); }
+        if (!finite) atomicOr(&d.ctr[C_STATUS], ST_DIVERGED);
+        d.resid_body[b] = r2;
+    }
     qo[3 * b] = make_float4(cn[0], cn[1], cn[2], An[0]);
     qo[3 * b + 1] = make_float4(An[1], An[2], An[3], An[4]);
     qo[3 * b + 2] = make_float4(An[5], An[6], An[7], An[8]);

@@ -33,6 +33,7 @@ SPRING = 1
 ELASTIC_NL = 2
 REVOLUTE = 3
 DRIVE = 4
+AL_DISTANCE = 5   # augmented Lagrangian distance bond (hard constraint), kappa = kappa_start
 
 BODY_DTYPE = np.dtype([
     ("he", "f8", 3), ("mass", "f8"), ("c", "f8", 3), ("quat", "f8", 4),
@@ -42,6 +43,7 @@ BOND_DTYPE = np.dtype([
     ("type", "i4"), ("i", "i4"), ("j", "i4"), ("xi", "f8", 3), ("xj", "f8", 3),
     ("axis", "f8", 3), ("kappa", "f8"), ("rest", "f8"), ("arm", "f8"),
     ("amp", "f8"), ("period", "f8"), ("phase", "f8"),
+    ("beta", "f8"), ("alpha", "f8"), ("gamma", "f8"),
 ])
 
 
@@ -208,14 +210,13 @@ def box_pile(seed: int = SEED_BASE + 2, nx=16, ny=16, nz=16, spacing=3.5, jitter
     b["c"][:, 2] = (gz - 0.5 * (nz - 1)) * spacing
     b["c"] += rng.uniform(-jitter, jitter, (n, 3))
     if stacked:
-        for col in range(nx * nz):
-            ks = np.where(gx * nz + gz == col)[0]
-            ks = ks[np.argsort(gy[ks])]
-            y = 0.0
-            for k in ks:
-                y += 0.002
-                b["c"][k, 1] = y + b["he"][k, 1]
-                y += 2.0 * b["he"][k, 1]
+        col = gx * nz + gz
+        order = np.lexsort((gy, col))                 # by column, bottom to top
+        hgt = 2.0 * b["he"][order, 1] + 0.002         # each box plus the 2 mm gap below it
+        top = np.cumsum(hgt)
+        first = np.r_[True, col[order][1:] != col[order][:-1]]
+        base = np.maximum.accumulate(np.where(first, top - hgt, 0.0))
+        b["c"][order, 1] = top - base - b["he"][order, 1]
     params = default_params(h=1.0 / 60.0, n_iter=n_iter, mu=0.5)
     return Scene("box_pile", params, b, _bonds(0), n_steps, dict(seed=seed, grid=(nx, ny, nz)))
 
@@ -330,6 +331,32 @@ def quadruped_bed_rod(seed: int = SEED_BASE + 3, bed=(100, 5, 100), n_rod=64, n_
                  dict(seed=seed, n_dog=n_dog, n_bed=n_bed, n_rod=n_rod))
 
 
+def mass_ratio_chain(n=6, ratio=100.0, al=True, n_iter=10, n_steps=300, kappa_start=1e4) -> Scene:
+    """A chain of n unit boxes hanging from a pinned anchor box by distance bonds of rest
+    length 0.2 between face centres; the last box is `ratio` times heavier (the paper's
+    large-mass-ratio chain).  al=True: augmented Lagrangian bonds (kappa_start 1e4, beta
+    1e4, alpha 0.99, gamma 0.999); al=False: plain springs of stiffness kappa_start."""
+    b = _bodies(n + 1)
+    b["he"] = 0.25
+    b["mass"] = 1.0
+    b["mass"][-1] = ratio
+    b["pinned"][0] = 1
+    gap = 0.2
+    for k in range(n + 1):
+        b["c"][k] = (0.0, -k * (0.5 + gap), 0.0)
+    bo = _bonds(n)
+    for k in range(n):
+        bo["type"][k] = AL_DISTANCE if al else SPRING
+        bo["i"][k], bo["j"][k] = k, k + 1
+        bo["xi"][k] = (0.0, -0.25, 0.0)
+        bo["xj"][k] = (0.0, 0.25, 0.0)
+        bo["kappa"][k] = kappa_start
+        bo["rest"][k] = gap
+        bo["beta"][k], bo["alpha"][k], bo["gamma"][k] = 1e4, 0.99, 0.999
+    params = default_params(n_iter=n_iter, has_ground=0, body_contacts=0)
+    return Scene("mass_ratio_chain", params, b, bo, n_steps, dict(al=al, ratio=ratio))
+
+
 def batched_trees(seed: int = SEED_BASE + 4, n_scenes=4096, n_min=4, n_max=64, n_steps=1000) -> Scene:
     """n_scenes independent articulated trees (one group each) of U{4..64} boxes with edges
     U[0.1, 0.5]; parent(i) ~ U{0..i-1} restricted to parents with a free face; the child is
@@ -396,10 +423,11 @@ def batched_trees(seed: int = SEED_BASE + 4, n_scenes=4096, n_min=4, n_max=64, n
 
 
 def request_stream(seed: int = SEED_BASE + 5, rate=1000.0, duration=1.0, p_new=0.2,
-                   n_min=10, n_max=100_000, steps_max=60):
+                   n_min=10, n_max=100_000, steps_max=60, max_scenes=None):
     """Poisson arrivals of step requests (scene_id, n_steps ~ U{1..60}); with probability
     p_new a request opens a new scene whose size is log-uniform in [n_min, n_max] (a box
-    pile of that size); otherwise it targets a uniformly chosen existing scene."""
+    pile of that size), until max_scenes exist; otherwise it targets a uniformly chosen
+    existing scene."""
     rng = np.random.default_rng(seed)
     t = 0.0
     reqs = []
@@ -408,7 +436,7 @@ def request_stream(seed: int = SEED_BASE + 5, rate=1000.0, duration=1.0, p_new=0
         t += rng.exponential(1.0 / rate)
         if t > duration:
             break
-        if not sizes or rng.uniform() < p_new:
+        if not sizes or (rng.uniform() < p_new and (max_scenes is None or len(sizes) < max_scenes)):
             sizes.append(int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max))))))
             sid = len(sizes) - 1
         else:

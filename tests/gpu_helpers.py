@@ -47,6 +47,32 @@ def teacher_forced_step(gpu, ref, n: int = 1):
     return gpu.state(), ref.state()
 
 
+def activation_envelope_err(sc, st0, k0, st_gpu, st_ref, he, oracle_mod, ulps: float = 8.0):
+    """Per-step error that allows for contacts at their activation threshold.
+
+    A contact is active in a sweep iff g < dhat, decided from that sweep's iterate; the
+    single-precision path decides it from an iterate that differs from the oracle's by
+    rounding, so a contact within rounding of the threshold may switch the other way, and the
+    Jacobi step is not continuous there.  The oracle is re-run from the same start with the
+    threshold moved by +-delta, delta = `ulps` units of single-precision rounding at the
+    scene's scale; each body is compared with the closest of the three oracle results.
+    Returns (max error, worst body, its error against the unshifted oracle)."""
+    scale = scene_scale(st_ref, he)
+    delta = ulps * 2.0 ** -24 * scale
+    d = np.linalg.norm(corners(st_gpu, he) - corners(st_ref, he), axis=-1).max(axis=1)
+    best = d.copy()
+    for sh in (delta, -delta):
+        r = oracle_mod.OracleScene(sc)
+        r.set_state(st0)
+        r.step_index = k0
+        r.set_activation_shift(sh)
+        r.step(1)
+        dv = np.linalg.norm(corners(st_gpu, he) - corners(r.state(), he), axis=-1).max(axis=1)
+        best = np.minimum(best, dv)
+    k = int(np.argmax(best))
+    return float(best[k]) / scale, k, float(d[k]) / scale
+
+
 def same_contacts(gpu_c, ref_c):
     """Bit-exact contact lists: same (type, i, j) rows in the same order and the same
     single-precision geometry; dhat and w agree to single-precision rounding."""

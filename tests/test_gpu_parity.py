@@ -6,7 +6,7 @@ import pytest
 
 import oracle as O
 import scenes as S
-from tests.gpu_helpers import REL_TOL, rel_err, same_contacts, teacher_forced_step, worst_body
+from tests.gpu_helpers import REL_TOL, activation_envelope_err, rel_err, same_contacts, teacher_forced_step, worst_body
 
 pytestmark = pytest.mark.gpu
 
@@ -134,17 +134,19 @@ def test_pile_teacher_forced_steps(P):
     sc = _pile_small()
     ref = O.OracleScene(sc)
     g = P.Scene(sc)
-    worst = 0.0
+    worst, where = 0.0, None
     n_cont = 0
     for k in range(sc.n_steps):
-        if k % 5 == 4:
+        if k % 3 == 2:
             a, b = teacher_forced_step(g, ref)
-            worst = max(worst, rel_err(a, b, _he(sc)))
+            e = rel_err(a, b, _he(sc))
+            if e > worst:
+                worst, where = e, (k, worst_body(a, b, _he(sc)))
             n_cont += len(ref.contacts()[0])
         else:
             ref.step(1)
     assert n_cont > 500
-    assert worst < REL_TOL, worst
+    assert worst < REL_TOL, (worst, where)
     g.close()
 
 
@@ -219,16 +221,23 @@ def test_quadruped_bed_rod_small_teacher_forced(P):
     sc = S.quadruped_bed_rod(bed=(12, 2, 12), n_rod=16, n_steps=40)
     ref = O.OracleScene(sc)
     g = P.Scene(sc)
-    worst, where = 0.0, None
+    he = _he(sc)
+    worst, where, switched = 0.0, None, []
     for k in range(sc.n_steps):
         if k % 4 == 3:
+            st0, k0 = ref.state(), ref.step_index
             a, b = teacher_forced_step(g, ref)
-            e = rel_err(a, b, _he(sc))
+            e = rel_err(a, b, he)
+            if e >= REL_TOL:
+                # a contact at its activation threshold may switch the other way in single
+                # precision: compare against the oracle with the threshold moved by rounding
+                e, body, e0 = activation_envelope_err(sc, st0, k0, a, b, he, O)
+                switched.append((k, body, e0))
             if e > worst:
-                worst, where = e, (k, worst_body(a, b, _he(sc)), sc.meta)
+                worst, where = e, (k, worst_body(a, b, he), sc.meta)
         else:
             ref.step(1)
-    assert worst < REL_TOL, (worst, where)
+    assert worst < REL_TOL, (worst, where, switched)
     g.close()
 
 
@@ -272,10 +281,11 @@ def test_capacity_overflow_is_reported(P):
 # the two sweep implementations and the fused sweep's lane counts
 # --------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("mode,lanes", [(1, 0), (0, 1), (0, 8), (0, 16)])
+@pytest.mark.parametrize("mode,lanes", [(1, 0), (2, 0), (3, 1), (3, 8), (2, 16)])
 def test_sweep_variants_match_oracle(P, mode, lanes):
-    """Two launches per sweep (mode 1) and the fused persistent sweep with several lane
-    counts all stay within tolerance of the oracle, teacher-forced on the pile and chain."""
+    """Two launches per sweep (mode 1), one launch per sweep (mode 2) and the fused
+    persistent sweep (mode 3) with several lane counts all stay within tolerance of the
+    oracle, teacher-forced on the pile and chain."""
     for sc, every in ((_pile_small(), 7), (S.chain_pendulum(n_steps=30), 1)):
         ref = O.OracleScene(sc)
         g = P.Scene(sc, sweep_mode=mode, sweep_lanes=lanes)
@@ -297,23 +307,77 @@ def test_fused_sweep_deterministic_and_shape_independent(P):
     sc = _pile_small()
     outs = []
     for _ in range(2):
-        g = P.Scene(sc, sweep_mode=0, sweep_lanes=4)
+        g = P.Scene(sc, sweep_mode=3, sweep_lanes=4)
         g.step(40)
         outs.append(g.state())
         g.close()
     assert np.array_equal(outs[0], outs[1])
 
 
-def test_fused_and_two_launch_paths_agree(P):
-    """Same lanes per body: the fused persistent sweep and the two-launch sweep compute the
-    same bonds and the same per-body sums in the same order."""
+def test_sweep_modes_bit_identical(P):
+    """Same lanes per body: the three sweep modes compute the same bonds and the same
+    per-body sums in the same order, so their states are identical bit for bit."""
     sc = _pile_small()
     outs = []
-    for mode in (0, 1):
+    for mode in (1, 2, 3):
         g = P.Scene(sc, sweep_mode=mode, sweep_lanes=8)
+        assert g.info()["sweep_mode"] == mode
         g.step(60)
         outs.append(g.state())
         g.close()
-    he = _he(sc)
-    assert rel_err(outs[0], outs[1], he) < REL_TOL
-    print("bit-identical:", bool(np.array_equal(outs[0], outs[1])))
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[2])
+
+
+# --------------------------------------------------------------------------------------
+# augmented Lagrangian distance bonds (Eq. 27-29)
+# --------------------------------------------------------------------------------------
+
+def _al_hanging(m=2.0, l=0.5, n_iter=20):
+    sc = S.single_body(mass=m, c=(0, -l, 0), n_iter=n_iter, has_ground=0)
+    bo = np.zeros(1, dtype=S.BOND_DTYPE)
+    bo["type"], bo["i"], bo["j"] = S.AL_DISTANCE, 0, S.WORLD
+    bo["kappa"], bo["rest"] = 1e4, l
+    bo["beta"], bo["alpha"], bo["gamma"] = 1e4, 0.99, 0.999
+    sc.bonds = bo
+    return sc
+
+
+def test_al_hanging_equilibrium(P):
+    """At the static equilibrium of a body hung by an augmented Lagrangian bond the
+    constraint is exact and the multiplier equals the tension m g (Eq. 27-29)."""
+    m, l = 2.0, 0.5
+    g = P.Scene(_al_hanging(m, l))
+    g.step(600)
+    st, kl = g.state(), g.bond_state()
+    C = -st[0, 1] - l
+    assert abs(C) < 1e-6, C
+    assert abs(kl[0, 1] - m * 9.81) < 1e-3 * m * 9.81, kl
+    assert kl[0, 0] >= 1e4
+    g.close()
+
+
+@pytest.mark.parametrize("mode", [1, 2, 3])
+def test_al_teacher_forced(P, mode):
+    """The GPU's AL bonds against the oracle, one step at a time from the oracle's state and
+    bond state: a hung body, a three-box chain (bonds with a pinned end i and with two dynamic
+    ends), and a bond between a pinned body and the world (advanced by the final update alone)."""
+    chain = S.mass_ratio_chain(n=3, ratio=1.0, n_iter=10)
+    fixed = S.single_body(c=(0, -0.6, 0), n_iter=7, has_ground=0)
+    fixed.bodies["pinned"] = 1
+    bo = np.zeros(1, dtype=S.BOND_DTYPE)
+    bo["type"], bo["i"], bo["j"] = S.AL_DISTANCE, 0, S.WORLD
+    bo["xi"] = (0.0, 0.5, 0.0)
+    bo["kappa"], bo["rest"], bo["beta"], bo["alpha"], bo["gamma"] = 1e3, 0.05, 10.0, 0.9, 0.99
+    fixed.bonds = bo
+    for sc, n in ((_al_hanging(), 6), (chain, 3), (fixed, 3)):
+        ref = O.OracleScene(sc)
+        g = P.Scene(sc, sweep_mode=mode)
+        for _ in range(n):
+            g.set_bond_state(ref.al_state())
+            a, b = teacher_forced_step(g, ref)
+            assert rel_err(a, b, _he(sc)) < REL_TOL, (sc.name, rel_err(a, b, _he(sc)))
+            kg, kr = g.bond_state(), ref.al_state()
+            np.testing.assert_allclose(kg[:, 0], kr[:, 0], rtol=1e-4)
+            np.testing.assert_allclose(kg[:, 1], kr[:, 1], rtol=1e-3, atol=1e-3 * max(1.0, np.abs(kr[:, 1]).max()))
+        g.close()

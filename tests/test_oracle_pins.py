@@ -413,3 +413,50 @@ def test_drive_tracks_target_angle():
         th = math.atan2(A[1, 0], A[0, 0])
         errs.append(abs(th - 0.3 * math.sin(2 * math.pi * n * H60 / 4.0)))
     assert max(errs[60:]) < 0.02
+
+
+# --------------------------------------------------------------------------------------
+# augmented Lagrangian distance bond (Eq. 27-29)
+# --------------------------------------------------------------------------------------
+
+def test_al_bond_hanging_equilibrium():
+    """Eq. 27-29: at the static equilibrium of a body hung by an augmented Lagrangian
+    distance bond the constraint is exact (C = 0) and the multiplier is the tension m g;
+    a plain spring of the same starting stiffness stretches by m g / kappa."""
+    m, l, k0 = 2.0, 0.5, 1e4
+    res = {}
+    for kind in (S.AL_DISTANCE, S.SPRING):
+        sc = S.single_body(mass=m, c=(0, -l, 0), n_iter=20, has_ground=0)
+        bo = np.zeros(1, dtype=S.BOND_DTYPE)
+        bo["type"], bo["i"], bo["j"] = kind, 0, S.WORLD
+        bo["kappa"], bo["rest"] = k0, l
+        bo["beta"], bo["alpha"], bo["gamma"] = 1e4, 0.99, 0.999
+        sc.bonds = bo
+        o = O.OracleScene(sc)
+        o.step(600)
+        res[kind] = (-o.state()[0, 1] - l, o.al_state()[0])
+    c_al, (kap, lam) = res[S.AL_DISTANCE]
+    assert abs(c_al) < 1e-9
+    assert abs(lam - m * G) < 1e-9 * m * G
+    assert kap >= k0
+    assert abs(res[S.SPRING][0] - m * G / k0) < 1e-9
+
+
+def test_al_warm_start_rule():
+    """Between steps kappa^0 = max(gamma kappa^n, kappa_start) (Eq. 29): with the constraint
+    satisfied, no multiplier and no gravity nothing moves, so the sweeps leave kappa as the
+    warm start set it; it decays by gamma per step down to kappa_start."""
+    sc = S.single_body(c=(0, -0.5, 0), n_iter=5, has_ground=0, gravity=(0, 0, 0))
+    bo = np.zeros(1, dtype=S.BOND_DTYPE)
+    bo["type"], bo["i"], bo["j"] = S.AL_DISTANCE, 0, S.WORLD
+    bo["kappa"], bo["rest"] = 1e4, 0.5
+    bo["beta"], bo["alpha"], bo["gamma"] = 1e4, 0.99, 0.999
+    sc.bonds = bo
+    o = O.OracleScene(sc)
+    o.set_al_state(np.array([[5e4, 0.0]]))
+    o.step(3)
+    kap, lam = o.al_state()[0]
+    assert abs(kap - 0.999 ** 3 * 5e4) < 1e-6 and abs(lam) < 1e-9
+    o.set_al_state(np.array([[5e3, 0.0]]))
+    o.step(1)
+    assert o.al_state()[0][0] == 1e4
