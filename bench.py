@@ -233,7 +233,9 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream(dev)
     sc = workload()
     K, W = args.steps, args.warmup
-    g = P.Scene(sc, device=dev, stream=stream, sweep_mode=args.sweep_mode, sweep_lanes=args.lanes)
+    # a settled granular bed reaches about 13 candidate pairs and 30 contact points per grain
+    cap = dict(max_pairs=32 * sc.n_bodies, max_contacts=64 * sc.n_bodies) if args.workload == "quadruped" else {}
+    g = P.Scene(sc, device=dev, stream=stream, sweep_mode=args.sweep_mode, sweep_lanes=args.lanes, **cap)
     st0 = g.state()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
 
