@@ -92,14 +92,26 @@ typedef struct {
     int project;              /* 1: local solve (polar rotation); 0: affine bodies */
     int body_contacts;        /* 0: only ground contacts */
     double large_he;          /* bodies with a half extent above this skip the grid */
-    int precision_policy;     /* 0: FP32 solves; 1: FP64 per-body solve where ill-conditioned */
+    int precision_policy;     /* per-body solves in FP32 (each body's 4x4 system assembled about
+                                 the weighted centre of its static bonds, which removes the
+                                 cancellation of stiff joints), and where still ill-conditioned
+                                 (static flag: the scaled static-only system has a Cholesky pivot
+                                 below 1e-2 of its diagonal; or at run time an FP32 pivot below
+                                 1e-3 of its diagonal) the
+                                 body's bond gather and factorisation redone in 1: double-float
+                                 (two floats, ~48-bit significand, FP32 pipes; the default),
+                                 2: FP64; 3: every body in double-float; 0: never (FP32 only).
+                                 Other values: PABD_ERR_ARG. */
     int sweep_mode;           /* 1: a bond launch + a solve launch per sweep; 2: one launch per
                                  sweep (the solve evaluates its bonds); 3: one cooperative launch
                                  runs all n_iter sweeps; 0: the library's choice (2).  All modes
                                  give the same results for the same sweep_lanes */
-    int sweep_lanes;          /* lanes per body in the per-body solve: 1, 2, 4, 8 or 16; 0 = 8.
-                                 Fixes the summation order (results depend on it, not on the
-                                 block / grid sizes, which the library autotunes) */
+    int sweep_lanes;          /* lanes per body in the per-body solve: 1, 2, 4, 8 or 16; 0 = from
+                                 the body count N: the largest of 16, 8, 4, 2, 1 with lanes * N
+                                 <= 2^17 (1 at least).  Fixes the summation order (results depend on
+                                 it, not on the block / grid sizes, which the library autotunes).
+                                 A body with more than 64 bond ends is summed by a block of 128
+                                 threads in every mode. */
     size_t max_pairs;         /* capacities: at most 16 M pairs, 0 = 16 per body (clamped to 16 M) */
     size_t max_contacts;      /* at most 60 M, 0 = 32 per body (clamped to 60 M); at most 8 M bodies.
                                  Exceeding one in a step latches PABD_ERR_CAPACITY. */
@@ -143,12 +155,16 @@ typedef struct {
     int64_t max_pairs, max_contacts;
     int64_t graph_nodes;      /* kernel + memset nodes of one captured step */
     int64_t launches;         /* kernels launched by this scene so far */
-    int64_t fp64_bodies;      /* bodies whose solve is statically flagged for FP64 */
+    int64_t fp64_bodies;      /* bodies whose solve is statically flagged for the extended type */
     int64_t device_bytes;     /* device memory held by the scene */
     int64_t sweep_mode, sweep_lanes, sweep_block, sweep_grid;  /* sweep mode (1, 2, 3) and the
                                  fused sweep's launch shape */
     int64_t coop_fallbacks;   /* steps whose cooperative sweep launch was refused and ran as
                                  two launches per sweep instead */
+    int64_t heavy_bodies;     /* bodies of the last step with more than 64 bond ends, each
+                                 gathered and solved by a block of 256 threads */
+    int64_t fp64_dynamic;     /* bodies that took the extended-precision redo in the last sweep
+                                 of the last step because of a small FP32 pivot */
 } pabd_info;
 
 /* Create an empty scene on the current CUDA device.  *out receives the handle. */

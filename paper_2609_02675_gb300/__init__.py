@@ -67,7 +67,8 @@ class pabd_info(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
         "n_bodies", "n_groups", "n_static_bonds", "n_bonds", "n_pairs", "n_contacts", "step_index",
         "max_pairs", "max_contacts", "graph_nodes", "launches", "fp64_bodies", "device_bytes",
-        "sweep_mode", "sweep_lanes", "sweep_block", "sweep_grid", "coop_fallbacks")]
+        "sweep_mode", "sweep_lanes", "sweep_block", "sweep_grid", "coop_fallbacks", "heavy_bodies",
+        "fp64_dynamic")]
 
 
 _P = ctypes.c_void_p

@@ -1,13 +1,15 @@
 // Collision detection (Alg. 1, first line) on the device.
 //
 // Broad phase: uniform grid hash.  Every body's inflated AABB is computed in IEEE single
-// precision with a fixed operation order; the cell size is the largest AABB width of the
-// grid bodies (times 1.01), so two overlapping boxes always sit in the same or in adjacent
-// cells.  Bodies are counting-sorted into hash buckets; each body scans the 27 cells around
-// its own and keeps the neighbours j > i whose boxes overlap, whose cell really is the
-// visited one (so hash collisions never duplicate a pair), that share its group and are
-// not joined to it by a user bond.  Bodies larger than the scene's `large_he` bypass the
-// grid and are tested against all bodies.  Each body's partner list is sorted, so the
+// precision with a fixed operation order.  The cell size is the widest grid box of the step
+// (times 1.01), so two overlapping grid boxes always sit in the same or in adjacent cells.
+// A scene caps it at creation from its grid bodies' extents (with an allowance for their
+// motion): a body whose inflated box is wider than the cap this step -- one flagged larger
+// than the scene's `large_he`, or one moving fast -- goes off the grid and is tested against
+// all bodies instead of widening every cell.  Bodies are counting-sorted into hash
+// buckets; each body scans the 27 cells around its own and keeps the neighbours j > i whose
+// boxes overlap, whose cell really is the visited one (so hash collisions never duplicate a
+// pair), that share its group and are not joined to it by a user bond.  Each body's partner list is sorted, so the
 // final list is the sorted set of overlapping pairs -- independent of bucket order.
 //
 // Narrow phase: box-box contact manifold (reference face by separating axis over the six
@@ -71,11 +73,19 @@ __global__ void k_aabb(Dev d) {
     }
     d.lo[b] = make_float4(lo[0], lo[1], lo[2], infl);
     d.hi[b] = make_float4(hi[0], hi[1], hi[2], 0.f);
-    if (!(d.bflags[b] & BF_LARGE)) {
-        float w = fmaxf(fmaxf(hi[0] - lo[0], hi[1] - lo[1]), hi[2] - lo[2]);
-        w = w * 1.01f + 1e-6f;
-        if (w < 1e30f) atomicMax(&d.ctr[C_CELLBITS], __float_as_int(w));  // positive floats order as ints
+    // off the grid: flagged large, or (with a fixed cell size) a box wider than a cell -- a fast
+    // body whose inflation grew its box -- or a box that is not finite
+    // The cell is the widest grid box of this step (times 1.01); with a scene cap p.cell, a box
+    // wider than the cap leaves the grid instead of widening every cell.
+    const float w = fmaxf(fmaxf(FS(hi[0], lo[0]), FS(hi[1], lo[1])), FS(hi[2], lo[2]));
+    bool large = d.bflags[b] & BF_LARGE;
+    if (d.p.cell > 0.f) large = large || !(w <= d.p.cell);
+    if (!large) {
+        const float wc = w * 1.01f + 1e-6f;
+        if (wc < 1e30f) atomicMax(&d.ctr[C_CELLBITS], __float_as_int(wc));  // positive floats order as ints
     }
+    d.cell[b] = make_int4(0, 0, 0, large ? -1 : 0);
+    if (large && d.large_ids) d.large_ids[atomicAdd(&d.ctr[C_NLARGE], 1)] = b;
 }
 
 __device__ __forceinline__ int cell_coord(float x, float inv_cs) {
@@ -95,8 +105,8 @@ __device__ __forceinline__ int cell_hash(int x, int y, int z, int bits) {
 __global__ void k_cells(Dev d) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= d.N) return;
-    if (d.bflags[b] & BF_LARGE) { d.cell[b] = make_int4(0, 0, 0, -1); return; }
-    float cs = __int_as_float(d.ctr[C_CELLBITS]);
+    if (d.cell[b].w < 0) return;  // off the grid (k_aabb)
+    const float cs = __int_as_float(d.ctr[C_CELLBITS]);
     float inv = 1.0f / cs;
     float4 a = d.qn[3 * b];
     int x = cell_coord(a.x, inv), y = cell_coord(a.y, inv), z = cell_coord(a.z, inv);
@@ -187,7 +197,8 @@ __device__ __forceinline__ int lane_partners(const Dev& d, int i, int lane, F&& 
             }
         }
     }
-    for (int k = lane; k < d.Nlarge; k += 32) {
+    const int nl = d.large_ids ? d.ctr[C_NLARGE] : 0;
+    for (int k = lane; k < nl; k += 32) {
         const int j = d.large_ids[k];
         if (j > i && pair_ok(d, i, j, gi, fi)) { f(j, n); ++n; }
     }
@@ -216,7 +227,7 @@ __global__ void k_pair_count(Dev d) {
     int n = 0;
     if (d.p.body_contacts) {
         const int gi = d.group[i], fi = d.bflags[i];
-        if (fi & BF_LARGE) {
+        if (d.cell[i].w < 0) {
             for (int j0 = i + 1; j0 < d.N; j0 += 32) {
                 const int j = j0 + lane;
                 n += (j < d.N && pair_ok(d, i, j, gi, fi)) ? 1 : 0;
@@ -237,7 +248,7 @@ __global__ void k_pair_write(Dev d) {
     const int cap = d.cap_pairs;
     if (d.p.body_contacts) {
         const int gi = d.group[i], fi = d.bflags[i];
-        if (fi & BF_LARGE) {
+        if (d.cell[i].w < 0) {
             int pos = s;
             for (int j0 = i + 1; j0 < d.N; j0 += 32) {
                 const int j = j0 + lane;
@@ -505,6 +516,7 @@ void launch_collision(const Dev& d, cudaStream_t st, long long* launches) {
     cudaMemsetAsync(d.bucket_cnt, 0, sizeof(int) * T, st);
     cudaMemsetAsync(d.bucket_cur, 0, sizeof(int) * T, st);
     cudaMemsetAsync(d.ctr + C_CELLBITS, 0, sizeof(int), st);
+    cudaMemsetAsync(d.ctr + C_NLARGE, 0, sizeof(int), st);
     k_aabb<<<nblk(d.N), CT, 0, st>>>(d);
     k_cells<<<nblk(d.N), CT, 0, st>>>(d);
     scan_exclusive(d.bucket_cnt, d.bucket_off, nullptr, T, d.scan_scratch, st, launches);

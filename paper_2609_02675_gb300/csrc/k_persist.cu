@@ -48,51 +48,95 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, int* status) {
     return s_ok != 0;
 }
 
-// accumulate the ends lane, lane + L, ... of body b's CSR slice (bond forces in T)
+// an augmented Lagrangian bond's state is stored by end i, or by end j when i is pinned
+__device__ __forceinline__ bool al_writer(const Dev& d, int4 m, int b) {
+    return (m.z == K_AL) && (m.x == b || (d.bflags[m.x] & BF_PINNED));
+}
+
+// accumulate the ends lane, lane + L, ... of body b's CSR slice (bond forces in T), in that
+// order.  Two ends per round in FP32: both records and both other bodies' iterates are loaded
+// before either force is evaluated, so a lane waits for two dependent loads per pair of ends.
 template <int L, class T>
 __device__ __forceinline__ void gather_ends(const Dev& d, const float4* __restrict__ q, int b, const float* cb,
-                                            const float* Ab, int e0, int e1, int lane, int it, Sys<T>& s) {
-    for (int p = e0 + lane; p < e1; p += L) {
+                                            const float* Ab, const float* xs, int e0, int e1, int lane, int it,
+                                            Sys<T>& s) {
+    int p = e0 + lane;
+    // (the FP64 redo, rare, keeps one end per round: fewer live registers)
+    if (sizeof(T) == 4) for (; p + L < e1; p += 2 * L) {
+        const int4 m0 = d.rec_m[p], m1 = d.rec_m[p + L];
+        const float4 a0 = d.rec_a[p], b0 = d.rec_b[p], a1 = d.rec_a[p + L], b1 = d.rec_b[p + L];
+        float c0[3], A0[9], c1[3], A1[9];
+        ld_q_or_zero(q, other_body(m0, b), c0, A0);
+        ld_q_or_zero(q, other_body(m1, b), c1, A1);
+        T f[3];
+        T w = end_force_q<T>(d, c0, A0, b, cb, Ab, m0, a0, b0, it, al_writer(d, m0, b), f);
+        sys_add_t(s, w, f, (m0.y == b) ? b0 : a0, xs);
+        w = end_force_q<T>(d, c1, A1, b, cb, Ab, m1, a1, b1, it, al_writer(d, m1, b), f);
+        sys_add_t(s, w, f, (m1.y == b) ? b1 : a1, xs);
+    }
+    for (; p < e1; p += L) {
         const int4 m = d.rec_m[p];
         const float4 xa = d.rec_a[p], xb = d.rec_b[p];
-        // an augmented Lagrangian bond's state is stored by end i, or by end j when i is pinned
-        const bool writer = (m.z == K_AL) && (m.x == b || (d.bflags[m.x] & BF_PINNED));
         T f[3];
-        const T w = end_force<T>(d, q, b, cb, Ab, m, xa, xb, it, writer, f);
-        sys_add_t(s, w, f, (m.y == b) ? xb : xa);
+        const T w = end_force<T>(d, q, b, cb, Ab, m, xa, xb, it, al_writer(d, m, b), f);
+        sys_add_t(s, w, f, (m.y == b) ? xb : xa, xs);
     }
 }
 
-template <int L>
-__global__ void k_sweep_fused(Dev d) {
+template <int L, class X>
+__global__ void __launch_bounds__(HEAVY_T, 4) k_sweep_fused(Dev d) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & (L - 1);
     const int grp = tid / L;
     const int ngrp = (gridDim.x * blockDim.x) / L;
     const unsigned mask = lane_mask<L>();
+    const int nheavy = d.ctr[C_NHEAVY];
     for (int it = 0; it < d.p.n_iter; ++it) {
         const float4* qi = (it & 1) ? d.qb : d.qa;
         float4* qo = (it & 1) ? d.qa : d.qb;
         const int last = it == d.p.n_iter - 1;
+        // bodies with many ends first: the first HEAVY_BLOCKS blocks take the heavy role (the
+        // launch uses HEAVY_T threads per block and at least HEAVY_BLOCKS blocks)
+        if ((int)blockIdx.x < HEAVY_BLOCKS && nheavy > 0)
+            heavy_role<X>(d, blockIdx.x, qi, qo, last,
+                [&](int b, auto& s, const float* c, const float* A, const float* xs, int e0, int e1, int ln) {
+                    gather_ends<32>(d, qi, b, c, A, xs, e0, e1, ln, it, s);
+                },
+                [&](int b, auto& s, const float* c, const float* A, const float* xs, int e0, int e1, int t) {
+                    gather_ends<HEAVY_T>(d, qi, b, c, A, xs, e0, e1, t, it, s);
+                });
         for (int b = grp; b < d.N; b += ngrp)
-            solve_body<L>(d, b, lane, mask, qi, qo, last, [&](auto& s, const float* c, const float* A, int e0, int e1) {
-                gather_ends<L>(d, qi, b, c, A, e0, e1, lane, it, s);
+            solve_body<L, X>(d, b, lane, mask, qi, qo, last, [&](auto& s, const float* c, const float* A, const float* xs, int e0, int e1) {
+                gather_ends<L>(d, qi, b, c, A, xs, e0, e1, lane, it, s);
             });
         if (it + 1 < d.p.n_iter && !grid_sync(d.gbar, &d.ctr[C_STATUS])) return;
     }
 }
 
 // One sweep per launch: the same per-body work as the fused kernel, with the launch boundary
-// (a graph edge) in place of the grid barrier.
-template <int L>
-__global__ void __launch_bounds__(128) k_sweep_one(Dev d, const float4* __restrict__ qi, float4* __restrict__ qo,
-                                                   int it) {
+// (a graph edge) in place of the grid barrier.  Capped at 128 registers (4 blocks per SM):
+// the heavy role and the extended-precision paths, which alone need more, spill a little.  The first `light` blocks take the bodies with
+// at most HEAVY_ENDS ends (L lanes each); the HEAVY_BLOCKS blocks after them take the heavy
+// bodies, a block each.
+template <int L, class X>
+__global__ void __launch_bounds__(128, 4) k_sweep_one(Dev d, const float4* __restrict__ qi, float4* __restrict__ qo,
+                                                   int it, int light) {
+    const int last = it == d.p.n_iter - 1;
+    if ((int)blockIdx.x >= light) {
+        heavy_role<X>(d, blockIdx.x - light, qi, qo, last,
+            [&](int b, auto& s, const float* c, const float* A, const float* xs, int e0, int e1, int ln) {
+                gather_ends<32>(d, qi, b, c, A, xs, e0, e1, ln, it, s);
+            },
+            [&](int b, auto& s, const float* c, const float* A, const float* xs, int e0, int e1, int t) {
+                gather_ends<HEAVY_T>(d, qi, b, c, A, xs, e0, e1, t, it, s);
+            });
+        return;
+    }
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int b = tid / L, lane = tid & (L - 1);
     if (b >= d.N) return;
-    const int last = it == d.p.n_iter - 1;
-    solve_body<L>(d, b, lane, lane_mask<L>(), qi, qo, last, [&](auto& s, const float* c, const float* A, int e0, int e1) {
-        gather_ends<L>(d, qi, b, c, A, e0, e1, lane, it, s);
+    solve_body<L, X>(d, b, lane, lane_mask<L>(), qi, qo, last, [&](auto& s, const float* c, const float* A, const float* xs, int e0, int e1) {
+        gather_ends<L>(d, qi, b, c, A, xs, e0, e1, lane, it, s);
     });
 }
 
@@ -100,15 +144,27 @@ void launch_end_records(const Dev& d, cudaStream_t st, long long* launches);
 
 void launch_sweep_one(const Dev& d, const float4* qi, float4* qo, int it, int L, cudaStream_t st,
                       long long* launches) {
+    static_assert(HEAVY_T == 128, "the sweep launch's blocks are the heavy bodies' blocks");
     const long long n = (long long)(d.N > 0 ? d.N : 1) * L;
-    const int grid = (int)((n + 127) / 128);
-    if (it == d.p.n_iter - 1) cudaMemsetAsync(d.ctr + C_FP64DYN, 0, sizeof(int), st);
-    switch (L) {
-        case 1: k_sweep_one<1><<<grid, 128, 0, st>>>(d, qi, qo, it); break;
-        case 2: k_sweep_one<2><<<grid, 128, 0, st>>>(d, qi, qo, it); break;
-        case 4: k_sweep_one<4><<<grid, 128, 0, st>>>(d, qi, qo, it); break;
-        case 8: k_sweep_one<8><<<grid, 128, 0, st>>>(d, qi, qo, it); break;
-        default: k_sweep_one<16><<<grid, 128, 0, st>>>(d, qi, qo, it); break;
+    const int light = (int)((n + 127) / 128);
+    const int grid = light + HEAVY_BLOCKS;
+    // the extended type of ill-conditioned bodies: FP64 under policy 2, double-float otherwise
+    if (d.p.precision_policy == 2) {
+        switch (L) {
+            case 1: k_sweep_one<1, double><<<grid, 128, 0, st>>>(d, qi, qo, it, light); break;
+            case 2: k_sweep_one<2, double><<<grid, 128, 0, st>>>(d, qi, qo, it, light); break;
+            case 4: k_sweep_one<4, double><<<grid, 128, 0, st>>>(d, qi, qo, it, light); break;
+            case 8: k_sweep_one<8, double><<<grid, 128, 0, st>>>(d, qi, qo, it, light); break;
+            default: k_sweep_one<16, double><<<grid, 128, 0, st>>>(d, qi, qo, it, light); break;
+        }
+    } else {
+        switch (L) {
+            case 1: k_sweep_one<1, df><<<grid, 128, 0, st>>>(d, qi, qo, it, light); break;
+            case 2: k_sweep_one<2, df><<<grid, 128, 0, st>>>(d, qi, qo, it, light); break;
+            case 4: k_sweep_one<4, df><<<grid, 128, 0, st>>>(d, qi, qo, it, light); break;
+            case 8: k_sweep_one<8, df><<<grid, 128, 0, st>>>(d, qi, qo, it, light); break;
+            default: k_sweep_one<16, df><<<grid, 128, 0, st>>>(d, qi, qo, it, light); break;
+        }
     }
     *launches += 1;
 }
@@ -126,21 +182,30 @@ __global__ void k_end_records(Dev d) {
 
 using FusedFn = void (*)(Dev);
 
-static FusedFn fused_fn(int L) {
+static FusedFn fused_fn(int L, bool fp64) {
+    if (fp64) {
+        switch (L) {
+            case 1: return k_sweep_fused<1, double>;
+            case 2: return k_sweep_fused<2, double>;
+            case 4: return k_sweep_fused<4, double>;
+            case 8: return k_sweep_fused<8, double>;
+            default: return k_sweep_fused<16, double>;
+        }
+    }
     switch (L) {
-        case 1: return k_sweep_fused<1>;
-        case 2: return k_sweep_fused<2>;
-        case 4: return k_sweep_fused<4>;
-        case 8: return k_sweep_fused<8>;
-        default: return k_sweep_fused<16>;
+        case 1: return k_sweep_fused<1, df>;
+        case 2: return k_sweep_fused<2, df>;
+        case 4: return k_sweep_fused<4, df>;
+        case 8: return k_sweep_fused<8, df>;
+        default: return k_sweep_fused<16, df>;
     }
 }
 
-int fused_max_blocks(int L, int block) {
+int fused_max_blocks(int L, int block, bool fp64) {
     int per_sm = 0, sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_fn(L), block, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_fn(L, fp64), block, 0);
     return per_sm * sms;
 }
 
@@ -154,7 +219,8 @@ cudaError_t launch_fused_sweep(const Dev& d, int L, int block, int grid, cudaStr
     launch_end_records(d, st, launches);
     Dev dd = d;
     void* args[] = {&dd};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void*)fused_fn(L), dim3(grid), dim3(block), args, 0, st);
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)fused_fn(L, d.p.precision_policy == 2), dim3(grid),
+                                                dim3(block), args, 0, st);
     *launches += 1;
     return e;
 }

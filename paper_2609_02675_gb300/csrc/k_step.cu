@@ -153,14 +153,19 @@ __global__ void k_csr_fill(Dev d) {
 }
 
 // Sort each body's slice of end ids (one warp per body), then record every end's slot and
-// material point.  Slices of up to 64 ends are sorted in registers by a bitonic network
-// (element k sits in lane k / 2, slot k % 2; padding is INT_MAX); longer slices fall back to
-// an insertion sort by lane 0.  Either way the slice ends up in ascending end id.
+// material point.  Slices of up to HEAVY_ENDS (64) ends are sorted in registers by a bitonic
+// network (element k sits in lane k / 2, slot k % 2; padding is INT_MAX); a longer slice's
+// body goes on the heavy list, whose slices k_csr_sort_long sorts.  Either way the slice ends
+// up in ascending end id.
 __global__ void k_csr_sort(Dev d) {
     const int body = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (body >= d.N) return;
     const int s = d.end_off[body], e = d.end_off[body + 1], n = e - s;
-    if (n <= 64) {
+    if (n > HEAVY_ENDS) {
+        if (lane == 0) d.heavy[atomicAdd(&d.ctr[C_NHEAVY], 1)] = body;
+        return;
+    }
+    {
         int v0 = (2 * lane < n) ? d.end_id[s + 2 * lane] : 0x7fffffff;
         int v1 = (2 * lane + 1 < n) ? d.end_id[s + 2 * lane + 1] : 0x7fffffff;
         for (int size = 2; size <= 64; size <<= 1) {
@@ -178,13 +183,6 @@ __global__ void k_csr_sort(Dev d) {
         }
         if (2 * lane < n) d.end_id[s + 2 * lane] = v0;
         if (2 * lane + 1 < n) d.end_id[s + 2 * lane + 1] = v1;
-    } else if (lane == 0) {
-        for (int a = s + 1; a < e; ++a) {
-            int v = d.end_id[a];
-            int k = a - 1;
-            while (k >= s && d.end_id[k] > v) { d.end_id[k + 1] = d.end_id[k]; --k; }
-            d.end_id[k + 1] = v;
-        }
     }
     __syncwarp();
     for (int p = s + lane; p < e; p += 32) {
@@ -194,6 +192,79 @@ __global__ void k_csr_sort(Dev d) {
         const float4 x = (id & 1) ? d.bxj[bond] : d.bxi[bond];
         d.end_x[p] = make_float4(x.x, x.y, x.z, 0.f);
     }
+}
+
+// The heavy bodies' slices, one block per body: runs of up to LONG_SMEM ends are sorted by a
+// bitonic network in shared memory (padded with INT_MAX to a power of two); longer slices
+// then merge their sorted runs pairwise, run length doubling, each end placed at its index in
+// its run plus its rank in the partner run (a binary search; ids are unique), ping-ponging
+// through the end-record buffer (unused at this stage) as scratch.
+constexpr int LONG_T = 1024;
+constexpr int LONG_SMEM = 32768;  // ints of dynamic shared memory (128 KB)
+
+__global__ void __launch_bounds__(LONG_T) k_csr_sort_long(Dev d) {
+    extern __shared__ int key[];
+    const int nheavy = d.ctr[C_NHEAVY];
+    for (int h = blockIdx.x; h < nheavy; h += gridDim.x) {
+        const int body = d.heavy[h];
+        const int s = d.end_off[body], e = d.end_off[body + 1], n = e - s;
+        for (int r0 = 0; r0 < n; r0 += LONG_SMEM) {
+            const int rn = min(LONG_SMEM, n - r0);
+            int m = 2;
+            while (m < rn) m <<= 1;
+            for (int k = threadIdx.x; k < m; k += LONG_T) key[k] = k < rn ? d.end_id[s + r0 + k] : 0x7fffffff;
+            __syncthreads();
+            for (int size = 2; size <= m; size <<= 1) {
+                for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                    for (int k = threadIdx.x; k < m; k += LONG_T) {
+                        const int l = k ^ stride;
+                        if (l > k) {
+                            const bool up = (k & size) == 0;
+                            const int a = key[k], b = key[l];
+                            if ((a > b) == up) { key[k] = b; key[l] = a; }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            for (int k = threadIdx.x; k < rn; k += LONG_T) d.end_id[s + r0 + k] = key[k];
+            __syncthreads();
+        }
+        int* src = d.end_id + s;
+        int* dst = reinterpret_cast<int*>(d.ends) + s;  // 4 ints per end slot; slots s..e-1 used
+        for (int R = LONG_SMEM; R < n; R <<= 1) {
+            for (int k = threadIdx.x; k < n; k += LONG_T) {
+                const int run = k / R, start = run * R, pstart = (run ^ 1) * R;
+                const int plen = max(0, min(R, n - pstart));
+                const int v = src[k];
+                int lo = 0, hi = plen;  // elements of the partner run below v
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (src[pstart + mid] < v) lo = mid + 1; else hi = mid;
+                }
+                dst[min(start, pstart) + (k - start) + lo] = v;
+            }
+            __syncthreads();
+            int* t = src; src = dst; dst = t;
+        }
+        if (src != d.end_id + s) {
+            for (int k = threadIdx.x; k < n; k += LONG_T) d.end_id[s + k] = src[k];
+            __syncthreads();
+        }
+        for (int p = s + threadIdx.x; p < e; p += LONG_T) {
+            const int id = d.end_id[p];
+            const int bond = id >> 1;
+            d.end_pos[id] = p;
+            const float4 x = (id & 1) ? d.bxj[bond] : d.bxi[bond];
+            d.end_x[p] = make_float4(x.x, x.y, x.z, 0.f);
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t setup_csr_kernels() {
+    return cudaFuncSetAttribute(k_csr_sort_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                LONG_SMEM * (int)sizeof(int));
 }
 
 // per-group residual sqrt(sum over the group's bodies of |q^{k+1} - q^k|^2): one block of
@@ -230,13 +301,15 @@ void launch_drive_update(const Dev& d, cudaStream_t st, long long* launches) {
 }
 
 void launch_csr(const Dev& d, cudaStream_t st, long long* launches) {
+    cudaMemsetAsync(d.ctr + C_NHEAVY, 0, sizeof(int), st);
     cudaMemsetAsync(d.end_cnt, 0, sizeof(int) * d.N, st);
     cudaMemsetAsync(d.end_cur, 0, sizeof(int) * d.N, st);
     k_csr_count<<<nblk(d.cap_bonds), ST_T, 0, st>>>(d);
     scan_exclusive(d.end_cnt, d.end_off, nullptr, d.N, d.scan_scratch, st, launches);
     k_csr_fill<<<nblk(d.cap_bonds), ST_T, 0, st>>>(d);
     k_csr_sort<<<nblk(d.N * 32), ST_T, 0, st>>>(d);
-    *launches += 3;
+    k_csr_sort_long<<<152, LONG_T, LONG_SMEM * sizeof(int), st>>>(d);
+    *launches += 4;
 }
 
 void launch_finalize(const Dev& d, const float4* q_fin, cudaStream_t st, long long* launches) {

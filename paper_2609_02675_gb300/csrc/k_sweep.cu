@@ -10,13 +10,13 @@
 //            structure of H (Eq. 20, 23-24: H = P (G (x) I3) P^T with G the 4x4
 //            diag(m, Pi) + sum w [1;x][1;x]^T), the 4x3 system G dX = M(s - q^k) + sum
 //            [1;x] f'^T; factors G by Cholesky (the 12x12 Cholesky factor is L (x) I3),
-//            solves the three right-hand sides, then takes the rotation of A^{k+1/2} by
-//            Higham's scaled Newton iteration for the polar decomposition
-//            (X <- (z X + X^-T / z)/2, z = |det X|^(-1/3)); a near-singular or reflected
-//            A falls back to an eigen-decomposition of A^T A with the proper-rotation
-//            sign fix.  FP32, except bodies whose 4x4 factorisation is ill-conditioned
-//            (statically flagged, or a Cholesky pivot below 1e-4 of its diagonal): those
-//            re-gather and factor in FP64.
+//            solves the three right-hand sides, then takes the rotation of A^{k+1/2}
+//            (the polar decomposition of sweep_math.cuh: Newton-Schulz, with Higham's
+//            scaled Newton iteration and an eigen-decomposition of A^T A as fallbacks).
+//            FP32, except bodies whose 4x4 factorisation is ill-conditioned (statically
+//            flagged, or a Cholesky pivot below 1e-4 of its diagonal): those re-gather and
+//            factor in an extended type -- double-float on the FP32 pipes (precision
+//            policy 1), or FP64 (policy 2).
 #include "sweep_math.cuh"
 
 namespace pabd {
@@ -24,6 +24,7 @@ namespace pabd {
 constexpr int BOND_T = 256;
 constexpr int SOLVE_T = 128;
 
+template <class X>
 __global__ void __launch_bounds__(BOND_T) k_bond(Dev d, const float4* __restrict__ q, int it) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= d.ctr[C_NBONDS]) return;
@@ -33,13 +34,13 @@ __global__ void __launch_bounds__(BOND_T) k_bond(Dev d, const float4* __restrict
     ld_q(q, m.x, c, A);
     const int4 mm = make_int4(m.x, m.y, m.z, b);
     const int fi = d.bflags[m.x], fj = m.y >= 0 ? d.bflags[m.y] : BF_PINNED;
-    const bool dbl = d.p.precision_policy && ((fi | fj) & BF_FP64);
+    const bool dbl = d.p.precision_policy == 3 || (d.p.precision_policy && ((fi | fj) & BF_FP64));
     // a bond between two fixed ends is advanced by the final update alone (as in the sweep kernels)
     const bool writer = !(fi & BF_PINNED) || !(fj & BF_PINNED);
     float w, f[3];
     if (dbl) {
-        double fd[3];
-        w = (float)end_force<double>(d, q, m.x, c, A, mm, xi, xj, it, writer, fd);
+        X fd[3];
+        w = (float)end_force<X>(d, q, m.x, c, A, mm, xi, xj, it, writer, fd);
         f[0] = (float)fd[0]; f[1] = (float)fd[1]; f[2] = (float)fd[2];
     } else {
         w = end_force<float>(d, q, m.x, c, A, mm, xi, xj, it, writer, f);
@@ -49,35 +50,56 @@ __global__ void __launch_bounds__(BOND_T) k_bond(Dev d, const float4* __restrict
     if (p1 >= 0) d.ends[p1] = make_float4(w, -f[0], -f[1], -f[2]);
 }
 
-// one body per group of L lanes; lane l adds the body's ends l, l + L, ... (float records)
-template <int L>
-__global__ void __launch_bounds__(SOLVE_T) k_solve(Dev d, const float4* __restrict__ qi, float4* __restrict__ qo,
-                                                   int last) {
+// one body per group of L lanes; lane l adds the body's ends l, l + L, ... (float records).
+// The first `light` blocks take the bodies with at most HEAVY_ENDS ends; the HEAVY_BLOCKS
+// blocks after them take the heavy bodies, a block each.
+template <int L, class X>
+__global__ void __launch_bounds__(SOLVE_T, 4) k_solve(Dev d, const float4* __restrict__ qi, float4* __restrict__ qo,
+                                                   int last, int light) {
+    if ((int)blockIdx.x >= light) {
+        heavy_role<X>(d, blockIdx.x - light, qi, qo, last,
+            [&](int, auto& s, const float*, const float*, const float* xs, int e0, int e1, int ln) {
+                for (int p = e0 + ln; p < e1; p += 32) sys_add(s, d.ends[p], d.end_x[p], xs);
+            },
+            [&](int, auto& s, const float*, const float*, const float* xs, int e0, int e1, int t) {
+                for (int p = e0 + t; p < e1; p += HEAVY_T) sys_add(s, d.ends[p], d.end_x[p], xs);
+            });
+        return;
+    }
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int b = tid / L, lane = tid & (L - 1);
     if (b >= d.N) return;
-    solve_body<L>(d, b, lane, lane_mask<L>(), qi, qo, last, [&](auto& s, const float*, const float*, int e0, int e1) {
-        for (int p = e0 + lane; p < e1; p += L) sys_add(s, d.ends[p], d.end_x[p]);
+    solve_body<L, X>(d, b, lane, lane_mask<L>(), qi, qo, last,
+                     [&](auto& s, const float*, const float*, const float* xs, int e0, int e1) {
+        for (int p = e0 + lane; p < e1; p += L) sys_add(s, d.ends[p], d.end_x[p], xs);
     });
 }
 
 void launch_bond(const Dev& d, const float4* q, int it, cudaStream_t st, long long* launches) {
     const int n = d.cap_bonds > 0 ? d.cap_bonds : 1;
-    k_bond<<<(n + BOND_T - 1) / BOND_T, BOND_T, 0, st>>>(d, q, it);
+    if (d.p.precision_policy == 2) k_bond<double><<<(n + BOND_T - 1) / BOND_T, BOND_T, 0, st>>>(d, q, it);
+    else k_bond<df><<<(n + BOND_T - 1) / BOND_T, BOND_T, 0, st>>>(d, q, it);
     *launches += 1;
 }
 
 void launch_solve(const Dev& d, const float4* q_in, float4* q_out, int last, int lanes, cudaStream_t st,
                   long long* launches) {
+    static_assert(SOLVE_T == HEAVY_T, "the solve launch's blocks are the heavy bodies' blocks");
     const long long n = (long long)(d.N > 0 ? d.N : 1) * lanes;
-    const int grid = (int)((n + SOLVE_T - 1) / SOLVE_T);
-    if (last) cudaMemsetAsync(d.ctr + C_FP64DYN, 0, sizeof(int), st);
+    const int light = (int)((n + SOLVE_T - 1) / SOLVE_T);
+    const int grid = light + HEAVY_BLOCKS;
+    const bool f64 = d.p.precision_policy == 2;
     switch (lanes) {
-        case 1: k_solve<1><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, last); break;
-        case 2: k_solve<2><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, last); break;
-        case 4: k_solve<4><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, last); break;
-        case 8: k_solve<8><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, last); break;
-        default: k_solve<16><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, last); break;
+        case 1: f64 ? k_solve<1, double><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, last, light)
+                    : k_solve<1, df><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, last, light); break;
+        case 2: f64 ? k_solve<2, double><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, last, light)
+                    : k_solve<2, df><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, last, light); break;
+        case 4: f64 ? k_solve<4, double><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, last, light)
+                    : k_solve<4, df><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, last, light); break;
+        case 8: f64 ? k_solve<8, double><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, last, light)
+                    : k_solve<8, df><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, last, light); break;
+        default: f64 ? k_solve<16, double><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, last, light)
+                     : k_solve<16, df><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, last, light); break;
     }
     *launches += 1;
 }
@@ -104,13 +126,11 @@ __global__ void k_al_final(Dev d, const float4* __restrict__ q) {
     const int4 m = d.bmeta[b];
     if (m.z != K_AL) return;
     const float4 xi = d.bxi[b], xj = d.bxj[b];
-    float c[3], A[9], yi[3], yj[3];
-    ld_q(q, m.x, c, A);
-    world_pt_t(c, A, xi, yi);
-    if (m.y >= 0) { ld_q(q, m.y, c, A); world_pt_t(c, A, xj, yj); }
-    else { yj[0] = xj.x; yj[1] = xj.y; yj[2] = xj.z; }
-    const float r0 = yj[0] - yi[0], r1 = yj[1] - yi[1], r2 = yj[2] - yi[2];
-    const float cc = sqrtf(r0 * r0 + r1 * r1 + r2 * r2) - xj.w;
+    float ci[3], Ai[9], cj[3], Aj[9], r[3];
+    ld_q(q, m.x, ci, Ai);
+    ld_q_or_zero(q, m.y, cj, Aj);
+    bond_vec_dot2(ci, Ai, xi, cj, Aj, xj, m.y < 0, r);
+    const float cc = sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]) - xj.w;
     const int it = d.p.n_iter;
     const float beta = d.al_par[b].y;
     float2* out = (it & 1) ? d.al_st1 : d.al_st0;

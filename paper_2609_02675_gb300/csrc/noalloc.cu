@@ -22,7 +22,8 @@ constexpr size_t OFF_BOFF = OFF_BCUR + al(sizeof(int) * NA_TABLE);
 constexpr size_t OFF_ITEMS = OFF_BOFF + al(sizeof(int) * (NA_TABLE + 1));
 constexpr size_t OFF_PCNT = OFF_ITEMS + al(sizeof(int) * NA_MAX);
 constexpr size_t OFF_POFF = OFF_PCNT + al(sizeof(int) * NA_MAX);
-constexpr size_t OFF_CTR = OFF_POFF + al(sizeof(int) * (NA_MAX + 1));
+constexpr size_t OFF_LARGE = OFF_POFF + al(sizeof(int) * (NA_MAX + 1));
+constexpr size_t OFF_CTR = OFF_LARGE + al(sizeof(int) * NA_MAX);
 constexpr size_t OFF_SCAN = OFF_CTR + al(sizeof(int) * C_COUNT);
 constexpr size_t SCAN_INTS = NA_TABLE / 4096 + 2;  // block totals of the largest scan
 constexpr size_t NA_BYTES = OFF_SCAN + al(sizeof(int) * SCAN_INTS);
@@ -33,7 +34,7 @@ unsigned char* g_addr[MAX_DEVICES] = {nullptr};
 
 }  // namespace
 
-// the scratch (about 1.4 MB); device code could name it directly, host code needs its address
+// the scratch (about 1.5 MB); device code could name it directly, host code needs its address
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
 extern "C" pabd_status pabd_broadphase_noalloc(const float* q, const float* vel, const float* he,
@@ -82,6 +83,7 @@ extern "C" pabd_status pabd_broadphase_noalloc(const float* q, const float* vel,
     d.pair_cnt = (int*)(base + OFF_PCNT);
     d.pair_off = (int*)(base + OFF_POFF);
     d.ctr = (int*)(base + OFF_CTR);
+    d.large_ids = (int*)(base + OFF_LARGE);
     d.scan_scratch = (int*)(base + OFF_SCAN);
     d.pairs = (int2*)pairs_out;
     long long launches = 0;

@@ -135,8 +135,10 @@ void enqueue_step(pabd_scene* s, long long* launches, const cudaEvent_t* ev = nu
     float4* nxt = d.qb;
     auto two_launch = [&]() {
         for (int it = 0; it < d.p.n_iter; ++it) {
+            const int last = it == d.p.n_iter - 1;
             launch_bond(d, cur, it, s->st, launches);
-            launch_solve(d, cur, nxt, it == d.p.n_iter - 1, s->lanes, s->st, launches);
+            if (last) cudaMemsetAsync(d.ctr + C_FP64DYN, 0, sizeof(int), s->st);
+            launch_solve(d, cur, nxt, last, s->lanes, s->st, launches);
             float4* t = cur; cur = nxt; nxt = t;
         }
     };
@@ -154,6 +156,7 @@ void enqueue_step(pabd_scene* s, long long* launches, const cudaEvent_t* ev = nu
     } else if (s->mode == 2) {
         launch_end_records(d, s->st, launches);
         for (int it = 0; it < d.p.n_iter; ++it) {
+            if (it == d.p.n_iter - 1) cudaMemsetAsync(d.ctr + C_FP64DYN, 0, sizeof(int), s->st);
             launch_sweep_one(d, cur, nxt, it, s->lanes, s->st, launches);
             float4* t = cur; cur = nxt; nxt = t;
         }
@@ -167,9 +170,9 @@ void enqueue_step(pabd_scene* s, long long* launches, const cudaEvent_t* ev = nu
 }
 
 // Launch-shape autotuner for the fused sweep: with the scene's step-0 collision, CSR and
-// predictor in place (none of them changes q^n), time the sweep for each block size at the
-// largest co-resident grid the work can use; keep the fastest.  The shape never changes the
-// results (each body's arithmetic does not depend on which block runs it).
+// predictor in place (none of them changes q^n), time the sweep for each candidate grid of
+// HEAVY_T-thread blocks; keep the fastest.  The shape never changes the results (each body's
+// arithmetic does not depend on which block runs it).
 pabd_status autotune_sweep(pabd_scene* s) {
     Dev& d = s->d;
     long long lc = 0;
@@ -178,17 +181,22 @@ pabd_status autotune_sweep(pabd_scene* s) {
     launch_csr(d, s->st, &lc);
     launch_predict(d, s->st, &lc);
     CK(cudaGetLastError());
-    const int blocks[] = {64, 128, 256, 512};
+    // blocks of HEAVY_T threads (a heavy body takes a whole block); the grid is tuned: all
+    // co-resident blocks, or the blocks the light bodies fill, or half or a quarter of those,
+    // never fewer than the HEAVY_BLOCKS blocks of the heavy role
+    const int bs = HEAVY_T;
+    const int maxg = fused_max_blocks(s->lanes, bs, d.p.precision_policy == 2);
+    const long long need = std::max<long long>(1, ((long long)d.N * s->lanes + bs - 1) / bs);
+    std::vector<int> grids;
+    for (long long g : {(long long)maxg, std::min<long long>(need, maxg), (long long)maxg / 2, (long long)maxg / 4}) {
+        g = std::max<long long>(g, HEAVY_BLOCKS);
+        if (g <= maxg && std::find(grids.begin(), grids.end(), (int)g) == grids.end()) grids.push_back((int)g);
+    }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best = 1e30f;
-    for (int bs : blocks) {
-        int maxg = fused_max_blocks(s->lanes, bs);
-        if (maxg <= 0) continue;
-        long long need = ((long long)d.N * s->lanes + bs - 1) / bs;
-        int grid = (int)std::min<long long>(need, maxg);
-        if (grid < 1) grid = 1;
+    for (int grid : grids) {
         float tot = 0.f;
         bool ok = true;
         for (int r = 0; r < 4 && ok; ++r) {
@@ -234,6 +242,7 @@ pabd_status finalize_scene(pabd_scene* s) {
     p.gd = (float)ds.ground_d;
     p.mu = (float)ds.mu; p.c_kappa = (float)ds.c_kappa; p.d_hat_rel = (float)ds.d_hat_rel; p.margin = (float)ds.margin;
     p.n_iter = ds.n_iter; p.has_ground = ds.has_ground; p.project = ds.project; p.body_contacts = ds.body_contacts;
+    if (ds.precision_policy < 0 || ds.precision_policy > 3) return PABD_ERR_ARG;
     p.precision_policy = ds.precision_policy;
     // capacities
     // the two-level scans cover 4096 x 4096 values; bond ends are counted in int.  Defaults:
@@ -257,7 +266,6 @@ pabd_status finalize_scene(pabd_scene* s) {
     // host staging
     std::vector<float4> qn(3 * N), vel(N), omg(N), quat(N), mass(N), he(N);
     std::vector<int> flags(N), group(N), group_off(d.G + 1, 0), large;
-    std::vector<double> wsum(N, 0.0);
     const float dr = (float)ds.d_hat_rel;
     for (int b = 0; b < N; ++b) {
         const pabd_body_desc& bd = s->bodies[b];
@@ -287,17 +295,80 @@ pabd_status finalize_scene(pabd_scene* s) {
     }
     for (int g = 1; g <= d.G; ++g) if (group_off[g] < group_off[g - 1]) group_off[g] = group_off[g - 1];
     d.Nlarge = (int)large.size();
-    // static FP64 flag: sum of bond weights against the smallest mass-matrix diagonal
-    for (const HostBond& hb : s->bonds) {
-        if (hb.i >= 0) wsum[hb.i] += hb.w;
-        if (hb.j >= 0) wsum[hb.j] += hb.w;
+    // cap of the grid cell: 1.25 x the widest box of a grid body at rest (any orientation:
+    // twice the half-extent norm, plus twice dhat + margin); faster bodies whose inflated box
+    // outgrows it leave the grid for that step
+    double cell = 0.0;
+    for (int b = 0; b < N; ++b) {
+        if (flags[b] & BF_LARGE) continue;
+        const pabd_body_desc& bd = s->bodies[b];
+        const double hn = std::sqrt(bd.he[0] * bd.he[0] + bd.he[1] * bd.he[1] + bd.he[2] * bd.he[2]);
+        const double dh = ds.d_hat_rel * 2.0 * std::min(std::min(bd.he[0], bd.he[1]), bd.he[2]);
+        cell = std::max(cell, 2.0 * hn + 2.0 * (dh + ds.margin));
     }
-    s->fp64_bodies = 0;
+    p.cell = (float)(1.25 * cell);
+    // Expansion point of each body's system (sys_init): x_s = sum w x / (m + sum w) over the
+    // ends of its static bonds (w = h^2 kappa; a drive's moving anchor at its rest angle).
+    // Static extended-precision flag (reading R18): the FP64 Cholesky of the diagonally scaled
+    // static-only system about x_s has a pivot below 1e-2 of its diagonal (ten times the
+    // dynamic test's margin, since contacts add to the system at run time).
+    std::vector<double> sw(N, 0.0), swx(3 * (size_t)N, 0.0);
+    for (const HostBond& hb : s->bonds) {
+        if (hb.i >= 0) { sw[hb.i] += hb.w; for (int k = 0; k < 3; ++k) swx[3 * hb.i + k] += hb.w * hb.xi[k]; }
+        if (hb.j >= 0) { sw[hb.j] += hb.w; for (int k = 0; k < 3; ++k) swx[3 * hb.j + k] += hb.w * hb.xj[k]; }
+    }
+    std::vector<float4> xs(N, make_float4(0, 0, 0, 0));
+    std::vector<double> xsd(3 * (size_t)N, 0.0);
+    for (int b = 0; b < N; ++b) {
+        if (flags[b] & BF_PINNED) continue;
+        const double m = s->bodies[b].mass;
+        for (int k = 0; k < 3; ++k) xsd[3 * b + k] = swx[3 * b + k] / (m + sw[b]);
+        xs[b] = make_float4((float)xsd[3 * b], (float)xsd[3 * b + 1], (float)xsd[3 * b + 2], 0.f);
+        if (xs[b].x != 0.f || xs[b].y != 0.f || xs[b].z != 0.f) flags[b] |= BF_SHIFT;
+        // the shifted expansion point as the device uses it (rounded to FP32)
+        for (int k = 0; k < 3; ++k) xsd[3 * b + k] = k == 0 ? xs[b].x : (k == 1 ? xs[b].y : xs[b].z);
+    }
+    std::vector<double> G(10 * (size_t)N, 0.0);
     for (int b = 0; b < N; ++b) {
         const pabd_body_desc& bd = s->bodies[b];
-        double m = bd.mass;
-        double pmin = m * std::fmin(std::fmin(bd.he[0] * bd.he[0], bd.he[1] * bd.he[1]), bd.he[2] * bd.he[2]) / 3.0;
-        if (!(flags[b] & BF_PINNED) && wsum[b] > 1e3 * std::fmin(m, pmin)) { flags[b] |= BF_FP64; s->fp64_bodies++; }
+        const double m = bd.mass, *x = &xsd[3 * b];
+        double* g = &G[10 * (size_t)b];
+        g[0] = m; g[1] = -m * x[0]; g[2] = -m * x[1]; g[3] = -m * x[2];
+        g[4] = m * bd.he[0] * bd.he[0] / 3.0 + m * x[0] * x[0]; g[5] = m * x[0] * x[1]; g[6] = m * x[0] * x[2];
+        g[7] = m * bd.he[1] * bd.he[1] / 3.0 + m * x[1] * x[1]; g[8] = m * x[1] * x[2];
+        g[9] = m * bd.he[2] * bd.he[2] / 3.0 + m * x[2] * x[2];
+    }
+    auto add_end = [&](int b, double w, const double* p) {
+        if (b < 0) return;
+        const double z[4] = {1.0, p[0] - xsd[3 * b], p[1] - xsd[3 * b + 1], p[2] - xsd[3 * b + 2]};
+        double* g = &G[10 * (size_t)b];
+        int k = 0;
+        for (int r = 0; r < 4; ++r)
+            for (int c = r; c < 4; ++c) g[k++] += w * z[r] * z[c];
+    };
+    for (const HostBond& hb : s->bonds) { add_end(hb.i, hb.w, hb.xi); add_end(hb.j, hb.w, hb.xj); }
+    s->fp64_bodies = 0;
+    for (int b = 0; b < N; ++b) {
+        if (flags[b] & BF_PINNED) continue;
+        const double* g = &G[10 * (size_t)b];
+        const double M[4][4] = {{g[0], g[1], g[2], g[3]}, {g[1], g[4], g[5], g[6]},
+                                {g[2], g[5], g[7], g[8]}, {g[3], g[6], g[8], g[9]}};
+        double Lm[4][4] = {{0}};
+        double worst = 1.0;
+        for (int i = 0; i < 4; ++i) {
+            for (int j = 0; j <= i; ++j) {
+                double t = M[i][j];
+                for (int k = 0; k < j; ++k) t -= Lm[i][k] * Lm[j][k];
+                if (i == j) {
+                    const double ratio = t / M[i][i];
+                    worst = std::min(worst, ratio);
+                    Lm[i][i] = std::sqrt(std::max(t, 1e-300));
+                } else {
+                    Lm[i][j] = t / Lm[j][j];
+                }
+            }
+        }
+        if (!(worst >= 1e-2)) { flags[b] |= BF_FP64; s->fp64_bodies++; }
     }
     // static bonds
     std::vector<int4> bmeta(Nc);
@@ -353,15 +424,15 @@ pabd_status finalize_scene(pabd_scene* s) {
     bool ok = true;
     ok &= alloc_arr(s, d.qn, 3 * N) && alloc_arr(s, d.qa, 3 * N) && alloc_arr(s, d.qb, 3 * N) && alloc_arr(s, d.sq, 3 * N);
     ok &= alloc_arr(s, d.vel, N) && alloc_arr(s, d.omg, N) && alloc_arr(s, d.quat, N) && alloc_arr(s, d.qstar, N);
-    ok &= alloc_arr(s, d.mass, N) && alloc_arr(s, d.he, N);
+    ok &= alloc_arr(s, d.mass, N) && alloc_arr(s, d.he, N) && alloc_arr(s, d.xs, N);
     ok &= alloc_arr(s, d.bflags, N) && alloc_arr(s, d.group, N) && alloc_arr(s, d.group_off, d.G + 1);
-    ok &= alloc_arr(s, d.large_ids, large.size());
+    ok &= alloc_arr(s, d.large_ids, N);
     ok &= alloc_arr(s, d.resid_body, N) && alloc_arr(s, d.resid_group, d.G);
     ok &= alloc_arr(s, d.bmeta, d.cap_bonds) && alloc_arr(s, d.bxi, d.cap_bonds) && alloc_arr(s, d.bxj, d.cap_bonds) &&
           alloc_arr(s, d.bn, d.cap_bonds);
     ok &= alloc_arr(s, d.drv, 3 * d.Ndrive) && alloc_arr(s, d.drv_t, d.Ndrive) && alloc_arr(s, d.drv_bond, d.Ndrive);
     ok &= alloc_arr(s, d.end_cnt, N) && alloc_arr(s, d.end_cur, N) && alloc_arr(s, d.end_off, N + 1);
-    ok &= alloc_arr(s, d.end_id, d.cap_ends) && alloc_arr(s, d.end_pos, d.cap_ends);
+    ok &= alloc_arr(s, d.end_id, d.cap_ends) && alloc_arr(s, d.end_pos, d.cap_ends) && alloc_arr(s, d.heavy, N);
     ok &= alloc_arr(s, d.ends, d.cap_ends) && alloc_arr(s, d.end_x, d.cap_ends);
     ok &= alloc_arr(s, d.rec_m, d.cap_ends) && alloc_arr(s, d.rec_a, d.cap_ends) && alloc_arr(s, d.rec_b, d.cap_ends);
     ok &= alloc_arr(s, d.gbar, 2);
@@ -392,10 +463,10 @@ pabd_status finalize_scene(pabd_scene* s) {
     CK(up(d.quat, quat.data(), sizeof(float4) * N));
     CK(up(d.mass, mass.data(), sizeof(float4) * N));
     CK(up(d.he, he.data(), sizeof(float4) * N));
+    CK(up(d.xs, xs.data(), sizeof(float4) * N));
     CK(up(d.bflags, flags.data(), sizeof(int) * N));
     CK(up(d.group, group.data(), sizeof(int) * N));
     CK(up(d.group_off, group_off.data(), sizeof(int) * (d.G + 1)));
-    CK(up(d.large_ids, large.data(), sizeof(int) * large.size()));
     CK(up(d.bmeta, bmeta.data(), sizeof(int4) * Nc));
     CK(up(d.bxi, bxi.data(), sizeof(float4) * Nc));
     CK(up(d.bxj, bxj.data(), sizeof(float4) * Nc));
@@ -420,7 +491,16 @@ pabd_status finalize_scene(pabd_scene* s) {
     CK(cudaStreamSynchronize(st));
 
     // lanes per body from the descriptor; fused sweep block / grid from a timing sweep
-    const int L = ds.sweep_lanes ? ds.sweep_lanes : 8;
+    CK(setup_csr_kernels());
+
+    // lanes per body: given, or from the body count -- the largest of 16, 8, 4, 2, 1 lanes
+    // with lanes * N <= 2^17 (the measured optimum on piles of 4 k to 1 M bodies and on the
+    // 140 k-body trees).  A function of N only, so a scene's results never depend on timing.
+    int L = ds.sweep_lanes;
+    if (L == 0) {
+        L = 16;
+        while (L > 1 && (long long)L * N > 131072) L >>= 1;
+    }
     if (L != 1 && L != 2 && L != 4 && L != 8 && L != 16) return PABD_ERR_ARG;
     s->lanes = L;
     // sweep mode: 1 two launches per sweep, 2 one launch per sweep, 3 fused persistent;
@@ -944,6 +1024,8 @@ pabd_status pabd_get_info(pabd_scene* s, pabd_info* info) {
     info->sweep_block = s->sw_block;
     info->sweep_grid = s->sw_grid;
     info->coop_fallbacks = s->coop_fallbacks;
+    info->heavy_bodies = c[C_NHEAVY];
+    info->fp64_dynamic = c[C_FP64DYN];
     return PABD_OK;
 }
 

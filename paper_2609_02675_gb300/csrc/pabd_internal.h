@@ -18,7 +18,8 @@ enum BondKind { K_SPHERICAL = 0, K_SPRING = 1, K_ELASTIC_NL = 2, K_DRIVE = 4, K_
 
 enum StatusBits { ST_CAPACITY = 1, ST_DIVERGED = 2, ST_TIMEOUT = 4 };
 
-enum BodyFlags { BF_PINNED = 1, BF_FP64 = 2, BF_LARGE = 4 };
+// BF_SHIFT: the body's system is assembled about a nonzero expansion point Dev::xs
+enum BodyFlags { BF_PINNED = 1, BF_FP64 = 2, BF_LARGE = 4, BF_SHIFT = 8 };
 
 // device counters (ints) -- one small array so that one memset resets them
 enum Counter {
@@ -29,6 +30,8 @@ enum Counter {
     C_STATUS,          // latched StatusBits (never reset by a step)
     C_CELLBITS,        // float bits of the grid cell size
     C_FP64DYN,         // bodies that switched to FP64 by the pivot test (last sweep)
+    C_NHEAVY,          // bodies with more than HEAVY_ENDS bond ends this step (list in Dev::heavy)
+    C_NLARGE,          // bodies off the grid this step (list in Dev::large_ids)
     C_COUNT
 };
 
@@ -37,9 +40,21 @@ struct Params {
     float g[3];
     float gn[3], gd;
     float mu, c_kappa, d_hat_rel, margin;
+    float cell;                 // cap of the grid cell size (0: none); wider boxes leave the grid
     int n_iter, has_ground, project, body_contacts, precision_policy;
     double h_d;
 };
+
+// A body with more than HEAVY_ENDS bond ends (a large body under a pile or a bed of grains)
+// is gathered and solved by a whole block of HEAVY_T threads instead of L lanes (the last
+// HEAVY_BLOCKS blocks of every sweep launch take the heavy bodies), and its CSR slice is
+// sorted by a block.
+constexpr int HEAVY_ENDS = 64;
+constexpr int HEAVY_T = 128;
+// of those, bodies with up to WIDE_ENDS ends are summed by one warp (32 lanes), more by the block
+constexpr int WIDE_ENDS = 256;
+// blocks appended to each sweep launch for the heavy bodies (they loop over the heavy list)
+constexpr int HEAVY_BLOCKS = 152;
 
 struct Dev {
     Params p;
@@ -51,7 +66,9 @@ struct Dev {
     float4 *vel, *omg, *quat, *qstar;
     float4 *mass;               // (m, Pi_xx, Pi_yy, Pi_zz)
     float4 *he;                 // (hx, hy, hz, dhat)
-    int *bflags, *group, *group_off, *large_ids;
+    float4 *xs;                 // expansion point of the per-body system (x, y, z, 0), see sys_init
+    int *bflags, *group, *group_off;
+    int *large_ids;             // this step's bodies off the grid (C_NLARGE of them), or null
     int *adj_off, *adj_nbr;     // sorted partners joined by user bonds (no contact), or null
     double *resid_body, *resid_group;
     // bonds
@@ -68,6 +85,7 @@ struct Dev {
     // CSR of bond ends
     int *end_cnt, *end_cur, *end_off, *end_id, *end_pos;
     float4 *ends, *end_x;
+    int *heavy;                 // ids of the bodies with more than HEAVY_ENDS ends (C_NHEAVY of them)
     // bond-end records in CSR order for the fused sweep: (i, j, type, bond), x_i (+w0), x_j (+p1)
     int4 *rec_m;
     float4 *rec_a, *rec_b;
@@ -98,6 +116,8 @@ int scan_scratch_ints(int n_cap);
 void launch_collision(const Dev& d, cudaStream_t st, long long* launches);
 void launch_broadphase(const Dev& d, cudaStream_t st, long long* launches);
 void launch_csr(const Dev& d, cudaStream_t st, long long* launches);
+// opt the CSR block sort into its 128 KB of dynamic shared memory (once per process and device)
+cudaError_t setup_csr_kernels();
 void launch_predict(const Dev& d, cudaStream_t st, long long* launches);
 void launch_bond(const Dev& d, const float4* q, int it, cudaStream_t st, long long* launches);
 // augmented Lagrangian: warm start (before the sweeps) and the update after the last sweep
@@ -109,10 +129,11 @@ void launch_finalize(const Dev& d, const float4* q_fin, cudaStream_t st, long lo
 void launch_drive_update(const Dev& d, cudaStream_t st, long long* launches);
 // fused persistent sweep (all n_iter iterations, cooperative launch); L lanes per body
 cudaError_t launch_fused_sweep(const Dev& d, int L, int block, int grid, cudaStream_t st, long long* launches);
-int fused_max_blocks(int L, int block);
+int fused_max_blocks(int L, int block, bool fp64);
 // one launch per sweep (bonds evaluated by the solve from CSR-ordered end records)
 void launch_end_records(const Dev& d, cudaStream_t st, long long* launches);
 void launch_sweep_one(const Dev& d, const float4* qi, float4* qo, int it, int L, cudaStream_t st,
                       long long* launches);
+
 
 }  // namespace pabd

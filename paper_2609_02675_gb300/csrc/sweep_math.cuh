@@ -2,9 +2,13 @@
 // k_persist.cu: the fused persistent sweep): bond split forces, the per-body 4x4 system
 // and the rotation of the local solve.  One copy, so both paths compute identical bonds.
 #pragma once
+#include "dfloat.cuh"
 #include "pabd_internal.h"
 
 namespace pabd {
+
+__device__ __forceinline__ float shfl_xor(unsigned mask, float v, int o) { return __shfl_xor_sync(mask, v, o); }
+__device__ __forceinline__ double shfl_xor(unsigned mask, double v, int o) { return __shfl_xor_sync(mask, v, o); }
 
 __device__ __forceinline__ void ld_q(const float4* __restrict__ q, int b, float* c, float* A) {
     float4 a = q[3 * b], bb = q[3 * b + 1], cc = q[3 * b + 2];
@@ -13,22 +17,19 @@ __device__ __forceinline__ void ld_q(const float4* __restrict__ q, int b, float*
     A[5] = cc.x; A[6] = cc.y; A[7] = cc.z; A[8] = cc.w;
 }
 
-__device__ __forceinline__ void world_pt(const float* c, const float* A, float4 x, float* y) {
-#pragma unroll
-    for (int k = 0; k < 3; ++k) y[k] = c[k] + A[3 * k] * x.x + A[3 * k + 1] * x.y + A[3 * k + 2] * x.z;
-}
 
 // Split force of one bond from the iterate (Eq. 15-17): returns w = h^2 phi+(d)/d and the
-// delta-form record f' of end i (end j gets -f'), see the file comment of k_sweep.cu.
-// T = float for the FP32 path; T = double for bodies on the FP64 path (the end points y
-// are then formed in double from the FP32 state, so no rounding of |y| enters f').
+// delta-form record f' of end i (end j gets -f'), see the file comment of k_sweep.cu.  Only
+// the end-to-end vector r = y_j - y_i enters (bond_vec forms it without rounding at the
+// scale of the bodies' positions).  T = float for the FP32 path; the extended type for
+// ill-conditioned bodies.
 template <class T>
-__device__ __forceinline__ T bond_force(int type, float4 xi, float4 xj, float4 nm, const T* yi, const T* yj, T* f) {
+__device__ __forceinline__ T bond_force(int type, float4 xi, float4 xj, float4 nm, const T* r, T* f) {
     T w = (T)xi.w;
     if (type == K_CONTACT || type == K_GROUND) {
         const T dhat = (T)xj.w;
         const T N[3] = {(T)nm.x, (T)nm.y, (T)nm.z};
-        T rr[3] = {yi[0] - yj[0], yi[1] - yj[1], yi[2] - yj[2]};
+        const T rr[3] = {-r[0], -r[1], -r[2]};  // y_i - y_j
         T g = N[0] * rr[0] + N[1] * rr[1] + N[2] * rr[2];
         if (g < dhat) {
             T t[3] = {rr[0] - g * N[0], rr[1] - g * N[1], rr[2] - g * N[2]};
@@ -43,7 +44,6 @@ __device__ __forceinline__ T bond_force(int type, float4 xi, float4 xj, float4 n
         }
         return w;
     }
-    T r[3] = {yj[0] - yi[0], yj[1] - yi[1], yj[2] - yi[2]};
     if (type == K_SPHERICAL || type == K_DRIVE) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) f[k] = w * r[k];
@@ -58,8 +58,10 @@ __device__ __forceinline__ T bond_force(int type, float4 xi, float4 xj, float4 n
     if (type == K_SPRING) {
         sc = w * (dd - l);                      // h^2 phi(d)
     } else {                                    // nonlinear elastic, tangent split
+        // h^2 phi(d) = (w / 3) (d^3 / l^2 - l) = (w / 3) (d - l) (d^2 + d l + l^2) / l^2: the
+        // factored form has no cancellation near the rest length
         const T il2 = T(1) / (l * l);
-        sc = (w * (T(1) / T(3))) * (dd * dd * dd * il2 - l);
+        sc = (w * (T(1) / T(3))) * ((dd - l) * ((dd * dd + dd * l + l * l) * il2));
         w = w * dd * dd * il2;
     }
 #pragma unroll
@@ -67,12 +69,25 @@ __device__ __forceinline__ T bond_force(int type, float4 xi, float4 xj, float4 n
     return w;
 }
 
+// r = y_j - y_i for end points y = c + A x, formed as (c_j - c_i) + (A_j x_j - A_i x_i): the
+// centres' difference rounds once at the scale of the bond, not of the positions, so a stiff
+// short bond far from the origin keeps its length to the precision of T.  A world end j is
+// the point x_j itself.
 template <class T>
-__device__ __forceinline__ void world_pt_t(const float* c, const float* A, float4 x, T* y) {
+__device__ __forceinline__ void bond_vec(const float* ci, const float* Ai, float4 xi, const float* cj,
+                                         const float* Aj, float4 xj, bool world_j, T* r) {
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
-        y[k] = (T)c[k] + (T)A[3 * k] * (T)x.x + (T)A[3 * k + 1] * (T)x.y + (T)A[3 * k + 2] * (T)x.z;
+    for (int k = 0; k < 3; ++k) {
+        const T ai = (T)Ai[3 * k] * (T)xi.x + (T)Ai[3 * k + 1] * (T)xi.y + (T)Ai[3 * k + 2] * (T)xi.z;
+        if (world_j) {
+            r[k] = ((T)(&xj.x)[k] - (T)ci[k]) - ai;
+        } else {
+            const T aj = (T)Aj[3 * k] * (T)xj.x + (T)Aj[3 * k + 1] * (T)xj.y + (T)Aj[3 * k + 2] * (T)xj.z;
+            r[k] = ((T)cj[k] - (T)ci[k]) + (aj - ai);
+        }
+    }
 }
+
 
 // Augmented Lagrangian distance bond at sweep `it` (Eq. 27-29): for it >= 1 first the dual
 // update from the constraint of this iterate (the primal result of sweep it - 1),
@@ -82,8 +97,7 @@ __device__ __forceinline__ void world_pt_t(const float* c, const float* A, float
 // (d kept above 1e-9), f' = w (y_j - y_i) + h^2 phi- n.  xi.w holds h^2, xj.w the rest length.
 template <class T>
 __device__ __forceinline__ T al_force(const Dev& d, int bond, int it, bool writer, float4 xi, float4 xj,
-                                      const T* yi, const T* yj, T* f) {
-    T r[3] = {yj[0] - yi[0], yj[1] - yi[1], yj[2] - yi[2]};
+                                      const T* r, T* f) {
     T dd = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
     T n[3];
     if (dd > T(0)) { T id = T(1) / dd; n[0] = r[0] * id; n[1] = r[1] * id; n[2] = r[2] * id; }
@@ -112,38 +126,90 @@ __device__ __forceinline__ T al_force(const Dev& d, int bond, int it, bool write
     return w;
 }
 
-// Force of the bond seen from body `self`: loads the other body from q, forms both end
-// points in T, evaluates the split force; returns w and writes the record of self's end.
-// `it` is the sweep index and `writer` whether this evaluation stores an augmented
-// Lagrangian bond's updated state (exactly one evaluation per bond does).
-template <class T>
-__device__ __forceinline__ T end_force(const Dev& d, const float4* __restrict__ q, int self, const float* cs,
-                                       const float* As, int4 m, float4 xa, float4 xb, int it, bool writer, T* f) {
-    const bool side_j = (m.y == self);
-    float c[3], A[9];
-    T yi[3], yj[3];
-    if (side_j) {
-        ld_q(q, m.x, c, A);
-        world_pt_t(c, A, xa, yi);
-        world_pt_t(cs, As, xb, yj);
-    } else {
-        world_pt_t(cs, As, xa, yi);
-        if (m.y >= 0) {
-            ld_q(q, m.y, c, A);
-            world_pt_t(c, A, xb, yj);
-        } else {
-            yj[0] = (T)xb.x; yj[1] = (T)xb.y; yj[2] = (T)xb.z;
+// The same vector for the FP32 path as accurately as if formed in twice the precision and
+// rounded once (Ogita, Rump and Oishi's Dot2: TwoSum / TwoProduct of every term, the errors
+// summed apart).  A stiff joint's gap is the small difference of the centres' offset and the
+// lever arms; in plain FP32 its rounding (an ulp of the lever, independently at each end)
+// reaches the forces as w times that ulp -- inconsistent between the two ends and far above
+// the joint's own resolution -- and from there the body's softly held rotations.
+__device__ __forceinline__ void bond_vec_dot2(const float* ci, const float* Ai, float4 xi, const float* cj,
+                                              const float* Aj, float4 xj, bool world_j, float* r) {
+    const float xiv[3] = {xi.x, xi.y, xi.z}, xjv[3] = {xj.x, xj.y, xj.z};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        df acc = two_sum(world_j ? xjv[k] : cj[k], -ci[k]);
+        float err = acc.lo;
+        float hi = acc.hi;
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            df p = two_prod(-Ai[3 * k + l], xiv[l]);
+            df t = two_sum(hi, p.hi);
+            hi = t.hi;
+            err = __fadd_rn(err, __fadd_rn(t.lo, p.lo));
+            if (!world_j) {
+                p = two_prod(Aj[3 * k + l], xjv[l]);
+                t = two_sum(hi, p.hi);
+                hi = t.hi;
+                err = __fadd_rn(err, __fadd_rn(t.lo, p.lo));
+            }
         }
+        r[k] = __fadd_rn(hi, err);
+    }
+}
+
+// Force of the bond seen from body `self`, given the other body's iterate (co, Ao; unused
+// when the other end is the world): forms the bond vector in T, evaluates the split force;
+// returns w and writes the record of self's end.  `it` is the sweep index and `writer`
+// whether this evaluation stores an augmented Lagrangian bond's updated state (exactly one
+// evaluation per bond does).
+template <class T>
+__device__ __forceinline__ T end_force_q(const Dev& d, const float* co, const float* Ao, int self, const float* cs,
+                                         const float* As, int4 m, float4 xa, float4 xb, int it, bool writer, T* f) {
+    const bool side_j = (m.y == self);
+    T r[3];
+    if (sizeof(T) == sizeof(float) && m.z != K_CONTACT && m.z != K_GROUND) {
+        // user bonds (stiff joints, elastic and AL bonds) in FP32: the compensated vector
+        float rf[3];
+        if (side_j) bond_vec_dot2(co, Ao, xa, cs, As, xb, false, rf);
+        else bond_vec_dot2(cs, As, xa, co, Ao, xb, m.y < 0, rf);
+        r[0] = (T)rf[0]; r[1] = (T)rf[1]; r[2] = (T)rf[2];
+    } else if (side_j) {
+        bond_vec<T>(co, Ao, xa, cs, As, xb, false, r);
+    } else {
+        bond_vec<T>(cs, As, xa, co, Ao, xb, m.y < 0, r);
     }
     T w;
     if (m.z == K_AL) {
-        w = al_force<T>(d, m.w, it, writer, xa, xb, yi, yj, f);
+        w = al_force<T>(d, m.w, it, writer, xa, xb, r, f);
     } else {
         const float4 nm = (m.z == K_CONTACT || m.z == K_GROUND) ? d.bn[m.w] : make_float4(0.f, 0.f, 0.f, 0.f);
-        w = bond_force<T>(m.z, xa, xb, nm, yi, yj, f);
+        w = bond_force<T>(m.z, xa, xb, nm, r, f);
     }
     if (side_j) { f[0] = -f[0]; f[1] = -f[1]; f[2] = -f[2]; }
     return w;
+}
+
+// the other end's body of bond record m seen from `self` (-1 for the world)
+__device__ __forceinline__ int other_body(int4 m, int self) { return m.y == self ? m.x : m.y; }
+
+// q of body o, or zeros for the world (o < 0)
+__device__ __forceinline__ void ld_q_or_zero(const float4* __restrict__ q, int o, float* c, float* A) {
+    if (o >= 0) {
+        ld_q(q, o, c, A);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) c[k] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) A[k] = 0.f;
+    }
+}
+
+template <class T>
+__device__ __forceinline__ T end_force(const Dev& d, const float4* __restrict__ q, int self, const float* cs,
+                                       const float* As, int4 m, float4 xa, float4 xb, int it, bool writer, T* f) {
+    float co[3], Ao[9];
+    ld_q_or_zero(q, other_body(m, self), co, Ao);
+    return end_force_q<T>(d, co, Ao, self, cs, As, m, xa, xb, it, writer, f);
 }
 
 // ---- 4x4 SPD system with three right-hand sides ----
@@ -154,58 +220,72 @@ struct Sys {
     T r[4][3];
 };
 
+// The system is assembled about a per-body expansion point x_s (Dev::xs; zero for most
+// bodies): with z = x - x_s the unknowns are c' = c + A x_s and A, so G = diag(m, Pi) +
+// sum w [1; x][1; x]^T becomes, exactly, T^-1 G T^-T = [m, -m x_s^T; -m x_s, Pi + m x_s x_s^T]
+// + sum w [1; z][1; z]^T and the right-hand side [R_0; R_A - x_s R_0].  Placing x_s at the
+// weighted centre of the body's stiff static bonds removes the cancellation between their
+// c and A couplings (the Schur complement of G_00), which otherwise dominates the rounding of
+// an FP32 factorisation of a stiffly jointed body; dc = dc' - dA x_s recovers the update.
 template <class T>
-__device__ __forceinline__ void sys_init(Sys<T>& s, float4 mass, const float* dc, const float* dA) {
-    s.g[0] = mass.x; s.g[1] = 0; s.g[2] = 0; s.g[3] = 0;
-    s.g[4] = mass.y; s.g[5] = 0; s.g[6] = 0;
-    s.g[7] = mass.z; s.g[8] = 0;
-    s.g[9] = mass.w;
-    const T pm[4] = {(T)mass.x, (T)mass.y, (T)mass.z, (T)mass.w};
+__device__ __forceinline__ void sys_init(Sys<T>& s, float4 mass, const float* dc, const float* dA, const float* xs) {
+    const T m = (T)mass.x;
+    const T mx[3] = {m * (T)xs[0], m * (T)xs[1], m * (T)xs[2]};
+    s.g[0] = m; s.g[1] = -mx[0]; s.g[2] = -mx[1]; s.g[3] = -mx[2];
+    s.g[4] = (T)mass.y + mx[0] * (T)xs[0]; s.g[5] = mx[0] * (T)xs[1]; s.g[6] = mx[0] * (T)xs[2];
+    s.g[7] = (T)mass.z + mx[1] * (T)xs[1]; s.g[8] = mx[1] * (T)xs[2];
+    s.g[9] = (T)mass.w + mx[2] * (T)xs[2];
+    const T pm[4] = {m, (T)mass.y, (T)mass.z, (T)mass.w};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         s.r[0][k] = pm[0] * (T)dc[k];
 #pragma unroll
-        for (int l = 0; l < 3; ++l) s.r[1 + l][k] = pm[1 + l] * (T)dA[3 * k + l];
+        for (int l = 0; l < 3; ++l) s.r[1 + l][k] = pm[1 + l] * (T)dA[3 * k + l] - mx[l] * (T)dc[k];
     }
 }
 
+// one bond end (w, f') at material point x of the body, about the expansion point x_s
 template <class T>
-__device__ __forceinline__ void sys_add(Sys<T>& s, float4 e, float4 x) {
-    const T w = e.x;
-    const T z1 = x.x, z2 = x.y, z3 = x.z;
+__device__ __forceinline__ void sys_add_t(Sys<T>& s, T w, const T* f, float4 x, const float* xs) {
+    const T z1 = (T)x.x - (T)xs[0], z2 = (T)x.y - (T)xs[1], z3 = (T)x.z - (T)xs[2];
     const T wz1 = w * z1, wz2 = w * z2, wz3 = w * z3;
     s.g[0] += w;   s.g[1] += wz1;      s.g[2] += wz2;      s.g[3] += wz3;
     s.g[4] += wz1 * z1; s.g[5] += wz1 * z2; s.g[6] += wz1 * z3;
     s.g[7] += wz2 * z2; s.g[8] += wz2 * z3;
     s.g[9] += wz3 * z3;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        s.r[0][k] += f[k];
+        s.r[1][k] += z1 * f[k];
+        s.r[2][k] += z2 * f[k];
+        s.r[3][k] += z3 * f[k];
+    }
+}
+
+// a stored end record e = (w, f') of the two-launch sweep
+template <class T>
+__device__ __forceinline__ void sys_add(Sys<T>& s, float4 e, float4 x, const float* xs) {
     const T f[3] = {(T)e.y, (T)e.z, (T)e.w};
+    sys_add_t(s, (T)e.x, f, x, xs);
+}
+
+// the update of c from the solution Y of the shifted system: dc = dc' - dA x_s
+__device__ __forceinline__ void unshift(float (*X)[3], const float* xs) {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        s.r[0][k] += f[k];
-        s.r[1][k] += z1 * f[k];
-        s.r[2][k] += z2 * f[k];
-        s.r[3][k] += z3 * f[k];
+    for (int k = 0; k < 3; ++k) X[0][k] -= xs[0] * X[1][k] + xs[1] * X[2][k] + xs[2] * X[3][k];
+}
+
+// the expansion point of body b (zero unless the body is flagged BF_SHIFT)
+__device__ __forceinline__ void ld_xs(const Dev& d, int b, int fl, float* xs) {
+    if (fl & BF_SHIFT) {
+        const float4 v = d.xs[b];
+        xs[0] = v.x; xs[1] = v.y; xs[2] = v.z;
+    } else {
+        xs[0] = xs[1] = xs[2] = 0.f;
     }
 }
 
-template <class T>
-__device__ __forceinline__ void sys_add_t(Sys<T>& s, T w, const T* f, float4 x) {
-    const T z1 = x.x, z2 = x.y, z3 = x.z;
-    const T wz1 = w * z1, wz2 = w * z2, wz3 = w * z3;
-    s.g[0] += w;   s.g[1] += wz1;      s.g[2] += wz2;      s.g[3] += wz3;
-    s.g[4] += wz1 * z1; s.g[5] += wz1 * z2; s.g[6] += wz1 * z3;
-    s.g[7] += wz2 * z2; s.g[8] += wz2 * z3;
-    s.g[9] += wz3 * z3;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        s.r[0][k] += f[k];
-        s.r[1][k] += z1 * f[k];
-        s.r[2][k] += z2 * f[k];
-        s.r[3][k] += z3 * f[k];
-    }
-}
-
-// Cholesky G = L L^T and solve; returns 1 if every pivot is at least 1e-4 of its diagonal
+// Cholesky G = L L^T and solve; returns 1 if every pivot is at least 1e-3 of its diagonal
 // (the factorisation is trusted), -1 otherwise
 __device__ __forceinline__ float inv_sqrt(float x) { return 1.f / sqrtf(x); }
 __device__ __forceinline__ double inv_sqrt(double x) { return 1.0 / sqrt(x); }
@@ -225,8 +305,9 @@ __device__ __forceinline__ T sys_solve(const Sys<T>& s, T out[4][3]) {
     T l32 = (g[8] - l30 * l20 - l31 * l21) * i2;
     T d3 = g[9] - l30 * l30 - l31 * l31 - l32 * l32;
     T i3 = inv_sqrt(d3);
-    // well conditioned iff every pivot keeps at least 1e-4 of its diagonal (no division)
-    const T lim = T(1e-4);
+    // well conditioned iff every pivot keeps at least 1e-3 of its diagonal (no division): a
+    // pivot ratio r costs about log10(1/r) digits of the FP32 solve
+    const T lim = T(1e-3);
     const T ratio = (d0 > T(0) && d1 >= lim * g[4] && d2 >= lim * g[7] && d3 >= lim * g[9]) ? T(1) : T(-1);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -400,11 +481,11 @@ __device__ __forceinline__ void sys_reduce(Sys<T>& s, unsigned mask) {
 #pragma unroll
     for (int o = 1; o < L; o <<= 1) {
 #pragma unroll
-        for (int k = 0; k < 10; ++k) s.g[k] += __shfl_xor_sync(mask, s.g[k], o);
+        for (int k = 0; k < 10; ++k) s.g[k] += shfl_xor(mask, s.g[k], o);
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
-            for (int k = 0; k < 3; ++k) s.r[r][k] += __shfl_xor_sync(mask, s.r[r][k], o);
+            for (int k = 0; k < 3; ++k) s.r[r][k] += shfl_xor(mask, s.r[r][k], o);
     }
 }
 
@@ -413,15 +494,19 @@ __device__ __forceinline__ unsigned lane_mask() {
     return (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << ((threadIdx.x & 31) & ~(L - 1)));
 }
 
+__device__ __forceinline__ void finish_body(const Dev& d, int b, int lane, float4* __restrict__ qo, int last,
+                                            const float* c, const float* A, const float (*Xs)[3]);
+
 // Global + local solve of body b by L cooperating lanes (Eq. 19-24, Sec. 4.3):
 // G dX = M (s - q^k) + sum_ends [1; x] f'^T, X^{k+1/2} = q^k + dX, A^{k+1} = rotation of
-// A^{k+1/2}; lane 0 stores q^{k+1} and the body's squared update.  gather(sys, c, A, e0, e1)
-// adds this lane's share of the body's bond ends (FP32 first; FP64 for flagged bodies or
-// when a Cholesky pivot falls below 1e-4 of its diagonal).
-template <int L, class Gather>
+// A^{k+1/2}; lane 0 stores q^{k+1} and the body's squared update.  gather(sys, c, A, xs, e0,
+// e1) adds this lane's share of the body's bond ends, about the expansion point xs: in FP32 first; in the extended type X
+// (double-float, or FP64) for flagged bodies or when an FP32 Cholesky pivot falls below 1e-3
+// of its diagonal.
+template <int L, class X, class Gather>
 __device__ __forceinline__ void solve_body(const Dev& d, int b, int lane, unsigned mask,
                                            const float4* __restrict__ qi, float4* __restrict__ qo, int last,
-                                           Gather&& gather) {
+                                           Gather&& gather, int max_ends = HEAVY_ENDS) {
     const int fl = d.bflags[b];
     if (fl & BF_PINNED) {
         if (lane == 0) {
@@ -430,6 +515,8 @@ __device__ __forceinline__ void solve_body(const Dev& d, int b, int lane, unsign
         }
         return;
     }
+    const int e0 = d.end_off[b], e1 = d.end_off[b + 1];
+    if (e1 - e0 > max_ends) return;  // solved by the heavy role (heavy_role)
     float c[3], A[9], sc[3], sA[9];
     ld_q(qi, b, c, A);
     ld_q(d.sq, b, sc, sA);
@@ -439,40 +526,49 @@ __device__ __forceinline__ void solve_body(const Dev& d, int b, int lane, unsign
 #pragma unroll
     for (int k = 0; k < 9; ++k) dA[k] = sA[k] - A[k];
     const float4 mass = d.mass[b];
-    const int e0 = d.end_off[b], e1 = d.end_off[b + 1];
-    float X[4][3];
-    bool use64 = d.p.precision_policy && (fl & BF_FP64);
-    if (!use64) {
+    float xs[3];
+    ld_xs(d, b, fl, xs);
+    float Xs[4][3];
+    bool ext = d.p.precision_policy == 3 || (d.p.precision_policy && (fl & BF_FP64));
+    if (!ext) {
         Sys<float> s;
-        if (lane == 0) sys_init(s, mass, dc, dA);
+        if (lane == 0) sys_init(s, mass, dc, dA, xs);
         else sys_zero(s);
-        gather(s, c, A, e0, e1);
+        gather(s, c, A, xs, e0, e1);
         sys_reduce<L>(s, mask);
-        const float ratio = sys_solve(s, X);
-        if (!(ratio >= 1e-4f) && d.p.precision_policy) {
-            use64 = true;
+        const float ratio = sys_solve(s, Xs);
+        if (!(ratio >= 1e-3f) && d.p.precision_policy) {
+            ext = true;
             if (last && lane == 0) atomicAdd(&d.ctr[C_FP64DYN], 1);
         }
     }
-    if (use64) {
-        Sys<double> s;
-        if (lane == 0) sys_init(s, mass, dc, dA);
+    if (ext) {
+        Sys<X> s;
+        if (lane == 0) sys_init(s, mass, dc, dA, xs);
         else sys_zero(s);
-        gather(s, c, A, e0, e1);
+        gather(s, c, A, xs, e0, e1);
         sys_reduce<L>(s, mask);
-        double Xd[4][3];
+        X Xd[4][3];
         sys_solve(s, Xd);
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
-            for (int k = 0; k < 3; ++k) X[r][k] = (float)Xd[r][k];
+            for (int k = 0; k < 3; ++k) Xs[r][k] = (float)Xd[r][k];
     }
+    unshift(Xs, xs);
+    finish_body(d, b, lane, qo, last, c, A, Xs);
+}
+
+// q^{k+1} from q^k and the solved update X: c + dc, rotation of A + dA; lane 0 stores it and,
+// on the last sweep, the body's squared update and the finiteness check
+__device__ __forceinline__ void finish_body(const Dev& d, int b, int lane, float4* __restrict__ qo, int last,
+                                            const float* c, const float* A, const float (*Xs)[3]) {
     float cn[3], An[9];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        cn[k] = c[k] + X[0][k];
+        cn[k] = c[k] + Xs[0][k];
 #pragma unroll
-        for (int l = 0; l < 3; ++l) An[3 * k + l] = A[3 * k + l] + X[1 + l][k];
+        for (int l = 0; l < 3; ++l) An[3 * k + l] = A[3 * k + l] + Xs[1 + l][k];
     }
     if (d.p.project) polar_rotation(An);
     if (lane != 0) return;
@@ -489,6 +585,121 @@ __device__ __forceinline__ void solve_body(const Dev& d, int b, int lane, unsign
     qo[3 * b] = make_float4(cn[0], cn[1], cn[2], An[0]);
     qo[3 * b + 1] = make_float4(An[1], An[2], An[3], An[4]);
     qo[3 * b + 2] = make_float4(An[5], An[6], An[7], An[8]);
+}
+
+// ---- bodies with many bond ends: one block of HEAVY_T threads per body ----
+
+// Sum the block's partial systems: a xor butterfly inside each warp, then thread 0 adds the
+// warps' sums in warp order (fixed, so the result depends only on HEAVY_T).  `buf` holds one
+// system per warp (as doubles, wide enough for every T).  The total is valid in thread 0.
+template <class T>
+__device__ __forceinline__ void block_reduce(Sys<T>& s, Sys<T>* buf) {
+    sys_reduce<32>(s, 0xffffffffu);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) buf[w] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < HEAVY_T / 32; ++k) {
+#pragma unroll
+            for (int i = 0; i < 10; ++i) s.g[i] += buf[k].g[i];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) s.r[r][i] += buf[k].r[r][i];
+        }
+    }
+    __syncthreads();
+}
+
+// Global + local solve of body b (more than HEAVY_ENDS ends) by the whole block: thread t
+// gathers ends t, t + HEAVY_T, ...; FP32 first, the extended type X where ill-conditioned
+// (same rule as solve_body); thread 0 solves, projects and stores.  Every thread of the block
+// must call it with the same b.
+template <class X, class Gather>
+__device__ __forceinline__ void solve_heavy(const Dev& d, int b, const float4* __restrict__ qi,
+                                            float4* __restrict__ qo, int last, Gather&& gather) {
+    __shared__ Sys<double> buf_raw[HEAVY_T / 32];
+    __shared__ int s_ext;
+    const int t = threadIdx.x;
+    const int fl = d.bflags[b];
+    const int e0 = d.end_off[b], e1 = d.end_off[b + 1];
+    float c[3], A[9], sc[3], sA[9];
+    ld_q(qi, b, c, A);
+    ld_q(d.sq, b, sc, sA);
+    float dc[3], dA[9];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) dc[k] = sc[k] - c[k];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) dA[k] = sA[k] - A[k];
+    const float4 mass = d.mass[b];
+    float xs[3];
+    ld_xs(d, b, fl, xs);
+    float Xs[4][3];
+    if (t == 0) s_ext = d.p.precision_policy == 3 || (d.p.precision_policy && (fl & BF_FP64));
+    __syncthreads();
+    if (!s_ext) {
+        Sys<float> s;
+        if (t == 0) sys_init(s, mass, dc, dA, xs);
+        else sys_zero(s);
+        gather(s, c, A, xs, e0, e1);
+        block_reduce(s, reinterpret_cast<Sys<float>*>(buf_raw));
+        if (t == 0) {
+            const float ratio = sys_solve(s, Xs);
+            if (!(ratio >= 1e-3f) && d.p.precision_policy) {
+                s_ext = 1;
+                if (last) atomicAdd(&d.ctr[C_FP64DYN], 1);
+            }
+        }
+        __syncthreads();
+    }
+    if (s_ext) {
+        Sys<X> s;
+        if (t == 0) sys_init(s, mass, dc, dA, xs);
+        else sys_zero(s);
+        gather(s, c, A, xs, e0, e1);
+        block_reduce(s, reinterpret_cast<Sys<X>*>(buf_raw));
+        if (t == 0) {
+            X Xd[4][3];
+            sys_solve(s, Xd);
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) Xs[r][k] = (float)Xd[r][k];
+        }
+    }
+    if (t == 0) {
+        unshift(Xs, xs);
+        finish_body(d, b, 0, qo, last, c, A, Xs);
+    }
+    __syncthreads();  // the shared buffers are reused by the block's next body
+}
+
+// The heavy role of a sweep launch's extra blocks (HEAVY_T threads each, block index hb of
+// HEAVY_BLOCKS): the bodies on the heavy list with up to WIDE_ENDS ends, one warp each
+// (32-lane butterfly, gather_w), then those with more, one block each (gather_b).  The
+// summation order depends only on the body's end count, never on which block runs it.
+template <class X, class GatherW, class GatherB>
+__device__ __forceinline__ void heavy_role(const Dev& d, int hb, const float4* __restrict__ qi,
+                                           float4* __restrict__ qo, int last, GatherW&& gather_w,
+                                           GatherB&& gather_b) {
+    const int nheavy = d.ctr[C_NHEAVY];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int h = hb * (HEAVY_T / 32) + warp; h < nheavy; h += HEAVY_BLOCKS * (HEAVY_T / 32)) {
+        const int b = d.heavy[h];
+        if (d.end_off[b + 1] - d.end_off[b] > WIDE_ENDS) continue;
+        solve_body<32, X>(d, b, lane, 0xffffffffu, qi, qo, last,
+                          [&](auto& s, const float* c, const float* A, const float* xs, int e0, int e1) {
+                              gather_w(b, s, c, A, xs, e0, e1, lane);
+                          },
+                          WIDE_ENDS);
+    }
+    for (int h = hb; h < nheavy; h += HEAVY_BLOCKS) {
+        const int b = d.heavy[h];
+        if (d.end_off[b + 1] - d.end_off[b] <= WIDE_ENDS) continue;
+        solve_heavy<X>(d, b, qi, qo, last, [&](auto& s, const float* c, const float* A, const float* xs, int e0, int e1) {
+            gather_b(b, s, c, A, xs, e0, e1, (int)threadIdx.x);
+        });
+    }
 }
 
 }  // namespace pabd

@@ -154,17 +154,20 @@ def random_small(seed: int, n_bodies=4, n_bonds=4, types=(SPHERICAL, SPRING, ELA
 # Workloads
 # ---------------------------------------------------------------------------------------
 
-def chain_pendulum(seed: int = SEED_BASE + 1, n_bodies=8, n_steps=100) -> Scene:
+def chain_pendulum(seed: int = SEED_BASE + 1, n_bodies=8, n_steps=100, diagonal=False) -> Scene:
     """Chain of unit cubes (mass 1) hung from a pinned body 0 by spherical joints that join
     the bottom corner (+1/2, -1/2, +1/2) of body i to the top corner (+1/2, +1/2, +1/2) of
-    body i+1; initial angles about z uniform in [-0.5, 0.5] rad; joints start satisfied."""
+    body i+1; initial angles about z uniform in [-0.5, 0.5] rad; joints start satisfied.
+    diagonal=True joins diagonally opposite corners (-1/2, -1/2, -1/2) and (+1/2, +1/2, +1/2)
+    instead: each inner body's two joints lie on its body diagonal, so its rotation about that
+    diagonal is held only by its inertia (an ill-conditioned per-body system)."""
     rng = np.random.default_rng(seed)
     h = 1.0 / 60.0
     b = _bodies(n_bodies)
     b["he"] = 0.5
     b["mass"] = 1.0
     b["pinned"][0] = 1
-    bot = np.array([0.5, -0.5, 0.5])
+    bot = np.array([-0.5, -0.5, -0.5]) if diagonal else np.array([0.5, -0.5, 0.5])
     top = np.array([0.5, 0.5, 0.5])
     Rs = [np.eye(3)]
     cs = [np.zeros(3)]
@@ -185,7 +188,7 @@ def chain_pendulum(seed: int = SEED_BASE + 1, n_bodies=8, n_steps=100) -> Scene:
         bo["xj"][k] = top
         bo["kappa"][k] = kappa
     params = default_params(h=h, n_iter=20, ground_d=-(float(n_bodies)) - 0.05, mu=0.5)
-    return Scene("chain_pendulum", params, b, bo, n_steps, dict(seed=seed))
+    return Scene("chain_pendulum", params, b, bo, n_steps, dict(seed=seed, diagonal=diagonal))
 
 
 def box_pile(seed: int = SEED_BASE + 2, nx=16, ny=16, nz=16, spacing=3.5, jitter=0.1,
@@ -219,6 +222,31 @@ def box_pile(seed: int = SEED_BASE + 2, nx=16, ny=16, nz=16, spacing=3.5, jitter
         b["c"][order, 1] = top - base - b["he"][order, 1]
     params = default_params(h=1.0 / 60.0, n_iter=n_iter, mu=0.5)
     return Scene("box_pile", params, b, _bonds(0), n_steps, dict(seed=seed, grid=(nx, ny, nz)))
+
+
+def slab_pile(n_side: int = 10, seed: int = SEED_BASE + 5, n_steps: int = 60, n_iter: int = 20) -> Scene:
+    """A dynamic slab (mass 50, half-height 0.1) resting 1 mm above the ground, carrying an
+    n_side x n_side grid of unit-mass cubes of edge 0.2 at spacing 0.4 (2 mm above it, yaw
+    jitter +-0.2 rad, position jitter +-0.02): the slab's four contacts per cube make it a
+    body with about 4 n_side^2 bond ends (a large body under a pile).  The slab is a large
+    body (it bypasses the grid); h = 1/60."""
+    rng = np.random.default_rng(seed)
+    n = n_side * n_side + 1
+    b = _bodies(n)
+    half = 0.2 * n_side + 0.1
+    b["he"][0] = (half, 0.1, half)
+    b["mass"][0] = 50.0
+    b["c"][0] = (0.0, 0.101, 0.0)
+    ii, kk = np.meshgrid(np.arange(n_side), np.arange(n_side), indexing="ij")
+    x = (ii.ravel() - 0.5 * (n_side - 1)) * 0.4 + rng.uniform(-0.02, 0.02, n - 1)
+    z = (kk.ravel() - 0.5 * (n_side - 1)) * 0.4 + rng.uniform(-0.02, 0.02, n - 1)
+    b["he"][1:] = 0.1
+    b["mass"][1:] = 1.0
+    b["c"][1:, 0], b["c"][1:, 1], b["c"][1:, 2] = x, 0.202 + 0.1 + 0.002, z
+    yaw = rng.uniform(-0.2, 0.2, n - 1)
+    b["quat"][1:] = np.stack([np.zeros(n - 1), np.sin(yaw / 2), np.zeros(n - 1), np.cos(yaw / 2)], axis=1)
+    params = default_params(h=1.0 / 60.0, n_iter=n_iter, large_he=1.0)
+    return Scene("slab_pile", params, b, _bonds(0), n_steps, dict(seed=seed, n_side=n_side))
 
 
 def box_pile_n(n: int, seed: int = SEED_BASE + 2, **kw) -> Scene:
@@ -355,6 +383,67 @@ def mass_ratio_chain(n=6, ratio=100.0, al=True, n_iter=10, n_steps=300, kappa_st
         bo["beta"][k], bo["alpha"][k], bo["gamma"][k] = 1e4, 0.99, 0.999
     params = default_params(n_iter=n_iter, has_ground=0, body_contacts=0)
     return Scene("mass_ratio_chain", params, b, bo, n_steps, dict(al=al, ratio=ratio))
+
+
+def mass_ratio_stack(n=6, ratio=10.0, n_iter=20, n_steps=300) -> Scene:
+    """A stack of n unit cubes on the ground, each `ratio` times heavier than the one below it
+    (1, 10, 100, ... kg from the bottom up), 2 mm apart; h = 1/60, mu = 0.5 -- the paper's
+    extreme-mass-ratio stack (Sec. 6, comparison with sequential impulses)."""
+    b = _bodies(n)
+    b["he"] = 0.5
+    b["mass"] = ratio ** np.arange(n)
+    b["c"][:, 1] = 0.5 + 0.002 + np.arange(n) * 1.002
+    params = default_params(h=1.0 / 60.0, n_iter=n_iter, mu=0.5)
+    return Scene("mass_ratio_stack", params, b, _bonds(0), n_steps, dict(ratio=ratio))
+
+
+def two_box_spring(n_iter=20, n_steps=60, kappa=1e4) -> Scene:
+    """Two unit cubes (1 kg) joined by a spring (Eq. 26 split) of rest length 1 between the
+    centres of their facing faces, stretched to twice its rest length; no gravity, no ground --
+    the paper's two-box convergence example (Sec. 6, comparison with AVBD)."""
+    b = _bodies(2)
+    b["he"] = 0.5
+    b["mass"] = 1.0
+    b["c"][0] = (-1.5, 0.0, 0.0)
+    b["c"][1] = (1.5, 0.0, 0.0)
+    bo = _bonds(1)
+    bo["type"], bo["i"], bo["j"] = SPRING, 0, 1
+    bo["xi"], bo["xj"] = (0.5, 0.0, 0.0), (-0.5, 0.0, 0.0)
+    bo["kappa"], bo["rest"] = kappa, 1.0
+    params = default_params(h=1.0 / 60.0, n_iter=n_iter, gravity=(0.0, 0.0, 0.0), has_ground=0, body_contacts=0)
+    return Scene("two_box_spring", params, b, bo, n_steps, dict(kappa=kappa))
+
+
+def spring_net(n=11, n_iter=20, n_steps=120, kappa=2e3, stretch=0.6) -> Scene:
+    """An n x n net of cubes (edge 0.2, 0.5 kg) in the x-y plane at spacing 0.5, each joined
+    to its four neighbours by springs between facing face centres (2 n (n - 1) springs: 220
+    for n = 11) whose rest length is `stretch` times the initial face gap, so the net starts
+    stretched; the two top corners are pinned and gravity pulls it down, so it contracts
+    toward the middle and sags -- the paper's 11 x 11 net (Sec. 6, comparison with VBD)."""
+    b = _bodies(n * n)
+    b["he"] = 0.1
+    b["mass"] = 0.5
+    ii, jj = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")  # ii: column (x), jj: row (y)
+    b["c"][:, 0] = (ii.ravel() - 0.5 * (n - 1)) * 0.5
+    b["c"][:, 1] = 1.0 + jj.ravel() * 0.5
+    top = [k for k in range(n * n) if jj.ravel()[k] == n - 1 and ii.ravel()[k] in (0, n - 1)]
+    b["pinned"][top] = 1
+    gap = 0.5 - 0.2
+    rows = []
+    for k in range(n * n):
+        x, y = ii.ravel()[k], jj.ravel()[k]
+        for dx, dy, ax in ((1, 0, 0), (0, 1, 1)):
+            if x + dx < n and y + dy < n:
+                m = (x + dx) * n + (y + dy)
+                r = np.zeros(1, dtype=BOND_DTYPE)[0]
+                r["type"], r["i"], r["j"] = SPRING, k, m
+                e = np.eye(3)[ax] * 0.1
+                r["xi"], r["xj"] = e, -e
+                r["kappa"], r["rest"] = kappa, stretch * gap
+                rows.append(r)
+    bo = np.array(rows, dtype=BOND_DTYPE)
+    params = default_params(h=1.0 / 60.0, n_iter=n_iter, has_ground=0, body_contacts=0)
+    return Scene("spring_net", params, b, bo, n_steps, dict(n=n, stretch=stretch))
 
 
 def batched_trees(seed: int = SEED_BASE + 4, n_scenes=4096, n_min=4, n_max=64, n_steps=1000) -> Scene:

@@ -1,0 +1,91 @@
+"""The paper's convergence and stability examples (Sec. 6), re-created as synthetic scenes,
+pinned on the oracle: the two-box spring (its first step's sweeps as a closed-form linear
+iteration), the 11 x 11 spring net (linear convergence; the fixed point of the unprojected
+sweeps is the dense-Newton minimiser on a small net) and the extreme-mass-ratio stack
+(stays upright and comes to rest)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import scenes as S
+from tests.dense_newton import minimise
+
+
+def _centre_gap_after(k, **kw):
+    o = O.OracleScene(S.two_box_spring(n_iter=k, **kw))
+    o.step(1)
+    st = o.state()
+    return st[1, 0] - st[0, 0]
+
+
+def test_two_box_spring_first_step_closed_form():
+    """Each body's system (Eq. 19) about its centre: G = [[m + w, w x], [w x, Pi + w x^2]]
+    (x = +-1/2 the face centre, w = h^2 kappa), right-hand side [m (s - c) + f', x f'] with
+    f' = +-w (gap - l).  The projection discards the stretch, so the centre distance u obeys
+    u <- u + G^-1_00 m (s_u - u) - 2 w (G^-1_00 + x G^-1_01) (u - 1 - l): a linear iteration
+    with ratio rho = 1 - m G^-1_00 - 2 w (G^-1_00 + G^-1_01 / 2) and fixed point
+    u* = (s_u m G^-1_00 + 2 w a (1 + l)) / (m G^-1_00 + 2 w a), a = G^-1_00 + G^-1_01 / 2."""
+    h, m, kappa, l, he = 1.0 / 60.0, 1.0, 1e4, 1.0, 0.5
+    w = h * h * kappa
+    Pi = m * he * he / 3.0
+    Gi = np.linalg.inv(np.array([[m + w, 0.5 * w], [0.5 * w, Pi + 0.25 * w]]))
+    a = Gi[0, 0] + 0.5 * Gi[0, 1]
+    rho = 1.0 - m * Gi[0, 0] - 2.0 * w * a
+    s_u = 3.0                                   # v = 0, no gravity: s = q^n
+    u_star = (s_u * m * Gi[0, 0] + 2.0 * w * a * (1.0 + l)) / (m * Gi[0, 0] + 2.0 * w * a)
+    u = [3.0] + [_centre_gap_after(k) for k in range(1, 9)]
+    e = np.array(u) - u_star
+    np.testing.assert_allclose(e[1:] / e[:-1], rho, rtol=1e-8)
+    assert rho < 0                              # the error alternates in sign
+    assert abs(_centre_gap_after(400) - u_star) < 1e-12
+
+
+def test_spring_net_converges_linearly():
+    """The 11 x 11 net's first step: the sweeps' error ratio settles to a constant below 1
+    (linear convergence of the successive substitution, Sec. 6)."""
+    ref = O.OracleScene(S.spring_net(n_iter=600))
+    ref.step(1)
+    q_star = ref.state()[:, :12]
+    errs = []
+    for k in (10, 20, 40, 80):
+        o = O.OracleScene(S.spring_net(n_iter=k))
+        o.step(1)
+        errs.append(np.abs(o.state()[:, :12] - q_star).max())
+    r = [errs[i + 1] / errs[i] for i in range(3)]
+    assert all(x < 1.0 for x in r), r
+    assert abs(np.log(r[2]) / np.log(r[1]) - 2.0) < 0.2    # doubling k squares the ratio: geometric
+
+
+def test_small_net_fixed_point_is_dense_newton_minimiser():
+    """A 3 x 3 net of affine bodies (no projection, nothing pinned, no gravity): the sweeps
+    iterated to convergence reach the minimiser of Eq. 13 found by dense Newton."""
+    sc = S.spring_net(n=3, n_iter=3000)
+    sc.params = dict(sc.params, project=0, gravity=(0.0, 0.0, 0.0))
+    sc.bodies["pinned"] = 0
+    o = O.OracleScene(sc)
+    st0 = o.state()
+    s_q = np.concatenate([st0[:, 0:3], st0[:, 3:12]], axis=1)
+    o.step(1)
+    st = o.state()
+    q_or = np.concatenate([st[:, 0:3], st[:, 3:12]], axis=1)
+    q_nt = minimise(sc, s_q)
+    assert np.abs(q_or - q_nt).max() < 1e-9
+    assert np.abs(q_or - s_q).max() > 1e-3
+
+
+def test_mass_ratio_stack_stays_upright_and_settles():
+    """Six cubes, each ten times heavier than the one below (1 kg to 100 t): over ten seconds
+    the stack stands -- no sideways drift, the order kept, each box above the one below it,
+    heights bounded -- and its bouncing dies down (stable, as the paper reports)."""
+    sc = S.mass_ratio_stack(n_steps=600)
+    o = O.OracleScene(sc)
+    vmax = []
+    for k in range(600):
+        o.step(1)
+        st = o.state()
+        assert np.isfinite(st).all()
+        assert np.abs(st[:, [0, 2]]).max() < 1e-9
+        assert np.all(np.diff(st[:, 1]) > 0.5) and st[:, 1].max() < 6.0
+        vmax.append(np.abs(st[:, 16:19]).max())
+    vmax = np.array(vmax)
+    assert vmax[500:].max() < 0.25 * vmax[100:200].max()
