@@ -100,10 +100,23 @@ ARGS = None
 
 
 def workload():
+    sc = _workload()
+    if ARGS is not None and ARGS.resid_tol > 0:
+        sc.params = dict(sc.params, resid_tol=ARGS.resid_tol)
+    return sc
+
+
+def _workload():
     if ARGS is not None and ARGS.workload == "trees":
         return S.batched_trees()
     if ARGS is not None and ARGS.workload == "quadruped":
         return S.quadruped_bed_rod()
+    if ARGS is not None and ARGS.workload == "stack":
+        return S.mass_ratio_stack()
+    if ARGS is not None and ARGS.workload == "spring":
+        return S.two_box_spring()
+    if ARGS is not None and ARGS.workload == "net":
+        return S.spring_net()
     n = ARGS.bodies if ARGS is not None else 4096
     if n == 4096 and not (ARGS is not None and ARGS.stacked):
         return S.box_pile()
@@ -112,6 +125,13 @@ def workload():
 
 def config_of(sc, K):
     start = ARGS.start_step if ARGS is not None else 0
+    if ARGS is not None and ARGS.workload in ("stack", "spring", "net"):
+        desc = {"stack": "six-cube stack, each cube 10x heavier than the one below",
+                "spring": "two unit cubes joined by a spring stretched to twice its rest length",
+                "net": "11 x 11 net of cubes joined by 220 pre-stretched springs, top corners pinned"}[ARGS.workload]
+        return {"workload": desc + f" ({sc.n_bodies} bodies), {sc.params['n_iter']} sweeps, steps {start}..{start + K - 1}",
+                "n_bodies": sc.n_bodies, "n_iter": sc.params["n_iter"], "l2": "flushed between timed steps (256 MB write)",
+                "parallelism": "replicas", **_tol_cfg()}
     if ARGS is not None and ARGS.workload in ("trees", "quadruped"):
         if ARGS.workload == "trees":
             desc = (f"{sc.n_groups} independent trees of 4-64 boxes ({sc.n_bodies} bodies), ground contact, "
@@ -121,12 +141,20 @@ def config_of(sc, K):
                     f"elastic rod ({sc.n_bodies} bodies), {sc.params['n_iter']} sweeps, h=1/60")
         return {"workload": desc + f", steps {start}..{start + K - 1}", "n_bodies": sc.n_bodies,
                 "n_iter": sc.params["n_iter"], "l2": "flushed between timed steps (256 MB write)",
-                "parallelism": "replicas"}
+                "parallelism": "replicas", **_tol_cfg()}
     kind = "stacked columns" if (ARGS is not None and ARGS.stacked) else "jittered grid, spacing 3.5"
     return {"workload": f"box pile {sc.n_bodies} ({kind}), {sc.params['n_iter']} sweeps, "
                         f"h=1/60, steps {start}..{start + K - 1} of the trajectory",
             "n_bodies": sc.n_bodies, "n_iter": sc.params["n_iter"], "l2": "flushed between timed steps (256 MB write)",
-            "parallelism": "replicas"}
+            "parallelism": "replicas", **_tol_cfg()}
+
+
+def _tol_cfg():
+    if ARGS is None or ARGS.resid_tol <= 0:
+        return {}
+    return {"resid_tol": ARGS.resid_tol,
+            "note": "each scene stops at its first sweep with residual <= resid_tol (at most n_iter); "
+                    "body-iterations count the sweeps actually run (mean_sweeps_per_step)"}
 
 
 def _kernel_hash():
@@ -262,6 +290,16 @@ def run_ours(args, rank, world, local_rank):
     g.sync()
     reset()
     n_body_iter = sc.n_bodies * sc.params["n_iter"]
+    mean_sweeps = None
+    if sc.params.get("resid_tol", 0.0) > 0:
+        # sweeps actually run per step under the threshold, from the same steps (untimed pass)
+        counts = []
+        for k in range(K):
+            g.step(1)
+            counts.append(g.info()["last_sweeps"])
+        mean_sweeps = float(np.mean(counts))
+        n_body_iter = sc.n_bodies * mean_sweeps
+        reset()
 
     # timed region: graph path, one CUDA-event pair per step on the scene's stream
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
@@ -385,6 +423,8 @@ def run_ours(args, rank, world, local_rank):
                                                                  "finalize_ms", "step_ms")}}
     cfg = config_of(sc, K)
     cfg["sweep"] = {k: info1[k] for k in ("sweep_mode", "sweep_lanes", "sweep_block", "sweep_grid")}
+    if mean_sweeps is not None:
+        cfg["mean_sweeps_per_step"] = mean_sweeps
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -454,7 +494,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="pile", choices=["pile", "trees", "quadruped", "served"])
+    ap.add_argument("--workload", default="pile",
+                    choices=["pile", "trees", "quadruped", "served", "stack", "spring", "net"])
+    ap.add_argument("--resid-tol", type=float, default=0.0,
+                    help="residual threshold of the sweeps (0: a fixed n_iter sweeps per step)")
     ap.add_argument("--rates", default="100,300,1000,3000,10000", help="served: request rates (req/s)")
     ap.add_argument("--duration", type=float, default=3.0, help="served: seconds of arrivals per rate")
     ap.add_argument("--bodies", type=int, default=4096, help="pile size (4096 = the 16^3 pile)")

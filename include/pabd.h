@@ -115,6 +115,12 @@ typedef struct {
     size_t max_pairs;         /* capacities: at most 16 M pairs, 0 = 16 per body (clamped to 16 M) */
     size_t max_contacts;      /* at most 60 M, 0 = 32 per body (clamped to 60 M); at most 8 M bodies.
                                  Exceeding one in a step latches PABD_ERR_CAPACITY. */
+    double resid_tol;         /* Sec. 4.2 stopping rule.  0: every step runs n_iter sweeps.  > 0:
+                                 each scene (group) stops after the first sweep whose residual
+                                 sqrt(sum |q^{k+1} - q^k|^2) is at most resid_tol (at most n_iter
+                                 sweeps); the loop ends on the device (a conditional graph node)
+                                 once every scene has stopped.  Runs the one-launch-per-sweep
+                                 mode; not with AL_DISTANCE bonds (PABD_ERR_ARG). */
     void* stream;             /* cudaStream_t on which all work is enqueued (NULL: default) */
     /* optional device allocator (e.g. a framework's caching allocator); NULL: cudaMalloc */
     void* (*alloc)(size_t bytes, void* ctx);
@@ -165,6 +171,7 @@ typedef struct {
                                  gathered and solved by a block of 256 threads */
     int64_t fp64_dynamic;     /* bodies that took the extended-precision redo in the last sweep
                                  of the last step because of a small FP32 pivot */
+    int64_t last_sweeps;      /* sweeps the last step ran (n_iter unless resid_tol ended it) */
 } pabd_info;
 
 /* Create an empty scene on the current CUDA device.  *out receives the handle. */

@@ -78,6 +78,8 @@ def lib():
         L.po_get_al_state.argtypes = [P, D]
         L.po_get_activation_margin.argtypes = [P, D]
         L.po_set_activation_shift.argtypes = [P, ctypes.c_double]
+        L.po_last_sweeps.argtypes = [P]
+        L.po_last_sweeps.restype = ctypes.c_int
         L.po_set_al_state.argtypes = [P, D]
         _lib = L
     return _lib
@@ -95,7 +97,7 @@ def pack_params(p: dict) -> np.ndarray:
     return np.array([
         p["h"], *p["gravity"], p["n_iter"], p["has_ground"], *p["ground_n"], p["ground_d"],
         p["mu"], p["c_kappa"], p["d_hat_rel"], p["margin"], p["project"], p["body_contacts"],
-        p["large_he"],
+        p["large_he"], p.get("resid_tol", 0.0),
     ], dtype=np.float64)
 
 
@@ -179,6 +181,10 @@ class OracleScene:
         out = np.zeros(max(self.n, 1))
         self.L.po_get_activation_margin(self.h, _dp(out))
         return out[:self.n]
+
+    def last_sweeps(self) -> int:
+        """Sweeps the last step ran (n_iter unless a residual threshold ended it sooner)."""
+        return self.L.po_last_sweeps(self.h)
 
     def set_activation_shift(self, shift: float):
         """Test probe: contacts switch on at g < dhat + shift in the following steps (0 = the method)."""

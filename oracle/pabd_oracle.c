@@ -68,6 +68,7 @@ typedef struct {
     double mu, c_kappa, d_hat_rel, margin;
     int project, body_contacts;
     double large_he;
+    double resid_tol;       /* 0: n_iter sweeps; else a scene stops when its residual <= resid_tol */
 } po_params;
 
 typedef struct {
@@ -86,6 +87,7 @@ typedef struct {
     double* resid;          /* per group, last iteration of the last step */
     double* amargin;        /* per body: min over the last step's sweeps of |g - dhat| of its contacts */
     double act_shift;       /* test probe of the contact activation threshold, 0 in the method */
+    int last_sweeps;        /* sweeps the last step ran (n_iter unless a residual threshold ended it) */
     /* adjacency of static bonds (pairs excluded from contact) */
     int n_excl, cap_excl;
     int* excl;              /* sorted (min, max) pairs */
@@ -303,6 +305,7 @@ void* po_create(const double* pr) {
     p->gn[0] = pr[6]; p->gn[1] = pr[7]; p->gn[2] = pr[8]; p->gd = pr[9];
     p->mu = pr[10]; p->c_kappa = pr[11]; p->d_hat_rel = pr[12]; p->margin = pr[13];
     p->project = (int)pr[14]; p->body_contacts = (int)pr[15]; p->large_he = pr[16];
+    p->resid_tol = pr[17];
     double n = norm3(p->gn);
     if (n > 0) for (int k = 0; k < 3; ++k) p->gn[k] /= n;
     return s;
@@ -920,12 +923,20 @@ static int step_once(po_scene* s) {
     if (!s->resid) s->resid = (double*)calloc((size_t)(s->n_groups > 0 ? s->n_groups : 1), sizeof(double));
     if (!s->amargin) s->amargin = (double*)calloc((size_t)(nb > 0 ? nb : 1), sizeof(double));
     for (int b = 0; b < nb; ++b) s->amargin[b] = INFINITY;
+    /* Sec. 4.2: the sweeps stop at n_iter, or -- with a residual threshold -- a scene (group)
+       stops after the first sweep whose residual is at most resid_tol; its bodies then keep
+       that sweep's iterate while the other scenes go on */
+    const int ng = s->n_groups > 0 ? s->n_groups : 1;
+    char* done = (char*)calloc((size_t)ng, 1);
+    double* r2g = (double*)calloc((size_t)ng, sizeof(double));
+    s->last_sweeps = 0;
     for (int it = 0; it < s->p.n_iter; ++it) {
         assemble_all(s, q, sq, t_next, H, rhs, s->amargin);      /* Jacobi: all read q^k */
-        for (int g = 0; g < s->n_groups; ++g) s->resid[g] = 0;
+        for (int g = 0; g < ng; ++g) r2g[g] = 0;
         for (int b = 0; b < nb; ++b) {
             double* out = q1 + 12 * b;
             if (s->bs[b].pinned) { memcpy(out, qn + 12 * b, 12 * sizeof(double)); continue; }
+            if (done[s->bs[b].group]) { memcpy(out, q + 12 * b, 12 * sizeof(double)); continue; }
             if (po_cholesky_solve(12, H + 144 * b, rhs + 12 * b, out) != 0) { err = 1; memcpy(out, q + 12 * b, 12 * sizeof(double)); }
             if (s->p.project) {                                   /* local solve */
                 double R[9];
@@ -934,13 +945,23 @@ static int step_once(po_scene* s) {
             }
             double r2 = 0;
             for (int k = 0; k < 12; ++k) { double dd = out[k] - q[12 * b + k]; r2 += dd * dd; }
-            s->resid[s->bs[b].group] += r2;
+            r2g[s->bs[b].group] += r2;
         }
         memcpy(q, q1, sizeof(double) * 12 * nb);
         for (int e = 0; e < s->nc; ++e)
             if (s->cb[e].type == PO_AL) al_update(&s->cb[e], q);
+        s->last_sweeps = it + 1;
+        int active = 0;
+        for (int g = 0; g < s->n_groups; ++g) {
+            if (done[g]) continue;
+            s->resid[g] = sqrt(r2g[g]);
+            if (s->p.resid_tol > 0 && s->resid[g] <= s->p.resid_tol) done[g] = 1;
+            else ++active;
+        }
+        if (s->p.resid_tol > 0 && active == 0) break;
     }
-    for (int g = 0; g < s->n_groups; ++g) s->resid[g] = sqrt(s->resid[g]);
+    free(done);
+    free(r2g);
     /* velocity recovery */
     for (int b = 0; b < nb; ++b) {
         po_state* x = &s->st[b];
@@ -1061,6 +1082,9 @@ void po_body_system(void* h, int body, double* H, double* rhs) {
     memcpy(rhs, rr + 12 * body, 12 * sizeof(double));
     free(q); free(HH); free(rr);
 }
+
+/* Sweeps the last step ran. */
+int po_last_sweeps(void* h) { return ((po_scene*)h)->last_sweeps; }
 
 /* Test probe: contacts of the following steps switch on at g < dhat + shift (0 restores the method). */
 void po_set_activation_shift(void* h, double shift) { ((po_scene*)h)->act_shift = shift; }

@@ -42,6 +42,7 @@ class pabd_scene_desc(ctypes.Structure):
         ("margin", ctypes.c_double), ("project", ctypes.c_int), ("body_contacts", ctypes.c_int),
         ("large_he", ctypes.c_double), ("precision_policy", ctypes.c_int),
         ("sweep_mode", ctypes.c_int), ("sweep_lanes", ctypes.c_int), ("max_pairs", ctypes.c_size_t), ("max_contacts", ctypes.c_size_t),
+        ("resid_tol", ctypes.c_double),
         ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
     ]
 
@@ -68,7 +69,7 @@ class pabd_info(ctypes.Structure):
         "n_bodies", "n_groups", "n_static_bonds", "n_bonds", "n_pairs", "n_contacts", "step_index",
         "max_pairs", "max_contacts", "graph_nodes", "launches", "fp64_bodies", "device_bytes",
         "sweep_mode", "sweep_lanes", "sweep_block", "sweep_grid", "coop_fallbacks", "heavy_bodies",
-        "fp64_dynamic")]
+        "fp64_dynamic", "last_sweeps")]
 
 
 _P = ctypes.c_void_p
@@ -326,6 +327,7 @@ def scene_desc(params: dict, stream=0, allocator: _TorchAllocator | None = None,
     d.sweep_lanes = int(sweep_lanes)
     d.max_pairs = int(max_pairs)
     d.max_contacts = int(max_contacts)
+    d.resid_tol = float(params.get("resid_tol", 0.0))
     d.stream = stream or None
     if allocator is not None:
         d.alloc = allocator.alloc_cb

@@ -48,41 +48,6 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, int* status) {
     return s_ok != 0;
 }
 
-// an augmented Lagrangian bond's state is stored by end i, or by end j when i is pinned
-__device__ __forceinline__ bool al_writer(const Dev& d, int4 m, int b) {
-    return (m.z == K_AL) && (m.x == b || (d.bflags[m.x] & BF_PINNED));
-}
-
-// accumulate the ends lane, lane + L, ... of body b's CSR slice (bond forces in T), in that
-// order.  Two ends per round in FP32: both records and both other bodies' iterates are loaded
-// before either force is evaluated, so a lane waits for two dependent loads per pair of ends.
-template <int L, class T>
-__device__ __forceinline__ void gather_ends(const Dev& d, const float4* __restrict__ q, int b, const float* cb,
-                                            const float* Ab, const float* xs, int e0, int e1, int lane, int it,
-                                            Sys<T>& s) {
-    int p = e0 + lane;
-    // (the FP64 redo, rare, keeps one end per round: fewer live registers)
-    if (sizeof(T) == 4) for (; p + L < e1; p += 2 * L) {
-        const int4 m0 = d.rec_m[p], m1 = d.rec_m[p + L];
-        const float4 a0 = d.rec_a[p], b0 = d.rec_b[p], a1 = d.rec_a[p + L], b1 = d.rec_b[p + L];
-        float c0[3], A0[9], c1[3], A1[9];
-        ld_q_or_zero(q, other_body(m0, b), c0, A0);
-        ld_q_or_zero(q, other_body(m1, b), c1, A1);
-        T f[3];
-        T w = end_force_q<T>(d, c0, A0, b, cb, Ab, m0, a0, b0, it, al_writer(d, m0, b), f);
-        sys_add_t(s, w, f, (m0.y == b) ? b0 : a0, xs);
-        w = end_force_q<T>(d, c1, A1, b, cb, Ab, m1, a1, b1, it, al_writer(d, m1, b), f);
-        sys_add_t(s, w, f, (m1.y == b) ? b1 : a1, xs);
-    }
-    for (; p < e1; p += L) {
-        const int4 m = d.rec_m[p];
-        const float4 xa = d.rec_a[p], xb = d.rec_b[p];
-        T f[3];
-        const T w = end_force<T>(d, q, b, cb, Ab, m, xa, xb, it, al_writer(d, m, b), f);
-        sys_add_t(s, w, f, (m.y == b) ? xb : xa, xs);
-    }
-}
-
 template <int L, class X>
 __global__ void __launch_bounds__(HEAVY_T, 4) k_sweep_fused(Dev d) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -121,7 +86,21 @@ __global__ void __launch_bounds__(HEAVY_T, 4) k_sweep_fused(Dev d) {
 template <int L, class X>
 __global__ void __launch_bounds__(128, 4) k_sweep_one(Dev d, const float4* __restrict__ qi, float4* __restrict__ qo,
                                                    int it, int light) {
-    const int last = it == d.p.n_iter - 1;
+    // Programmatic dependent launch: this block lets the next sweep's launch proceed, then waits
+    // until the previous sweep has completed and its writes are visible (no-ops when launched
+    // without the attribute)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    int last = it == d.p.n_iter - 1;
+    if (it < 0) {
+        // under a residual threshold: the sweep index and buffers from the device, the
+        // per-body residual every sweep; nothing once the loop has ended (eager launches)
+        if (!d.sweep_ctl[2]) return;
+        it = d.sweep_ctl[0];
+        qi = (it & 1) ? d.qb : d.qa;
+        qo = (it & 1) ? d.qa : d.qb;
+        last = 1;
+    }
     if ((int)blockIdx.x >= light) {
         heavy_role<X>(d, blockIdx.x - light, qi, qo, last,
             [&](int b, auto& s, const float* c, const float* A, const float* xs, int e0, int e1, int ln) {
@@ -142,30 +121,45 @@ __global__ void __launch_bounds__(128, 4) k_sweep_one(Dev d, const float4* __res
 
 void launch_end_records(const Dev& d, cudaStream_t st, long long* launches);
 
+template <int L, class X>
+static void sweep_one_ex(const Dev& d, const float4* qi, float4* qo, int it, int light, int grid, bool pdl,
+                         cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(128);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, k_sweep_one<L, X>, d, qi, qo, it, light);
+}
+
+template <class X>
+static void sweep_one_l(const Dev& d, const float4* qi, float4* qo, int it, int L, int light, int grid, bool pdl,
+                        cudaStream_t st) {
+    switch (L) {
+        case 1: sweep_one_ex<1, X>(d, qi, qo, it, light, grid, pdl, st); break;
+        case 2: sweep_one_ex<2, X>(d, qi, qo, it, light, grid, pdl, st); break;
+        case 4: sweep_one_ex<4, X>(d, qi, qo, it, light, grid, pdl, st); break;
+        case 8: sweep_one_ex<8, X>(d, qi, qo, it, light, grid, pdl, st); break;
+        default: sweep_one_ex<16, X>(d, qi, qo, it, light, grid, pdl, st); break;
+    }
+}
+
+// `pdl`: launched as a programmatic dependent of the previous kernel on the stream (the
+// previous sweep), so that its launch overlaps that sweep's tail
 void launch_sweep_one(const Dev& d, const float4* qi, float4* qo, int it, int L, cudaStream_t st,
-                      long long* launches) {
+                      long long* launches, bool pdl) {
     static_assert(HEAVY_T == 128, "the sweep launch's blocks are the heavy bodies' blocks");
     const long long n = (long long)(d.N > 0 ? d.N : 1) * L;
     const int light = (int)((n + 127) / 128);
     const int grid = light + HEAVY_BLOCKS;
     // the extended type of ill-conditioned bodies: FP64 under policy 2, double-float otherwise
-    if (d.p.precision_policy == 2) {
-        switch (L) {
-            case 1: k_sweep_one<1, double><<<grid, 128, 0, st>>>(d, qi, qo, it, light); break;
-            case 2: k_sweep_one<2, double><<<grid, 128, 0, st>>>(d, qi, qo, it, light); break;
-            case 4: k_sweep_one<4, double><<<grid, 128, 0, st>>>(d, qi, qo, it, light); break;
-            case 8: k_sweep_one<8, double><<<grid, 128, 0, st>>>(d, qi, qo, it, light); break;
-            default: k_sweep_one<16, double><<<grid, 128, 0, st>>>(d, qi, qo, it, light); break;
-        }
-    } else {
-        switch (L) {
-            case 1: k_sweep_one<1, df><<<grid, 128, 0, st>>>(d, qi, qo, it, light); break;
-            case 2: k_sweep_one<2, df><<<grid, 128, 0, st>>>(d, qi, qo, it, light); break;
-            case 4: k_sweep_one<4, df><<<grid, 128, 0, st>>>(d, qi, qo, it, light); break;
-            case 8: k_sweep_one<8, df><<<grid, 128, 0, st>>>(d, qi, qo, it, light); break;
-            default: k_sweep_one<16, df><<<grid, 128, 0, st>>>(d, qi, qo, it, light); break;
-        }
-    }
+    if (d.p.precision_policy == 2) sweep_one_l<double>(d, qi, qo, it, L, light, grid, pdl, st);
+    else sweep_one_l<df>(d, qi, qo, it, L, light, grid, pdl, st);
     *launches += 1;
 }
 

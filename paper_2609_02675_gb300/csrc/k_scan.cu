@@ -1,7 +1,8 @@
 // Exclusive prefix sums of int arrays whose length lives in device memory, so that the
 // launches can be captured once in a CUDA graph and replayed while the lengths change.
 // Chunks of 4096 values (1024 threads x 4) are scanned per block; block totals go to a
-// scratch array that one block scans; a third pass adds the block offsets.
+// scratch array that one block scans; a third pass adds the block offsets.  Up to 16 chunks
+// are scanned by a single block in one launch.
 #include "pabd_internal.h"
 
 namespace pabd {
@@ -98,6 +99,38 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_add(int* out, const int* 
         if (base + k < n) out[base + k] += add;
 }
 
+// one block over up to SCAN_LOOP_MAX values: chunk after chunk, carrying the running total
+// (one launch instead of three for the small arrays of a small scene)
+constexpr int SCAN_LOOP_MAX = 16 * SCAN_CHUNK;
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_loop(const int* __restrict__ in, int* __restrict__ out,
+                                                            const int* n_dev, int n_cap) {
+    __shared__ int smem[32];
+    const int n = n_dev ? min(*n_dev, n_cap) : n_cap;
+    int carry = 0;
+    for (int c0 = 0; c0 < n; c0 += SCAN_CHUNK) {
+        const int base = c0 + threadIdx.x * SCAN_ITEMS;
+        int v[SCAN_ITEMS];
+        int s = 0;
+#pragma unroll
+        for (int k = 0; k < SCAN_ITEMS; ++k) {
+            v[k] = (base + k < n) ? in[base + k] : 0;
+            s += v[k];
+        }
+        int total;
+        const int incl = block_incl_scan(s, smem, &total);
+        int run = carry + incl - s;
+#pragma unroll
+        for (int k = 0; k < SCAN_ITEMS; ++k) {
+            if (base + k < n) out[base + k] = run;
+            run += v[k];
+        }
+        carry += total;
+        __syncthreads();  // smem is rewritten by the next chunk's scan
+    }
+    if (threadIdx.x == 0) out[n] = carry;
+}
+
 int scan_scratch_ints(int n_cap) { return (n_cap + SCAN_CHUNK - 1) / SCAN_CHUNK + 1; }
 
 void scan_exclusive(const int* in, int* out, const int* n_dev, int n_cap, int* scratch, cudaStream_t st,
@@ -105,6 +138,11 @@ void scan_exclusive(const int* in, int* out, const int* n_dev, int n_cap, int* s
     const int nb = n_cap > 0 ? (n_cap + SCAN_CHUNK - 1) / SCAN_CHUNK : 1;
     if (nb == 1) {
         k_scan_chunks<<<1, SCAN_THREADS, 0, st>>>(in, out, n_dev, n_cap, scratch, 1);
+        *launches += 1;
+        return;
+    }
+    if (n_cap <= SCAN_LOOP_MAX) {
+        k_scan_loop<<<1, SCAN_THREADS, 0, st>>>(in, out, n_dev, n_cap);
         *launches += 1;
         return;
     }

@@ -74,7 +74,9 @@ __device__ __forceinline__ float4 mat_to_quat(const float* R) {
 
 // Velocity recovery (Alg. 1, Sec. 4.4): v = (c^{n+1} - c^n)/h;
 // [w]x = skew part of (A^{n+1} - A^n)(A^n)^T / h; Q^{n+1} = quat(A^{n+1}), sign-continuous.
-__global__ void k_finalize(Dev d, const float4* __restrict__ qf) {
+__global__ void k_finalize(Dev d, const float4* __restrict__ qf, int dyn) {
+    // under a residual threshold the last iterate sits in the buffer of the sweep count's parity
+    if (dyn) qf = (d.sweep_ctl[0] & 1) ? d.qb : d.qa;
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b == 0) atomicAdd((unsigned long long*)d.step_index, 1ull);
     if (b >= d.N) return;
@@ -313,9 +315,80 @@ void launch_csr(const Dev& d, cudaStream_t st, long long* launches) {
 }
 
 void launch_finalize(const Dev& d, const float4* q_fin, cudaStream_t st, long long* launches) {
-    k_finalize<<<nblk(d.N), ST_T, 0, st>>>(d, q_fin);
+    k_finalize<<<nblk(d.N), ST_T, 0, st>>>(d, q_fin, 0);
     k_group_resid<<<d.G > 0 ? d.G : 1, RES_T, 0, st>>>(d);
     *launches += 2;
+}
+
+// ---- sweeps under a residual threshold (Sec. 4.2 stopping rule, per scene) ----
+
+__global__ void k_sweep_ctl_init(Dev d) {
+    d.sweep_ctl[0] = 0;  // sweeps done
+    d.sweep_ctl[1] = 0;  // scenes still active after this sweep
+    d.sweep_ctl[2] = 1;  // loop on
+    d.sweep_ctl[3] = 0;
+}
+
+// After a sweep: one block per scene still running computes that sweep's residual (the same
+// fixed reduction as k_group_resid); at most resid_tol stops the scene, else it counts as
+// active.  The last block to finish (a ticket counter) runs the loop control: one more sweep
+// done, go on while a scene is active and fewer than n_iter sweeps ran; in a graph it also
+// sets the conditional node's value.  The decision depends only on integer counts.
+__global__ void __launch_bounds__(RES_T) k_sweep_check(Dev d, cudaGraphConditionalHandle h, int use_handle) {
+    __shared__ double part[RES_T / 32];
+    __shared__ int s_last;
+    const int g = blockIdx.x;
+    const bool on = d.sweep_ctl[2] != 0;
+    if (on && g < d.G && !d.group_done[g]) {
+        const int s = d.group_off[g], e = d.group_off[g + 1];
+        double acc = 0.0;
+        for (int b = s + threadIdx.x; b < e; b += RES_T) acc += d.resid_body[b];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < RES_T / 32; ++w) t += part[w];
+            const double r = sqrt(t);
+            d.resid_group[g] = r;
+            if (r <= d.p.resid_tol) d.group_done[g] = 1;
+            else atomicAdd(&d.sweep_ctl[1], 1);
+        }
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&d.sweep_ctl[3], 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last || threadIdx.x != 0) return;
+    __threadfence();
+    d.sweep_ctl[3] = 0;
+    int go = 0;
+    if (on) {
+        const int it = d.sweep_ctl[0] + 1;
+        d.sweep_ctl[0] = it;
+        go = atomicAdd(&d.sweep_ctl[1], 0) > 0 && it < d.p.n_iter;
+        d.sweep_ctl[1] = 0;
+        d.sweep_ctl[2] = go;
+    }
+    if (use_handle) cudaGraphSetConditional(h, go);
+}
+
+void launch_sweep_ctl_init(const Dev& d, cudaStream_t st, long long* launches) {
+    k_sweep_ctl_init<<<1, 1, 0, st>>>(d);
+    cudaMemsetAsync(d.group_done, 0, d.G > 0 ? d.G : 1, st);
+    *launches += 1;
+}
+
+void launch_sweep_check(const Dev& d, unsigned long long handle, cudaStream_t st, long long* launches) {
+    k_sweep_check<<<d.G > 0 ? d.G : 1, RES_T, 0, st>>>(d, (cudaGraphConditionalHandle)handle, handle != 0);
+    *launches += 1;
+}
+
+void launch_finalize_dynamic(const Dev& d, cudaStream_t st, long long* launches) {
+    k_finalize<<<nblk(d.N), ST_T, 0, st>>>(d, nullptr, 1);
+    *launches += 1;
 }
 
 }  // namespace pabd

@@ -17,6 +17,8 @@
 //            flagged, or a Cholesky pivot below 1e-4 of its diagonal): those re-gather and
 //            factor in an extended type -- double-float on the FP32 pipes (precision
 //            policy 1), or FP64 (policy 2).
+#include <type_traits>
+
 #include "sweep_math.cuh"
 
 namespace pabd {
@@ -24,7 +26,6 @@ namespace pabd {
 constexpr int BOND_T = 256;
 constexpr int SOLVE_T = 128;
 
-template <class X>
 __global__ void __launch_bounds__(BOND_T) k_bond(Dev d, const float4* __restrict__ q, int it) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= d.ctr[C_NBONDS]) return;
@@ -34,35 +35,43 @@ __global__ void __launch_bounds__(BOND_T) k_bond(Dev d, const float4* __restrict
     ld_q(q, m.x, c, A);
     const int4 mm = make_int4(m.x, m.y, m.z, b);
     const int fi = d.bflags[m.x], fj = m.y >= 0 ? d.bflags[m.y] : BF_PINNED;
-    const bool dbl = d.p.precision_policy == 3 || (d.p.precision_policy && ((fi | fj) & BF_FP64));
     // a bond between two fixed ends is advanced by the final update alone (as in the sweep kernels)
     const bool writer = !(fi & BF_PINNED) || !(fj & BF_PINNED);
-    float w, f[3];
-    if (dbl) {
-        X fd[3];
-        w = (float)end_force<X>(d, q, m.x, c, A, mm, xi, xj, it, writer, fd);
-        f[0] = (float)fd[0]; f[1] = (float)fd[1]; f[2] = (float)fd[2];
-    } else {
-        w = end_force<float>(d, q, m.x, c, A, mm, xi, xj, it, writer, f);
-    }
+    float f[3];
+    const float w = end_force<float>(d, q, m.x, c, A, mm, xi, xj, it, writer, f);
     const int p0 = d.end_pos[2 * b], p1 = (m.y >= 0) ? d.end_pos[2 * b + 1] : -1;
     if (p0 >= 0) d.ends[p0] = make_float4(w, f[0], f[1], f[2]);
     if (p1 >= 0) d.ends[p1] = make_float4(w, -f[0], -f[1], -f[2]);
 }
+
+// The FP32 records of the bond kernel are summed; a body on the extended path evaluates its
+// ends again in the extended type from the CSR-ordered records (as the one-launch sweep does),
+// so the two modes agree bit for bit.
+template <class T>
+constexpr bool is_fp32_sys() { return std::is_same<T, Sys<float>>::value; }
 
 // one body per group of L lanes; lane l adds the body's ends l, l + L, ... (float records).
 // The first `light` blocks take the bodies with at most HEAVY_ENDS ends; the HEAVY_BLOCKS
 // blocks after them take the heavy bodies, a block each.
 template <int L, class X>
 __global__ void __launch_bounds__(SOLVE_T, 4) k_solve(Dev d, const float4* __restrict__ qi, float4* __restrict__ qo,
-                                                   int last, int light) {
+                                                   int it, int light) {
+    const int last = it == d.p.n_iter - 1;
     if ((int)blockIdx.x >= light) {
         heavy_role<X>(d, blockIdx.x - light, qi, qo, last,
-            [&](int, auto& s, const float*, const float*, const float* xs, int e0, int e1, int ln) {
-                for (int p = e0 + ln; p < e1; p += 32) sys_add(s, d.ends[p], d.end_x[p], xs);
+            [&](int b, auto& s, const float* c, const float* A, const float* xs, int e0, int e1, int ln) {
+                if constexpr (is_fp32_sys<std::decay_t<decltype(s)>>()) {
+                    for (int p = e0 + ln; p < e1; p += 32) sys_add(s, d.ends[p], d.end_x[p], xs);
+                } else {
+                    gather_ends<32>(d, qi, b, c, A, xs, e0, e1, ln, it, s);
+                }
             },
-            [&](int, auto& s, const float*, const float*, const float* xs, int e0, int e1, int t) {
-                for (int p = e0 + t; p < e1; p += HEAVY_T) sys_add(s, d.ends[p], d.end_x[p], xs);
+            [&](int b, auto& s, const float* c, const float* A, const float* xs, int e0, int e1, int t) {
+                if constexpr (is_fp32_sys<std::decay_t<decltype(s)>>()) {
+                    for (int p = e0 + t; p < e1; p += HEAVY_T) sys_add(s, d.ends[p], d.end_x[p], xs);
+                } else {
+                    gather_ends<HEAVY_T>(d, qi, b, c, A, xs, e0, e1, t, it, s);
+                }
             });
         return;
     }
@@ -70,19 +79,22 @@ __global__ void __launch_bounds__(SOLVE_T, 4) k_solve(Dev d, const float4* __res
     const int b = tid / L, lane = tid & (L - 1);
     if (b >= d.N) return;
     solve_body<L, X>(d, b, lane, lane_mask<L>(), qi, qo, last,
-                     [&](auto& s, const float*, const float*, const float* xs, int e0, int e1) {
-        for (int p = e0 + lane; p < e1; p += L) sys_add(s, d.ends[p], d.end_x[p], xs);
+                     [&](auto& s, const float* c, const float* A, const float* xs, int e0, int e1) {
+        if constexpr (is_fp32_sys<std::decay_t<decltype(s)>>()) {
+            for (int p = e0 + lane; p < e1; p += L) sys_add(s, d.ends[p], d.end_x[p], xs);
+        } else {
+            gather_ends<L>(d, qi, b, c, A, xs, e0, e1, lane, it, s);
+        }
     });
 }
 
 void launch_bond(const Dev& d, const float4* q, int it, cudaStream_t st, long long* launches) {
     const int n = d.cap_bonds > 0 ? d.cap_bonds : 1;
-    if (d.p.precision_policy == 2) k_bond<double><<<(n + BOND_T - 1) / BOND_T, BOND_T, 0, st>>>(d, q, it);
-    else k_bond<df><<<(n + BOND_T - 1) / BOND_T, BOND_T, 0, st>>>(d, q, it);
+    k_bond<<<(n + BOND_T - 1) / BOND_T, BOND_T, 0, st>>>(d, q, it);
     *launches += 1;
 }
 
-void launch_solve(const Dev& d, const float4* q_in, float4* q_out, int last, int lanes, cudaStream_t st,
+void launch_solve(const Dev& d, const float4* q_in, float4* q_out, int it, int lanes, cudaStream_t st,
                   long long* launches) {
     static_assert(SOLVE_T == HEAVY_T, "the solve launch's blocks are the heavy bodies' blocks");
     const long long n = (long long)(d.N > 0 ? d.N : 1) * lanes;
@@ -90,16 +102,16 @@ void launch_solve(const Dev& d, const float4* q_in, float4* q_out, int last, int
     const int grid = light + HEAVY_BLOCKS;
     const bool f64 = d.p.precision_policy == 2;
     switch (lanes) {
-        case 1: f64 ? k_solve<1, double><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, last, light)
-                    : k_solve<1, df><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, last, light); break;
-        case 2: f64 ? k_solve<2, double><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, last, light)
-                    : k_solve<2, df><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, last, light); break;
-        case 4: f64 ? k_solve<4, double><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, last, light)
-                    : k_solve<4, df><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, last, light); break;
-        case 8: f64 ? k_solve<8, double><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, last, light)
-                    : k_solve<8, df><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, last, light); break;
-        default: f64 ? k_solve<16, double><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, last, light)
-                     : k_solve<16, df><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, last, light); break;
+        case 1: f64 ? k_solve<1, double><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light)
+                    : k_solve<1, df><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light); break;
+        case 2: f64 ? k_solve<2, double><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light)
+                    : k_solve<2, df><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light); break;
+        case 4: f64 ? k_solve<4, double><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light)
+                    : k_solve<4, df><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light); break;
+        case 8: f64 ? k_solve<8, double><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light)
+                    : k_solve<8, df><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light); break;
+        default: f64 ? k_solve<16, double><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light)
+                     : k_solve<16, df><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light); break;
     }
     *launches += 1;
 }

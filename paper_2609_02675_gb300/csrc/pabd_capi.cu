@@ -84,6 +84,8 @@ struct pabd_scene {
     long long coop_fallbacks = 0;
     // augmented Lagrangian bonds: (kappa_start, 0) per static bond, the state before the first step
     std::vector<float2> al_init;
+    // stream on which the body of the residual-threshold loop is captured into its graph node
+    cudaStream_t body_st = nullptr;
 
     void* dalloc(size_t n) {
         if (n == 0) n = 16;
@@ -135,10 +137,9 @@ void enqueue_step(pabd_scene* s, long long* launches, const cudaEvent_t* ev = nu
     float4* nxt = d.qb;
     auto two_launch = [&]() {
         for (int it = 0; it < d.p.n_iter; ++it) {
-            const int last = it == d.p.n_iter - 1;
             launch_bond(d, cur, it, s->st, launches);
-            if (last) cudaMemsetAsync(d.ctr + C_FP64DYN, 0, sizeof(int), s->st);
-            launch_solve(d, cur, nxt, last, s->lanes, s->st, launches);
+            if (it == d.p.n_iter - 1) cudaMemsetAsync(d.ctr + C_FP64DYN, 0, sizeof(int), s->st);
+            launch_solve(d, cur, nxt, it, s->lanes, s->st, launches);
             float4* t = cur; cur = nxt; nxt = t;
         }
     };
@@ -153,19 +154,63 @@ void enqueue_step(pabd_scene* s, long long* launches, const cudaEvent_t* ev = nu
         } else {
             if (d.p.n_iter & 1) { float4* t = cur; cur = nxt; nxt = t; }
         }
+    } else if (s->mode == 2 && d.p.resid_tol > 0) {
+        // Sec. 4.2 stopping rule: the sweeps loop on the device until every scene's residual
+        // is at most resid_tol (or n_iter sweeps).  In a graph the loop is a conditional WHILE
+        // node whose body is one sweep; launched eagerly, n_iter sweeps are enqueued and those
+        // after the loop has ended return at once.
+        launch_end_records(d, s->st, launches);
+        launch_sweep_ctl_init(d, s->st, launches);
+        auto one_sweep = [&](cudaStream_t st, unsigned long long handle) {
+            cudaMemsetAsync(d.ctr + C_FP64DYN, 0, sizeof(int), st);
+            launch_sweep_one(d, nullptr, nullptr, -1, s->lanes, st, launches);
+            launch_sweep_check(d, handle, st, launches);
+        };
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(s->st, &cs);
+        if (cs == cudaStreamCaptureStatusActive) {
+            cudaGraph_t g = nullptr;
+            const cudaGraphNode_t* deps = nullptr;
+            size_t nd = 0;
+            cudaStreamGetCaptureInfo(s->st, &cs, nullptr, &g, &deps, nullptr, &nd);
+            cudaGraphConditionalHandle h = 0;
+            cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+            cudaGraphNodeParams cp = {};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = h;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            cudaGraphNode_t node = nullptr;
+            cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp);
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            // four sweeps (each followed by its check) per pass of the loop: the sweeps after the
+            // loop has ended return at once, and a pass of the conditional node costs more than
+            // a launch
+            cudaStreamBeginCaptureToGraph(s->body_st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+            for (int u = 0; u < 4; ++u) one_sweep(s->body_st, (unsigned long long)h);
+            cudaStreamEndCapture(s->body_st, &body);
+            cudaStreamUpdateCaptureDependencies(s->st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+        } else {
+            for (int it = 0; it < d.p.n_iter; ++it) one_sweep(s->st, 0);
+        }
+        cur = nullptr;  // the last iterate's buffer is known on the device only
     } else if (s->mode == 2) {
         launch_end_records(d, s->st, launches);
+        // the counter of run-time extended-precision redos is reset before the sweeps (it counts
+        // the last sweep's): the sweeps then follow each other as programmatic dependents
+        cudaMemsetAsync(d.ctr + C_FP64DYN, 0, sizeof(int), s->st);
         for (int it = 0; it < d.p.n_iter; ++it) {
-            if (it == d.p.n_iter - 1) cudaMemsetAsync(d.ctr + C_FP64DYN, 0, sizeof(int), s->st);
-            launch_sweep_one(d, cur, nxt, it, s->lanes, s->st, launches);
+            launch_sweep_one(d, cur, nxt, it, s->lanes, s->st, launches, it > 0);
             float4* t = cur; cur = nxt; nxt = t;
         }
     } else {
+        launch_end_records(d, s->st, launches);  // the extended path's own evaluation reads them
         two_launch();
     }
-    launch_al_final(d, cur, s->st, launches);
+    if (cur) launch_al_final(d, cur, s->st, launches);
     mark();
-    launch_finalize(d, cur, s->st, launches);
+    if (cur) launch_finalize(d, cur, s->st, launches);
+    else launch_finalize_dynamic(d, s->st, launches);
     mark();
 }
 
@@ -244,6 +289,8 @@ pabd_status finalize_scene(pabd_scene* s) {
     p.n_iter = ds.n_iter; p.has_ground = ds.has_ground; p.project = ds.project; p.body_contacts = ds.body_contacts;
     if (ds.precision_policy < 0 || ds.precision_policy > 3) return PABD_ERR_ARG;
     p.precision_policy = ds.precision_policy;
+    if (!(ds.resid_tol >= 0) || !std::isfinite(ds.resid_tol)) return PABD_ERR_ARG;
+    p.resid_tol = ds.resid_tol;
     // capacities
     // the two-level scans cover 4096 x 4096 values; bond ends are counted in int.  Defaults:
     // 16 pairs and 32 contacts per body (a dense granular bed reaches about 24), clamped to
@@ -311,7 +358,8 @@ pabd_status finalize_scene(pabd_scene* s) {
     // ends of its static bonds (w = h^2 kappa; a drive's moving anchor at its rest angle).
     // Static extended-precision flag (reading R18): the FP64 Cholesky of the diagonally scaled
     // static-only system about x_s has a pivot below 1e-2 of its diagonal (ten times the
-    // dynamic test's margin, since contacts add to the system at run time).
+    // dynamic test's margin, since contacts add to the system at run time), or the static
+    // bonds' weights sum to more than 100 times the mass (BF_STIFF).
     std::vector<double> sw(N, 0.0), swx(3 * (size_t)N, 0.0);
     for (const HostBond& hb : s->bonds) {
         if (hb.i >= 0) { sw[hb.i] += hb.w; for (int k = 0; k < 3; ++k) swx[3 * hb.i + k] += hb.w * hb.xi[k]; }
@@ -325,6 +373,7 @@ pabd_status finalize_scene(pabd_scene* s) {
         for (int k = 0; k < 3; ++k) xsd[3 * b + k] = swx[3 * b + k] / (m + sw[b]);
         xs[b] = make_float4((float)xsd[3 * b], (float)xsd[3 * b + 1], (float)xsd[3 * b + 2], 0.f);
         if (xs[b].x != 0.f || xs[b].y != 0.f || xs[b].z != 0.f) flags[b] |= BF_SHIFT;
+        if (sw[b] > 100.0 * m) flags[b] |= BF_STIFF;
         // the shifted expansion point as the device uses it (rounded to FP32)
         for (int k = 0; k < 3; ++k) xsd[3 * b + k] = k == 0 ? xs[b].x : (k == 1 ? xs[b].y : xs[b].z);
     }
@@ -368,7 +417,11 @@ pabd_status finalize_scene(pabd_scene* s) {
                 }
             }
         }
-        if (!(worst >= 1e-2)) { flags[b] |= BF_FP64; s->fp64_bodies++; }
+        // stiffly jointed bodies too: their FP32 system resolves a joint correction only to
+        // about 1e-4 (joint weights thousands of times the mass against a rotational inertia
+        // that is not -- the cancellation lands on the rotation), and taking them straight to
+        // the extended type costs less than a test-and-redo
+        if (!(worst >= 1e-2) || (flags[b] & BF_STIFF)) { flags[b] |= BF_FP64; s->fp64_bodies++; }
     }
     // static bonds
     std::vector<int4> bmeta(Nc);
@@ -453,6 +506,7 @@ pabd_status finalize_scene(pabd_scene* s) {
         ok &= alloc_arr(s, d.adj_off, N + 1) && alloc_arr(s, d.adj_nbr, adj_nbr.size());
     }
     if (d.Nal) ok &= alloc_arr(s, d.al_st0, Nc) && alloc_arr(s, d.al_st1, Nc) && alloc_arr(s, d.al_par, Nc);
+    if (p.resid_tol > 0) ok &= alloc_arr(s, d.sweep_ctl, 4) && alloc_arr(s, d.group_done, d.G);
     if (!ok) return PABD_ERR_OOM;
 
     cudaStream_t st = s->st;
@@ -504,9 +558,15 @@ pabd_status finalize_scene(pabd_scene* s) {
     if (L != 1 && L != 2 && L != 4 && L != 8 && L != 16) return PABD_ERR_ARG;
     s->lanes = L;
     // sweep mode: 1 two launches per sweep, 2 one launch per sweep, 3 fused persistent;
-    // 0 = one launch per sweep (the fastest on the measured scenes)
+    // 0 = one launch per sweep (the fastest on the measured scenes).  A residual threshold
+    // runs one launch per sweep.
     if (ds.sweep_mode < 0 || ds.sweep_mode > 3) return PABD_ERR_ARG;
     s->mode = ds.sweep_mode == 0 ? 2 : ds.sweep_mode;
+    if (p.resid_tol > 0) {
+        if (d.Nal) return PABD_ERR_ARG;
+        s->mode = 2;
+        CK(cudaStreamCreateWithFlags(&s->body_st, cudaStreamNonBlocking));
+    }
     s->fused = (s->mode == 3) && N > 0;
     if (s->fused) {
         int coop = 0, dev = 0;
@@ -1026,6 +1086,12 @@ pabd_status pabd_get_info(pabd_scene* s, pabd_info* info) {
     info->coop_fallbacks = s->coop_fallbacks;
     info->heavy_bodies = c[C_NHEAVY];
     info->fp64_dynamic = c[C_FP64DYN];
+    info->last_sweeps = s->d.p.n_iter;
+    if (s->d.sweep_ctl) {
+        int ctl[4] = {0, 0, 0, 0};
+        CK(cudaMemcpy(ctl, s->d.sweep_ctl, sizeof ctl, cudaMemcpyDeviceToHost));
+        info->last_sweeps = ctl[0];
+    }
     return PABD_OK;
 }
 
@@ -1043,6 +1109,7 @@ pabd_status pabd_destroy_scene(pabd_scene* s) {
         if (s->desc.free) s->desc.free(p, s->desc.alloc_ctx);
         else cudaFree(p);
     }
+    if (s->body_st) cudaStreamDestroy(s->body_st);
     if (s->own_stream) cudaStreamDestroy(s->st);
     delete s;
     return PABD_OK;

@@ -18,8 +18,9 @@ enum BondKind { K_SPHERICAL = 0, K_SPRING = 1, K_ELASTIC_NL = 2, K_DRIVE = 4, K_
 
 enum StatusBits { ST_CAPACITY = 1, ST_DIVERGED = 2, ST_TIMEOUT = 4 };
 
-// BF_SHIFT: the body's system is assembled about a nonzero expansion point Dev::xs
-enum BodyFlags { BF_PINNED = 1, BF_FP64 = 2, BF_LARGE = 4, BF_SHIFT = 8 };
+// BF_SHIFT: the body's system is assembled about a nonzero expansion point Dev::xs.
+// BF_STIFF: its static bonds' weights sum to more than 100 times its mass (stiff joints).
+enum BodyFlags { BF_PINNED = 1, BF_FP64 = 2, BF_LARGE = 4, BF_SHIFT = 8, BF_STIFF = 16 };
 
 // device counters (ints) -- one small array so that one memset resets them
 enum Counter {
@@ -41,6 +42,7 @@ struct Params {
     float gn[3], gd;
     float mu, c_kappa, d_hat_rel, margin;
     float cell;                 // cap of the grid cell size (0: none); wider boxes leave the grid
+    double resid_tol;           // per-scene residual threshold of the sweeps (0: fixed n_iter)
     int n_iter, has_ground, project, body_contacts, precision_policy;
     double h_d;
 };
@@ -102,6 +104,10 @@ struct Dev {
     int *npc, *npc_off, *gnd_cnt, *gnd_off;
     // misc
     int *ctr;                   // Counter array
+    // sweeps under a residual threshold: (sweeps done, scenes still active, loop on, -) and
+    // the scenes that have stopped
+    int *sweep_ctl;
+    unsigned char *group_done;
     long long *step_index;
     int *scan_scratch;          // block sums of the scans
 };
@@ -123,9 +129,15 @@ void launch_bond(const Dev& d, const float4* q, int it, cudaStream_t st, long lo
 // augmented Lagrangian: warm start (before the sweeps) and the update after the last sweep
 void launch_al_warm(const Dev& d, cudaStream_t st, long long* launches);
 void launch_al_final(const Dev& d, const float4* q, cudaStream_t st, long long* launches);
-void launch_solve(const Dev& d, const float4* q_in, float4* q_out, int last, int lanes, cudaStream_t st,
+void launch_solve(const Dev& d, const float4* q_in, float4* q_out, int it, int lanes, cudaStream_t st,
                   long long* launches);
 void launch_finalize(const Dev& d, const float4* q_fin, cudaStream_t st, long long* launches);
+// sweeps under a residual threshold (Dev::sweep_ctl): the loop's start, one sweep's residual
+// check and loop control (sets the conditional node's value when `handle` is non-zero), and
+// the finalize that reads the last iterate from the buffer of the sweep count's parity
+void launch_sweep_ctl_init(const Dev& d, cudaStream_t st, long long* launches);
+void launch_sweep_check(const Dev& d, unsigned long long handle, cudaStream_t st, long long* launches);
+void launch_finalize_dynamic(const Dev& d, cudaStream_t st, long long* launches);
 void launch_drive_update(const Dev& d, cudaStream_t st, long long* launches);
 // fused persistent sweep (all n_iter iterations, cooperative launch); L lanes per body
 cudaError_t launch_fused_sweep(const Dev& d, int L, int block, int grid, cudaStream_t st, long long* launches);
@@ -133,7 +145,7 @@ int fused_max_blocks(int L, int block, bool fp64);
 // one launch per sweep (bonds evaluated by the solve from CSR-ordered end records)
 void launch_end_records(const Dev& d, cudaStream_t st, long long* launches);
 void launch_sweep_one(const Dev& d, const float4* qi, float4* qo, int it, int L, cudaStream_t st,
-                      long long* launches);
+                      long long* launches, bool pdl = false);
 
 
 }  // namespace pabd

@@ -497,12 +497,14 @@ __device__ __forceinline__ unsigned lane_mask() {
 __device__ __forceinline__ void finish_body(const Dev& d, int b, int lane, float4* __restrict__ qo, int last,
                                             const float* c, const float* A, const float (*Xs)[3]);
 
+
 // Global + local solve of body b by L cooperating lanes (Eq. 19-24, Sec. 4.3):
 // G dX = M (s - q^k) + sum_ends [1; x] f'^T, X^{k+1/2} = q^k + dX, A^{k+1} = rotation of
 // A^{k+1/2}; lane 0 stores q^{k+1} and the body's squared update.  gather(sys, c, A, xs, e0,
-// e1) adds this lane's share of the body's bond ends, about the expansion point xs: in FP32 first; in the extended type X
-// (double-float, or FP64) for flagged bodies or when an FP32 Cholesky pivot falls below 1e-3
-// of its diagonal.
+// e1) adds this lane's share of the body's bond ends, about the expansion point xs: in FP32
+// first; in the extended type X (double-float, or FP64) for flagged bodies (ill-conditioned or
+// stiffly jointed, see the scene set-up) or when an FP32 Cholesky pivot falls below 1e-3 of
+// its diagonal.
 template <int L, class X, class Gather>
 __device__ __forceinline__ void solve_body(const Dev& d, int b, int lane, unsigned mask,
                                            const float4* __restrict__ qi, float4* __restrict__ qo, int last,
@@ -517,6 +519,10 @@ __device__ __forceinline__ void solve_body(const Dev& d, int b, int lane, unsign
     }
     const int e0 = d.end_off[b], e1 = d.end_off[b + 1];
     if (e1 - e0 > max_ends) return;  // solved by the heavy role (heavy_role)
+    if (d.group_done && d.group_done[d.group[b]]) {  // its scene has stopped (residual threshold)
+        if (lane == 0) { qo[3 * b] = qi[3 * b]; qo[3 * b + 1] = qi[3 * b + 1]; qo[3 * b + 2] = qi[3 * b + 2]; }
+        return;
+    }
     float c[3], A[9], sc[3], sA[9];
     ld_q(qi, b, c, A);
     ld_q(d.sq, b, sc, sA);
@@ -537,7 +543,7 @@ __device__ __forceinline__ void solve_body(const Dev& d, int b, int lane, unsign
         gather(s, c, A, xs, e0, e1);
         sys_reduce<L>(s, mask);
         const float ratio = sys_solve(s, Xs);
-        if (!(ratio >= 1e-3f) && d.p.precision_policy) {
+        if (d.p.precision_policy && !(ratio >= 1e-3f)) {
             ext = true;
             if (last && lane == 0) atomicAdd(&d.ctr[C_FP64DYN], 1);
         }
@@ -587,6 +593,41 @@ __device__ __forceinline__ void finish_body(const Dev& d, int b, int lane, float
     qo[3 * b + 2] = make_float4(An[5], An[6], An[7], An[8]);
 }
 
+// an augmented Lagrangian bond's state is stored by end i, or by end j when i is pinned
+__device__ __forceinline__ bool al_writer(const Dev& d, int4 m, int b) {
+    return (m.z == K_AL) && (m.x == b || (d.bflags[m.x] & BF_PINNED));
+}
+
+// accumulate the ends lane, lane + L, ... of body b's CSR slice (bond forces in T), in that
+// order.  Two ends per round in FP32: both records and both other bodies' iterates are loaded
+// before either force is evaluated, so a lane waits for two dependent loads per pair of ends.
+template <int L, class T>
+__device__ __forceinline__ void gather_ends(const Dev& d, const float4* __restrict__ q, int b, const float* cb,
+                                            const float* Ab, const float* xs, int e0, int e1, int lane, int it,
+                                            Sys<T>& s) {
+    int p = e0 + lane;
+    // (the FP64 redo, rare, keeps one end per round: fewer live registers)
+    if (sizeof(T) == 4) for (; p + L < e1; p += 2 * L) {
+        const int4 m0 = d.rec_m[p], m1 = d.rec_m[p + L];
+        const float4 a0 = d.rec_a[p], b0 = d.rec_b[p], a1 = d.rec_a[p + L], b1 = d.rec_b[p + L];
+        float c0[3], A0[9], c1[3], A1[9];
+        ld_q_or_zero(q, other_body(m0, b), c0, A0);
+        ld_q_or_zero(q, other_body(m1, b), c1, A1);
+        T f[3];
+        T w = end_force_q<T>(d, c0, A0, b, cb, Ab, m0, a0, b0, it, al_writer(d, m0, b), f);
+        sys_add_t(s, w, f, (m0.y == b) ? b0 : a0, xs);
+        w = end_force_q<T>(d, c1, A1, b, cb, Ab, m1, a1, b1, it, al_writer(d, m1, b), f);
+        sys_add_t(s, w, f, (m1.y == b) ? b1 : a1, xs);
+    }
+    for (; p < e1; p += L) {
+        const int4 m = d.rec_m[p];
+        const float4 xa = d.rec_a[p], xb = d.rec_b[p];
+        T f[3];
+        const T w = end_force<T>(d, q, b, cb, Ab, m, xa, xb, it, al_writer(d, m, b), f);
+        sys_add_t(s, w, f, (m.y == b) ? xb : xa, xs);
+    }
+}
+
 // ---- bodies with many bond ends: one block of HEAVY_T threads per body ----
 
 // Sum the block's partial systems: a xor butterfly inside each warp, then thread 0 adds the
@@ -622,6 +663,10 @@ __device__ __forceinline__ void solve_heavy(const Dev& d, int b, const float4* _
     __shared__ int s_ext;
     const int t = threadIdx.x;
     const int fl = d.bflags[b];
+    if (d.group_done && d.group_done[d.group[b]]) {  // its scene has stopped (residual threshold)
+        if (t == 0) { qo[3 * b] = qi[3 * b]; qo[3 * b + 1] = qi[3 * b + 1]; qo[3 * b + 2] = qi[3 * b + 2]; }
+        return;
+    }
     const int e0 = d.end_off[b], e1 = d.end_off[b + 1];
     float c[3], A[9], sc[3], sA[9];
     ld_q(qi, b, c, A);
@@ -645,7 +690,7 @@ __device__ __forceinline__ void solve_heavy(const Dev& d, int b, const float4* _
         block_reduce(s, reinterpret_cast<Sys<float>*>(buf_raw));
         if (t == 0) {
             const float ratio = sys_solve(s, Xs);
-            if (!(ratio >= 1e-3f) && d.p.precision_policy) {
+            if (d.p.precision_policy && !(ratio >= 1e-3f)) {
                 s_ext = 1;
                 if (last) atomicAdd(&d.ctr[C_FP64DYN], 1);
             }

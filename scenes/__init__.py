@@ -53,7 +53,7 @@ def default_params(**kw) -> dict:
         h=1.0 / 60.0, gravity=(0.0, -9.81, 0.0), n_iter=20,
         has_ground=1, ground_n=(0.0, 1.0, 0.0), ground_d=0.0,
         mu=0.5, c_kappa=1.0, d_hat_rel=1e-3, margin=1e-3,
-        project=1, body_contacts=1, large_he=1e30,
+        project=1, body_contacts=1, large_he=1e30, resid_tol=0.0,
     )
     p.update(kw)
     return p

@@ -89,3 +89,45 @@ def test_mass_ratio_stack_stays_upright_and_settles():
         vmax.append(np.abs(st[:, 16:19]).max())
     vmax = np.array(vmax)
     assert vmax[500:].max() < 0.25 * vmax[100:200].max()
+
+
+def _trees_two(resid_tol=0.0, n_iter=40):
+    sc = S.batched_trees(n_scenes=2, n_min=4, n_max=12, n_steps=10)
+    sc.params = dict(sc.params, n_iter=n_iter, resid_tol=resid_tol)
+    return sc
+
+
+def test_residual_threshold_stops_each_scene_at_its_first_converged_sweep():
+    """Sec. 4.2's stopping rule per scene: with a threshold, each independent scene (group)
+    keeps the iterate of the first sweep whose residual is at most the threshold.  Pinned
+    against the definition: the same scene alone with a fixed count k, the smallest k whose
+    residual is at most the threshold."""
+    tol = 1e-4
+    sc = _trees_two(resid_tol=tol)
+    o = O.OracleScene(sc)
+    o.step(3)
+    st0, k0 = o.state(), o.step_index
+    o.step(1)
+    st_tol = o.state()
+    sizes = sc.meta["sizes"]
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    for g in range(2):
+        sl = slice(off[g], off[g + 1])
+        for k in range(1, 41):
+            sub = _trees_two(n_iter=k)
+            r = O.OracleScene(sub)
+            r.set_state(st0)
+            r.step_index = k0
+            r.step(1)
+            if r.residual()[g] <= tol or k == 40:
+                assert np.array_equal(r.state()[sl], st_tol[sl]), (g, k)
+                break
+    assert o.last_sweeps() < 40
+
+
+def test_zero_threshold_changes_nothing():
+    a = O.OracleScene(_trees_two())
+    b = O.OracleScene(_trees_two(resid_tol=0.0))
+    a.step(5)
+    b.step(5)
+    assert np.array_equal(a.state(), b.state()) and a.last_sweeps() == 40
