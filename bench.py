@@ -158,24 +158,24 @@ def _tol_cfg():
 
 
 def _kernel_hash():
+    """Hash of the sources of the sweep kernels (their arithmetic and memory accesses)."""
     h = hashlib.sha256()
-    for f in ("k_sweep.cu", "k_persist.cu", "sweep_math.cuh", "pabd_internal.h"):
+    for f in ("k_sweep.cu", "k_persist.cu", "sweep_math.cuh", "dfloat.cuh"):
         with open(os.path.join(ROOT, "paper_2609_02675_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def _ncu_traffic(kernel: str):
-    """dram bytes per launch of `kernel` from the committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
+def _ncu_traffic(kernel: str, workload: str):
+    """dram bytes per launch of `kernel` on `workload` from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
             t = json.load(f)
-        e = t[kernel]
-        if e.get("source_hash") != _kernel_hash():
+        if t.get("source_hash") != _kernel_hash():
             return None
-        return e
+        return t["entries"].get(f"{kernel}|{workload}")
     except Exception:
         return None
 
@@ -413,7 +413,8 @@ def run_ours(args, rank, world, local_rank):
         ms_launch *= 2.0  # one bond + one solve launch per sweep
     achieved = per_launch_bytes / (ms_launch * 1e-3) / 1e9
     peak, peak_kind = _peaks()
-    tr = _ncu_traffic(kernel)
+    wl_key = f"{args.workload}|{'stacked' if args.stacked else 'grid'}|{sc.n_bodies}"
+    tr = _ncu_traffic(kernel, wl_key)
     roof = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
             "traffic": tr["bytes_per_launch"] if tr else None,

@@ -121,6 +121,9 @@ typedef struct {
                                  sweeps); the loop ends on the device (a conditional graph node)
                                  once every scene has stopped.  Runs the one-launch-per-sweep
                                  mode; not with AL_DISTANCE bonds (PABD_ERR_ARG). */
+    int broadphase;           /* 0: uniform grid hash (cell = widest grid box of the step, capped;
+                                 wider boxes tested against all bodies); 1: linear BVH over the
+                                 boxes' Morton codes (Sec. 5).  Both give the same pair list. */
     void* stream;             /* cudaStream_t on which all work is enqueued (NULL: default) */
     /* optional device allocator (e.g. a framework's caching allocator); NULL: cudaMalloc */
     void* (*alloc)(size_t bytes, void* ctx);

@@ -42,7 +42,7 @@ class pabd_scene_desc(ctypes.Structure):
         ("margin", ctypes.c_double), ("project", ctypes.c_int), ("body_contacts", ctypes.c_int),
         ("large_he", ctypes.c_double), ("precision_policy", ctypes.c_int),
         ("sweep_mode", ctypes.c_int), ("sweep_lanes", ctypes.c_int), ("max_pairs", ctypes.c_size_t), ("max_contacts", ctypes.c_size_t),
-        ("resid_tol", ctypes.c_double),
+        ("resid_tol", ctypes.c_double), ("broadphase", ctypes.c_int),
         ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
     ]
 
@@ -307,7 +307,7 @@ class _TorchAllocator:
 
 
 def scene_desc(params: dict, stream=0, allocator: _TorchAllocator | None = None, precision_policy=1,
-               max_pairs=0, max_contacts=0, sweep_mode=0, sweep_lanes=0) -> pabd_scene_desc:
+               max_pairs=0, max_contacts=0, sweep_mode=0, sweep_lanes=0, broadphase=0) -> pabd_scene_desc:
     d = pabd_scene_desc()
     d.h = params["h"]
     d.gravity = D3(*params["gravity"])
@@ -328,6 +328,7 @@ def scene_desc(params: dict, stream=0, allocator: _TorchAllocator | None = None,
     d.max_pairs = int(max_pairs)
     d.max_contacts = int(max_contacts)
     d.resid_tol = float(params.get("resid_tol", 0.0))
+    d.broadphase = int(broadphase)
     d.stream = stream or None
     if allocator is not None:
         d.alloc = allocator.alloc_cb
@@ -342,7 +343,8 @@ class Scene:
     """A library scene built from a ``scenes.Scene`` (bodies and user bonds)."""
 
     def __init__(self, scene, device: int = 0, stream=None, torch_memory: bool = True, precision_policy: int = 1,
-                 max_pairs: int = 0, max_contacts: int = 0, sweep_mode: int = 0, sweep_lanes: int = 0):
+                 max_pairs: int = 0, max_contacts: int = 0, sweep_mode: int = 0, sweep_lanes: int = 0,
+                 broadphase: int = 0):
         import torch
         torch.cuda.set_device(device)
         if stream is None:
@@ -350,7 +352,7 @@ class Scene:
         self.torch_stream = stream
         self._alloc = _TorchAllocator(device, stream.cuda_stream) if torch_memory else None
         self.desc = scene_desc(scene.params, stream.cuda_stream, self._alloc, precision_policy, max_pairs,
-                               max_contacts, sweep_mode, sweep_lanes)
+                               max_contacts, sweep_mode, sweep_lanes, broadphase)
         self.h = pabd_create_scene(self.desc)
         self.n = scene.n_bodies
         self.n_groups = scene.n_groups

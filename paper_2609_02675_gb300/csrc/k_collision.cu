@@ -20,7 +20,7 @@
 //
 // All arithmetic here that decides an integer (overlap, inside, face) uses __fmul_rn /
 // __fadd_rn / __fsub_rn so that no multiply-add is contracted into an FMA.
-#include "pabd_internal.h"
+#include "pair_filter.cuh"
 
 namespace pabd {
 
@@ -130,33 +130,6 @@ __global__ void k_bucket_fill(Dev d) {
         d.brec_hi[pos] = make_float4(hi.x, hi.y, hi.z, __int_as_float(d.group[b]));
         d.brec_cell[pos] = make_int4(c.x, c.y, c.z, d.bflags[b]);
     }
-}
-
-__device__ __forceinline__ bool overlap(const float4& la, const float4& ha, const float4& lb, const float4& hb) {
-    return la.x <= hb.x && lb.x <= ha.x && la.y <= hb.y && lb.y <= ha.y && la.z <= hb.z && lb.z <= ha.z;
-}
-
-// pairs joined by a user bond never collide: binary search in the body's sorted list of
-// bonded partners (a CSR built once on the host)
-__device__ __forceinline__ bool adj_has(const Dev& d, int a, int b) {
-    if (!d.adj_off) return false;
-    int lo = d.adj_off[a], hi = d.adj_off[a + 1];
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        int v = d.adj_nbr[mid];
-        if (v == b) return true;
-        if (v < b) lo = mid + 1; else hi = mid;
-    }
-    return false;
-}
-
-__device__ __forceinline__ bool pair_ok(const Dev& d, int i, int j, int gi, int fi) {
-    if (d.group[j] != gi) return false;
-    int fj = d.bflags[j];
-    if ((fi & BF_PINNED) && (fj & BF_PINNED)) return false;
-    if (!overlap(d.lo[i], d.hi[i], d.lo[j], d.hi[j])) return false;
-    if (adj_has(d, i, j)) return false;
-    return true;
 }
 
 // Pair finding, one warp per body i.  A grid body: lane c < 27 scans neighbour cell c
@@ -512,25 +485,31 @@ void launch_broadphase(const Dev& d, cudaStream_t st, long long* launches) {
 }
 
 void launch_collision(const Dev& d, cudaStream_t st, long long* launches) {
-    const int T = 1 << d.table_bits;
-    cudaMemsetAsync(d.bucket_cnt, 0, sizeof(int) * T, st);
-    cudaMemsetAsync(d.bucket_cur, 0, sizeof(int) * T, st);
     cudaMemsetAsync(d.ctr + C_CELLBITS, 0, sizeof(int), st);
     cudaMemsetAsync(d.ctr + C_NLARGE, 0, sizeof(int), st);
     k_aabb<<<nblk(d.N), CT, 0, st>>>(d);
-    k_cells<<<nblk(d.N), CT, 0, st>>>(d);
-    scan_exclusive(d.bucket_cnt, d.bucket_off, nullptr, T, d.scan_scratch, st, launches);
-    k_bucket_fill<<<nblk(d.N), CT, 0, st>>>(d);
-    const int wblk = (d.N * 32 + CT - 1) / CT > 0 ? (d.N * 32 + CT - 1) / CT : 1;  // one warp per body
-    k_pair_count<<<wblk, CT, 0, st>>>(d);
-    scan_exclusive(d.pair_cnt, d.pair_off, nullptr, d.N, d.scan_scratch, st, launches);
-    k_pair_write<<<wblk, CT, 0, st>>>(d);
+    *launches += 1;
+    if (d.p.broadphase == 1) {
+        launch_lbvh_pairs(d, st, launches);
+    } else {
+        const int T = 1 << d.table_bits;
+        cudaMemsetAsync(d.bucket_cnt, 0, sizeof(int) * T, st);
+        cudaMemsetAsync(d.bucket_cur, 0, sizeof(int) * T, st);
+        k_cells<<<nblk(d.N), CT, 0, st>>>(d);
+        scan_exclusive(d.bucket_cnt, d.bucket_off, nullptr, T, d.scan_scratch, st, launches);
+        k_bucket_fill<<<nblk(d.N), CT, 0, st>>>(d);
+        const int wblk = (d.N * 32 + CT - 1) / CT > 0 ? (d.N * 32 + CT - 1) / CT : 1;  // one warp per body
+        k_pair_count<<<wblk, CT, 0, st>>>(d);
+        scan_exclusive(d.pair_cnt, d.pair_off, nullptr, d.N, d.scan_scratch, st, launches);
+        k_pair_write<<<wblk, CT, 0, st>>>(d);
+        *launches += 4;
+    }
     const int nt = d.cap_pairs > d.N ? d.cap_pairs : d.N;
     k_narrow_count<<<nblk(nt), CT, 0, st>>>(d);
     scan_exclusive(d.npc, d.npc_off, d.ctr + C_NPAIRS, d.cap_pairs, d.scan_scratch, st, launches);
     scan_exclusive(d.gnd_cnt, d.gnd_off, nullptr, d.N, d.scan_scratch, st, launches);
     k_narrow_write<<<nblk(nt), CT, 0, st>>>(d);
-    *launches += 7;
+    *launches += 2;
 }
 
 }  // namespace pabd

@@ -1,6 +1,7 @@
 // Per-step kernels around the sweep: the predictor and the velocity recovery of Alg. 1,
 // the time-dependent drive anchors, the CSR of bond ends and the per-group residual.
 #include "pabd_internal.h"
+#include "sort_slices.cuh"
 
 namespace pabd {
 
@@ -167,25 +168,7 @@ __global__ void k_csr_sort(Dev d) {
         if (lane == 0) d.heavy[atomicAdd(&d.ctr[C_NHEAVY], 1)] = body;
         return;
     }
-    {
-        int v0 = (2 * lane < n) ? d.end_id[s + 2 * lane] : 0x7fffffff;
-        int v1 = (2 * lane + 1 < n) ? d.end_id[s + 2 * lane + 1] : 0x7fffffff;
-        for (int size = 2; size <= 64; size <<= 1) {
-            const bool up = ((2 * lane) & size) == 0;       // ascending block (same for both slots)
-            for (int stride = size >> 1; stride > 1; stride >>= 1) {
-                const bool lower = ((2 * lane) & stride) == 0; // partner k ^ stride is in lane ^ stride/2
-                const int o0 = __shfl_xor_sync(0xffffffffu, v0, stride >> 1);
-                const int o1 = __shfl_xor_sync(0xffffffffu, v1, stride >> 1);
-                v0 = (lower == up) ? min(v0, o0) : max(v0, o0);
-                v1 = (lower == up) ? min(v1, o1) : max(v1, o1);
-            }
-            const int mn = min(v0, v1), mx = max(v0, v1);  // stride 1: the lane's own pair
-            v0 = up ? mn : mx;
-            v1 = up ? mx : mn;
-        }
-        if (2 * lane < n) d.end_id[s + 2 * lane] = v0;
-        if (2 * lane + 1 < n) d.end_id[s + 2 * lane + 1] = v1;
-    }
+    warp_sort_slice64(d.end_id + s, n, lane);
     __syncwarp();
     for (int p = s + lane; p < e; p += 32) {
         const int id = d.end_id[p];
@@ -196,63 +179,15 @@ __global__ void k_csr_sort(Dev d) {
     }
 }
 
-// The heavy bodies' slices, one block per body: runs of up to LONG_SMEM ends are sorted by a
-// bitonic network in shared memory (padded with INT_MAX to a power of two); longer slices
-// then merge their sorted runs pairwise, run length doubling, each end placed at its index in
-// its run plus its rank in the partner run (a binary search; ids are unique), ping-ponging
-// through the end-record buffer (unused at this stage) as scratch.
-constexpr int LONG_T = 1024;
-constexpr int LONG_SMEM = 32768;  // ints of dynamic shared memory (128 KB)
-
+// The heavy bodies' slices, one block per body (block_sort_slice), the end-record buffer
+// (unused at this stage) as scratch.
 __global__ void __launch_bounds__(LONG_T) k_csr_sort_long(Dev d) {
     extern __shared__ int key[];
     const int nheavy = d.ctr[C_NHEAVY];
     for (int h = blockIdx.x; h < nheavy; h += gridDim.x) {
         const int body = d.heavy[h];
         const int s = d.end_off[body], e = d.end_off[body + 1], n = e - s;
-        for (int r0 = 0; r0 < n; r0 += LONG_SMEM) {
-            const int rn = min(LONG_SMEM, n - r0);
-            int m = 2;
-            while (m < rn) m <<= 1;
-            for (int k = threadIdx.x; k < m; k += LONG_T) key[k] = k < rn ? d.end_id[s + r0 + k] : 0x7fffffff;
-            __syncthreads();
-            for (int size = 2; size <= m; size <<= 1) {
-                for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                    for (int k = threadIdx.x; k < m; k += LONG_T) {
-                        const int l = k ^ stride;
-                        if (l > k) {
-                            const bool up = (k & size) == 0;
-                            const int a = key[k], b = key[l];
-                            if ((a > b) == up) { key[k] = b; key[l] = a; }
-                        }
-                    }
-                    __syncthreads();
-                }
-            }
-            for (int k = threadIdx.x; k < rn; k += LONG_T) d.end_id[s + r0 + k] = key[k];
-            __syncthreads();
-        }
-        int* src = d.end_id + s;
-        int* dst = reinterpret_cast<int*>(d.ends) + s;  // 4 ints per end slot; slots s..e-1 used
-        for (int R = LONG_SMEM; R < n; R <<= 1) {
-            for (int k = threadIdx.x; k < n; k += LONG_T) {
-                const int run = k / R, start = run * R, pstart = (run ^ 1) * R;
-                const int plen = max(0, min(R, n - pstart));
-                const int v = src[k];
-                int lo = 0, hi = plen;  // elements of the partner run below v
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (src[pstart + mid] < v) lo = mid + 1; else hi = mid;
-                }
-                dst[min(start, pstart) + (k - start) + lo] = v;
-            }
-            __syncthreads();
-            int* t = src; src = dst; dst = t;
-        }
-        if (src != d.end_id + s) {
-            for (int k = threadIdx.x; k < n; k += LONG_T) d.end_id[s + k] = src[k];
-            __syncthreads();
-        }
+        block_sort_slice(d.end_id + s, n, reinterpret_cast<int*>(d.ends) + s, key);
         for (int p = s + threadIdx.x; p < e; p += LONG_T) {
             const int id = d.end_id[p];
             const int bond = id >> 1;

@@ -291,6 +291,8 @@ pabd_status finalize_scene(pabd_scene* s) {
     p.precision_policy = ds.precision_policy;
     if (!(ds.resid_tol >= 0) || !std::isfinite(ds.resid_tol)) return PABD_ERR_ARG;
     p.resid_tol = ds.resid_tol;
+    if (ds.broadphase < 0 || ds.broadphase > 1) return PABD_ERR_ARG;
+    p.broadphase = ds.broadphase;
     // capacities
     // the two-level scans cover 4096 x 4096 values; bond ends are counted in int.  Defaults:
     // 16 pairs and 32 contacts per body (a dense granular bed reaches about 24), clamped to
@@ -359,7 +361,7 @@ pabd_status finalize_scene(pabd_scene* s) {
     // Static extended-precision flag (reading R18): the FP64 Cholesky of the diagonally scaled
     // static-only system about x_s has a pivot below 1e-2 of its diagonal (ten times the
     // dynamic test's margin, since contacts add to the system at run time), or the static
-    // bonds' weights sum to more than 100 times the mass (BF_STIFF).
+    // bonds' weights sum to more than 10 times the mass (BF_STIFF).
     std::vector<double> sw(N, 0.0), swx(3 * (size_t)N, 0.0);
     for (const HostBond& hb : s->bonds) {
         if (hb.i >= 0) { sw[hb.i] += hb.w; for (int k = 0; k < 3; ++k) swx[3 * hb.i + k] += hb.w * hb.xi[k]; }
@@ -373,7 +375,7 @@ pabd_status finalize_scene(pabd_scene* s) {
         for (int k = 0; k < 3; ++k) xsd[3 * b + k] = swx[3 * b + k] / (m + sw[b]);
         xs[b] = make_float4((float)xsd[3 * b], (float)xsd[3 * b + 1], (float)xsd[3 * b + 2], 0.f);
         if (xs[b].x != 0.f || xs[b].y != 0.f || xs[b].z != 0.f) flags[b] |= BF_SHIFT;
-        if (sw[b] > 100.0 * m) flags[b] |= BF_STIFF;
+        if (sw[b] > 10.0 * m) flags[b] |= BF_STIFF;
         // the shifted expansion point as the device uses it (rounded to FP32)
         for (int k = 0; k < 3; ++k) xsd[3 * b + k] = k == 0 ? xs[b].x : (k == 1 ? xs[b].y : xs[b].z);
     }
@@ -418,9 +420,10 @@ pabd_status finalize_scene(pabd_scene* s) {
             }
         }
         // stiffly jointed bodies too: their FP32 system resolves a joint correction only to
-        // about 1e-4 (joint weights thousands of times the mass against a rotational inertia
-        // that is not -- the cancellation lands on the rotation), and taking them straight to
-        // the extended type costs less than a test-and-redo
+        // about 1e-4 (joint weights many times the mass against a rotational inertia that is
+        // not -- the cancellation lands on the rotation), errors that the joints pass on to
+        // their neighbours; taking them straight to the extended type costs less than a
+        // test-and-redo
         if (!(worst >= 1e-2) || (flags[b] & BF_STIFF)) { flags[b] |= BF_FP64; s->fp64_bodies++; }
     }
     // static bonds
@@ -499,6 +502,7 @@ pabd_status finalize_scene(pabd_scene* s) {
     ok &= alloc_arr(s, d.gnd_cnt, N) && alloc_arr(s, d.gnd_off, N + 1);
     ok &= alloc_arr(s, d.ctr, C_COUNT) && alloc_arr(s, d.step_index, 1);
     int ns = scan_scratch_ints(T);
+    ns = std::max(ns, scan_scratch_ints(256 * (N / 1024 + 1)));
     ns = std::max(ns, scan_scratch_ints(N + 1));
     ns = std::max(ns, scan_scratch_ints(d.cap_pairs));
     ok &= alloc_arr(s, d.scan_scratch, ns);
@@ -507,6 +511,15 @@ pabd_status finalize_scene(pabd_scene* s) {
     }
     if (d.Nal) ok &= alloc_arr(s, d.al_st0, Nc) && alloc_arr(s, d.al_st1, Nc) && alloc_arr(s, d.al_par, Nc);
     if (p.resid_tol > 0) ok &= alloc_arr(s, d.sweep_ctl, 4) && alloc_arr(s, d.group_done, d.G);
+    if (p.broadphase == 1) {
+        const size_t ntile = ((size_t)N + 1023) / 1024 + 1;
+        ok &= alloc_arr(s, d.bvh_key, N) && alloc_arr(s, d.bvh_key2, N) && alloc_arr(s, d.bvh_id, N) &&
+              alloc_arr(s, d.bvh_id2, N) && alloc_arr(s, d.rx_cnt, 256 * ntile) && alloc_arr(s, d.rx_off, 256 * ntile + 1);
+        ok &= alloc_arr(s, d.bvh_kids, N) && alloc_arr(s, d.bvh_parent, 2 * (size_t)N) && alloc_arr(s, d.bvh_lo, N) &&
+              alloc_arr(s, d.bvh_hi, N) && alloc_arr(s, d.bvh_visit, N) && alloc_arr(s, d.bvh_bounds, 6);
+        ok &= alloc_arr(s, d.pair_j, d.cap_pairs) && alloc_arr(s, d.pair_tmp, d.cap_pairs) &&
+              alloc_arr(s, d.pair_heavy, N);
+    }
     if (!ok) return PABD_ERR_OOM;
 
     cudaStream_t st = s->st;
@@ -546,6 +559,7 @@ pabd_status finalize_scene(pabd_scene* s) {
 
     // lanes per body from the descriptor; fused sweep block / grid from a timing sweep
     CK(setup_csr_kernels());
+    if (p.broadphase == 1) CK(setup_lbvh_kernels());
 
     // lanes per body: given, or from the body count -- the largest of 16, 8, 4, 2, 1 lanes
     // with lanes * N <= 2^17 (the measured optimum on piles of 4 k to 1 M bodies and on the

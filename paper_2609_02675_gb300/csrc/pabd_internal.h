@@ -19,7 +19,7 @@ enum BondKind { K_SPHERICAL = 0, K_SPRING = 1, K_ELASTIC_NL = 2, K_DRIVE = 4, K_
 enum StatusBits { ST_CAPACITY = 1, ST_DIVERGED = 2, ST_TIMEOUT = 4 };
 
 // BF_SHIFT: the body's system is assembled about a nonzero expansion point Dev::xs.
-// BF_STIFF: its static bonds' weights sum to more than 100 times its mass (stiff joints).
+// BF_STIFF: its static bonds' weights sum to more than 10 times its mass (stiff joints).
 enum BodyFlags { BF_PINNED = 1, BF_FP64 = 2, BF_LARGE = 4, BF_SHIFT = 8, BF_STIFF = 16 };
 
 // device counters (ints) -- one small array so that one memset resets them
@@ -33,6 +33,7 @@ enum Counter {
     C_FP64DYN,         // bodies that switched to FP64 by the pivot test (last sweep)
     C_NHEAVY,          // bodies with more than HEAVY_ENDS bond ends this step (list in Dev::heavy)
     C_NLARGE,          // bodies off the grid this step (list in Dev::large_ids)
+    C_NPHEAVY,         // bodies with more than 64 LBVH partners this step (list in Dev::pair_heavy)
     C_COUNT
 };
 
@@ -43,6 +44,7 @@ struct Params {
     float mu, c_kappa, d_hat_rel, margin;
     float cell;                 // cap of the grid cell size (0: none); wider boxes leave the grid
     double resid_tol;           // per-scene residual threshold of the sweeps (0: fixed n_iter)
+    int broadphase;             // 0: uniform grid hash, 1: linear BVH
     int n_iter, has_ground, project, body_contacts, precision_policy;
     double h_d;
 };
@@ -102,6 +104,17 @@ struct Dev {
     int *pair_cnt, *pair_off;
     int2 *pairs;
     int *npc, *npc_off, *gnd_cnt, *gnd_off;
+    // linear BVH broad phase (Params::broadphase == 1)
+    unsigned *bvh_key, *bvh_key2;   // Morton codes (radix sort ping-pong)
+    int *bvh_id, *bvh_id2;          // body ids in Morton order
+    int *rx_cnt, *rx_off;           // radix sort: counts per (digit, tile) and their prefix sums
+    int2 *bvh_kids;                 // children of the internal nodes (leaf k is node N - 1 + k)
+    int *bvh_parent;                // parent of every node (-1 at the root)
+    float4 *bvh_lo, *bvh_hi;        // boxes of the internal nodes
+    int *bvh_visit;                 // refit arrivals per internal node
+    int *bvh_bounds;                // box of the centres (order-preserving int bits: min xyz, max xyz)
+    int *pair_j, *pair_tmp;         // partner slices while they are sorted
+    int *pair_heavy;                // bodies with more than 64 partners
     // misc
     int *ctr;                   // Counter array
     // sweeps under a residual threshold: (sweeps done, scenes still active, loop on, -) and
@@ -120,6 +133,9 @@ void scan_exclusive(const int* in, int* out, const int* n_dev, int n_cap, int* s
 int scan_scratch_ints(int n_cap);
 
 void launch_collision(const Dev& d, cudaStream_t st, long long* launches);
+// LBVH pairs from this step's boxes (after k_aabb): the same output as the grid's pair stage
+void launch_lbvh_pairs(const Dev& d, cudaStream_t st, long long* launches);
+cudaError_t setup_lbvh_kernels();
 void launch_broadphase(const Dev& d, cudaStream_t st, long long* launches);
 void launch_csr(const Dev& d, cudaStream_t st, long long* launches);
 // opt the CSR block sort into its 128 KB of dynamic shared memory (once per process and device)

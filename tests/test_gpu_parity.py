@@ -521,3 +521,49 @@ def test_residual_threshold_graph_and_eager_identical(P):
     assert a.info()["last_sweeps"] == b.info()["last_sweeps"]
     a.close()
     b.close()
+
+
+# --------------------------------------------------------------------------------------
+# LBVH broad phase: the same pair list as the grid hash (and the oracle), bit for bit
+# --------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("make,steps", [(lambda: S.box_pile(nx=6, ny=6, nz=6, spacing=2.3), (0, 40, 90)),
+                                        (lambda: S.quadruped_bed_rod(bed=(12, 2, 12), n_rod=16), (0, 15, 30)),
+                                        (lambda: S.slab_pile(48), (0, 3)),
+                                        (lambda: S.batched_trees(n_scenes=24), (0, 12))])
+def test_lbvh_pairs_match_grid_and_oracle(P, make, steps):
+    sc = make()
+    ref = O.OracleScene(sc)
+    grid = P.Scene(sc)
+    bvh = P.Scene(sc, broadphase=1)
+    done, checked = 0, 0
+    for k in range(max(steps) + 1):
+        if k in steps:
+            st = ref.state()
+            for g in (grid, bvh):
+                g.set_state(st)
+                g.set_step_index(ref.step_index)
+                g.detect()
+            ref.detect()
+            rp = ref.pairs()
+            assert np.array_equal(bvh.pairs(), rp), (k, len(bvh.pairs()), len(rp))
+            assert np.array_equal(grid.pairs(), rp)
+            same_contacts(bvh.contacts(), ref.contacts())
+            done += len(rp)
+            checked += 1
+        ref.step(1)
+    assert checked == len(steps)
+    assert done > 0 or not sc.params["body_contacts"]
+    grid.close()
+    bvh.close()
+
+
+def test_lbvh_and_grid_steps_identical(P):
+    """Same pairs, so the same contacts and the same steps, bit for bit."""
+    sc = S.quadruped_bed_rod(bed=(12, 2, 12), n_rod=16)
+    a, b = P.Scene(sc), P.Scene(sc, broadphase=1)
+    a.step(30)
+    b.step(30)
+    assert np.array_equal(a.state(), b.state())
+    a.close()
+    b.close()
