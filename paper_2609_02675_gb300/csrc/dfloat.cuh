@@ -52,6 +52,12 @@ __device__ __forceinline__ df operator+(df x, df y) {
     return fast_two_sum(v.hi, __fadd_rn(t.lo, v.lo));
 }
 
+// a double-word plus a float (JMP's DWPlusFP)
+__device__ __forceinline__ df operator+(df x, float y) {
+    const df s = two_sum(x.hi, y);
+    return fast_two_sum(s.hi, __fadd_rn(x.lo, s.lo));
+}
+
 __device__ __forceinline__ df operator-(df x) { return df(-x.hi, -x.lo, 0); }
 __device__ __forceinline__ df operator-(df x, df y) { return x + (-y); }
 
@@ -60,6 +66,13 @@ __device__ __forceinline__ df operator*(df x, df y) {
     const float t = __fmaf_rn(x.hi, y.lo, __fmul_rn(x.lo, y.lo));
     return fast_two_sum(c.hi, __fadd_rn(c.lo, __fmaf_rn(x.lo, y.hi, t)));
 }
+
+// a double-word times a float (JMP's DWTimesFP with FMA)
+__device__ __forceinline__ df operator*(df x, float y) {
+    const df c = two_prod(x.hi, y);
+    return fast_two_sum(c.hi, __fmaf_rn(x.lo, y, c.lo));
+}
+__device__ __forceinline__ df operator*(float y, df x) { return x * y; }
 
 __device__ __forceinline__ df operator/(df x, df y) {
     const float th = __fdiv_rn(x.hi, y.hi);
@@ -70,6 +83,7 @@ __device__ __forceinline__ df operator/(df x, df y) {
 }
 
 __device__ __forceinline__ df& operator+=(df& x, df y) { return x = x + y; }
+__device__ __forceinline__ df& operator+=(df& x, float y) { return x = x + y; }
 __device__ __forceinline__ df& operator-=(df& x, df y) { return x = x - y; }
 __device__ __forceinline__ df& operator*=(df& x, df y) { return x = x * y; }
 

@@ -7,8 +7,8 @@
 // arithmetic as the bond kernel of the two-launch path -- and accumulate their share of the
 // 4x4 system G dX = R; the shares are combined by a fixed butterfly of warp shuffles, so the
 // result depends only on L, never on scheduling.  Every lane then solves, projects, and
-// lane 0 stores q^{k+1}.  Bodies whose factorisation is ill-conditioned redo the
-// accumulation and the solve in FP64 (same rule as the two-launch path).
+// lane 0 stores q^{k+1}.  Bodies whose factorisation is ill-conditioned accumulate the same
+// single-precision forces and solve in the extended type (same rule as the two-launch path).
 //
 // The grid barrier is a counter + generation word in device memory; every wait is bounded
 // (about a second), after which the block records PABD_ERR_TIMEOUT and leaves the kernel.

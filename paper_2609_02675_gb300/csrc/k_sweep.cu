@@ -14,11 +14,9 @@
 //            (the polar decomposition of sweep_math.cuh: Newton-Schulz, with Higham's
 //            scaled Newton iteration and an eigen-decomposition of A^T A as fallbacks).
 //            FP32, except bodies whose 4x4 factorisation is ill-conditioned (statically
-//            flagged, or a Cholesky pivot below 1e-4 of its diagonal): those re-gather and
-//            factor in an extended type -- double-float on the FP32 pipes (precision
-//            policy 1), or FP64 (policy 2).
-#include <type_traits>
-
+//            flagged, or a Cholesky pivot below 1e-3 of its diagonal): those sum the same
+//            single-precision records and factor in an extended type -- double-float on
+//            the FP32 pipes (precision policy 1), or FP64 (policy 2).
 #include "sweep_math.cuh"
 
 namespace pabd {
@@ -38,21 +36,17 @@ __global__ void __launch_bounds__(BOND_T) k_bond(Dev d, const float4* __restrict
     // a bond between two fixed ends is advanced by the final update alone (as in the sweep kernels)
     const bool writer = !(fi & BF_PINNED) || !(fj & BF_PINNED);
     float f[3];
-    const float w = end_force<float>(d, q, m.x, c, A, mm, xi, xj, it, writer, f);
+    const float w = end_force(d, q, m.x, c, A, mm, xi, xj, it, writer, f);
     const int p0 = d.end_pos[2 * b], p1 = (m.y >= 0) ? d.end_pos[2 * b + 1] : -1;
     if (p0 >= 0) d.ends[p0] = make_float4(w, f[0], f[1], f[2]);
     if (p1 >= 0) d.ends[p1] = make_float4(w, -f[0], -f[1], -f[2]);
 }
 
-// The FP32 records of the bond kernel are summed; a body on the extended path evaluates its
-// ends again in the extended type from the CSR-ordered records (as the one-launch sweep does),
-// so the two modes agree bit for bit.
-template <class T>
-constexpr bool is_fp32_sys() { return std::is_same<T, Sys<float>>::value; }
-
-// one body per group of L lanes; lane l adds the body's ends l, l + L, ... (float records).
-// The first `light` blocks take the bodies with at most HEAVY_ENDS ends; the HEAVY_BLOCKS
-// blocks after them take the heavy bodies, a block each.
+// One body per group of L lanes; lane l adds the bond kernel's records of the body's ends
+// l, l + L, ... -- in FP32, or in the extended type for a body on the extended path (the same
+// records and order as the one-launch sweep, so the two modes agree bit for bit).  The first
+// `light` blocks take the bodies with at most HEAVY_ENDS ends; the HEAVY_BLOCKS blocks after
+// them take the heavy bodies, a block each.
 template <int L, class X>
 __global__ void __launch_bounds__(SOLVE_T, 4) k_solve(Dev d, const float4* __restrict__ qi, float4* __restrict__ qo,
                                                    int it, int light) {
@@ -60,18 +54,10 @@ __global__ void __launch_bounds__(SOLVE_T, 4) k_solve(Dev d, const float4* __res
     if ((int)blockIdx.x >= light) {
         heavy_role<X>(d, blockIdx.x - light, qi, qo, last,
             [&](int b, auto& s, const float* c, const float* A, const float* xs, int e0, int e1, int ln) {
-                if constexpr (is_fp32_sys<std::decay_t<decltype(s)>>()) {
-                    for (int p = e0 + ln; p < e1; p += 32) sys_add(s, d.ends[p], d.end_x[p], xs);
-                } else {
-                    gather_ends<32>(d, qi, b, c, A, xs, e0, e1, ln, it, s);
-                }
+                for (int p = e0 + ln; p < e1; p += 32) sys_add(s, d.ends[p], d.end_x[p], xs);
             },
             [&](int b, auto& s, const float* c, const float* A, const float* xs, int e0, int e1, int t) {
-                if constexpr (is_fp32_sys<std::decay_t<decltype(s)>>()) {
-                    for (int p = e0 + t; p < e1; p += HEAVY_T) sys_add(s, d.ends[p], d.end_x[p], xs);
-                } else {
-                    gather_ends<HEAVY_T>(d, qi, b, c, A, xs, e0, e1, t, it, s);
-                }
+                for (int p = e0 + t; p < e1; p += HEAVY_T) sys_add(s, d.ends[p], d.end_x[p], xs);
             });
         return;
     }
@@ -80,11 +66,7 @@ __global__ void __launch_bounds__(SOLVE_T, 4) k_solve(Dev d, const float4* __res
     if (b >= d.N) return;
     solve_body<L, X>(d, b, lane, lane_mask<L>(), qi, qo, last,
                      [&](auto& s, const float* c, const float* A, const float* xs, int e0, int e1) {
-        if constexpr (is_fp32_sys<std::decay_t<decltype(s)>>()) {
-            for (int p = e0 + lane; p < e1; p += L) sys_add(s, d.ends[p], d.end_x[p], xs);
-        } else {
-            gather_ends<L>(d, qi, b, c, A, xs, e0, e1, lane, it, s);
-        }
+        for (int p = e0 + lane; p < e1; p += L) sys_add(s, d.ends[p], d.end_x[p], xs);
     });
 }
 

