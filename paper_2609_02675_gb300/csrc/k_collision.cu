@@ -201,6 +201,7 @@ __global__ void k_pair_count(Dev d) {
     if (d.p.body_contacts) {
         const int gi = d.group[i], fi = d.bflags[i];
         if (d.cell[i].w < 0) {
+            if (d.offgrid_sep) return;  // counted by k_offgrid_pairs
             for (int j0 = i + 1; j0 < d.N; j0 += 32) {
                 const int j = j0 + lane;
                 n += (j < d.N && pair_ok(d, i, j, gi, fi)) ? 1 : 0;
@@ -221,7 +222,9 @@ __global__ void k_pair_write(Dev d) {
     const int cap = d.cap_pairs;
     if (d.p.body_contacts) {
         const int gi = d.group[i], fi = d.bflags[i];
-        if (d.cell[i].w < 0) {
+        if (d.cell[i].w < 0 && d.offgrid_sep) {
+            // written by k_offgrid_pairs
+        } else if (d.cell[i].w < 0) {
             int pos = s;
             for (int j0 = i + 1; j0 < d.N; j0 += 32) {
                 const int j = j0 + lane;
@@ -253,6 +256,57 @@ __global__ void k_pair_write(Dev d) {
         int tot = d.pair_off[d.N];
         if (tot > cap) atomicOr(&d.ctr[C_STATUS], ST_CAPACITY);
         d.ctr[C_NPAIRS] = min(tot, cap);
+    }
+}
+
+// Pairs of the bodies off the grid when a scene has some by design (very wide bodies, or a
+// cell cap below the widest box): body i of the off-grid list against every j > i, one block
+// of OFF_T threads per body.  Warp w takes the w-th of 32 contiguous runs of (i, N), so the
+// warps' hits concatenated in warp order keep the slice sorted by j; the runs' loads are
+// independent, so a body's scan costs about N / OFF_T dependent rounds instead of N / 32.
+// WRITE = false counts (pair_cnt[i], and each warp's count in lane_cnt[32 i + w]); true stores.
+constexpr int OFF_T = 1024;
+constexpr int OFF_BLOCKS = 152;
+
+template <bool WRITE>
+__global__ void __launch_bounds__(OFF_T) k_offgrid_pairs(Dev d) {
+    __shared__ int s_cnt[OFF_T / 32];
+    if (!d.p.body_contacts) return;
+    const int nl = d.ctr[C_NLARGE];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cap = d.cap_pairs;
+    for (int h = blockIdx.x; h < nl; h += gridDim.x) {
+        const int i = d.large_ids[h];
+        const int gi = d.group[i], fi = d.bflags[i];
+        const int len = (((d.N - i - 1) + 31) / 32 + 31) & ~31;  // per warp, a multiple of 32
+        const int j_beg = i + 1 + w * len, j_end = min(d.N, j_beg + len);
+        if (!WRITE) {
+            int n = 0;
+            for (int j0 = j_beg; j0 < j_end; j0 += 32) {
+                const int j = j0 + lane;
+                n += (j < j_end && pair_ok(d, i, j, gi, fi)) ? 1 : 0;
+            }
+            n = warp_sum(n);
+            if (lane == 0) { d.lane_cnt[32 * i + w] = n; s_cnt[w] = n; }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int t = 0;
+                for (int k = 0; k < OFF_T / 32; ++k) t += s_cnt[k];
+                d.pair_cnt[i] = t;
+            }
+            __syncthreads();
+        } else {
+            int pos = d.pair_off[i];
+            for (int k = 0; k < w; ++k) pos += d.lane_cnt[32 * i + k];
+            for (int j0 = j_beg; j0 < j_end; j0 += 32) {
+                const int j = j0 + lane;
+                const bool ok = j < j_end && pair_ok(d, i, j, gi, fi);
+                const unsigned bal = __ballot_sync(0xffffffffu, ok);
+                const int at = pos + __popc(bal & ((1u << lane) - 1u));
+                if (ok && at < cap) d.pairs[at] = make_int2(i, j);
+                pos += __popc(bal);
+            }
+        }
     }
 }
 
@@ -500,9 +554,11 @@ void launch_collision(const Dev& d, cudaStream_t st, long long* launches) {
         k_bucket_fill<<<nblk(d.N), CT, 0, st>>>(d);
         const int wblk = (d.N * 32 + CT - 1) / CT > 0 ? (d.N * 32 + CT - 1) / CT : 1;  // one warp per body
         k_pair_count<<<wblk, CT, 0, st>>>(d);
+        if (d.offgrid_sep) k_offgrid_pairs<false><<<OFF_BLOCKS, OFF_T, 0, st>>>(d);
         scan_exclusive(d.pair_cnt, d.pair_off, nullptr, d.N, d.scan_scratch, st, launches);
         k_pair_write<<<wblk, CT, 0, st>>>(d);
-        *launches += 4;
+        if (d.offgrid_sep) k_offgrid_pairs<true><<<OFF_BLOCKS, OFF_T, 0, st>>>(d);
+        *launches += 4 + (d.offgrid_sep ? 2 : 0);
     }
     const int nt = d.cap_pairs > d.N ? d.cap_pairs : d.N;
     k_narrow_count<<<nblk(nt), CT, 0, st>>>(d);

@@ -3,12 +3,94 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/pabd.h"
 #include "pabd_internal.h"
+
+namespace {
+
+// Cap of the grid cell.  Every grid body tests the bodies of the 27 cells around its own, so
+// the cell should be about as wide as the common box rather than the widest one: a few much
+// wider boxes are cheaper off the grid, where each is tested against all N bodies.  The
+// candidates are 1.25 x the widest grid box at rest (inflated by dhat and the margin) and
+// 1.25 x the width that leaves the widest 8, 32, 128 or 512 boxes off the grid.  Each is
+// scored by the pair tests it would take at the positions of creation: the bodies in the 27
+// cells around each body (counted on a strided sample of at most 2^18 bodies, scaled back),
+// plus 1.5 N per body off the grid; the cheapest wins.  With a single candidate (boxes of
+// similar size) nothing is counted.
+double grid_cell_cap(const std::vector<pabd_body_desc>& bodies, const std::vector<int>& flags,
+                     const pabd_scene_desc& ds, bool* below_widest) {
+    *below_widest = false;
+    const int N = (int)bodies.size();
+    std::vector<double> w;
+    std::vector<int> ids;
+    for (int b = 0; b < N; ++b) {
+        if (flags[b] & pabd::BF_LARGE) continue;
+        const double* he = bodies[b].he;
+        const double hn = std::sqrt(he[0] * he[0] + he[1] * he[1] + he[2] * he[2]);
+        const double dh = ds.d_hat_rel * 2.0 * std::min(std::min(he[0], he[1]), he[2]);
+        w.push_back(2.0 * hn + 2.0 * (dh + ds.margin));
+        ids.push_back(b);
+    }
+    if (w.empty()) return 0.0;
+    std::vector<double> sorted = w;
+    std::sort(sorted.begin(), sorted.end(), [](double a, double b) { return a > b; });
+    std::vector<double> caps = {1.25 * sorted[0]};
+    if (ds.body_contacts) {
+        for (int k : {8, 32, 128, 512}) {
+            if (k >= (int)sorted.size() / 4) break;
+            const double c = 1.25 * sorted[k];
+            if (c < 0.8 * caps.back()) caps.push_back(c);
+        }
+    }
+    if (caps.size() == 1) return caps[0];
+    const int n = (int)w.size();
+    const int stride = std::max(1, n / (1 << 18));
+    double best = caps[0], best_cost = -1.0;
+    for (const double cap : caps) {
+        double cell = 0.0;
+        long long off = 0;
+        for (int i = 0; i < n; ++i) {
+            if (w[i] > cap) ++off;
+            else cell = std::max(cell, w[i]);
+        }
+        cell *= 1.01;
+        auto key = [&](long long x, long long y, long long z) {
+            return (uint64_t)((x & 0x1fffff) | ((y & 0x1fffff) << 21) | ((z & 0x1fffff) << 42));
+        };
+        std::unordered_map<uint64_t, int> cnt;
+        std::vector<long long> cx(n), cy(n), cz(n);
+        for (int i = 0; i < n; ++i) {
+            const double* c = bodies[ids[i]].c;
+            cx[i] = (long long)std::floor(c[0] / cell);
+            cy[i] = (long long)std::floor(c[1] / cell);
+            cz[i] = (long long)std::floor(c[2] / cell);
+            if (i % stride == 0 && w[i] <= cap) ++cnt[key(cx[i], cy[i], cz[i])];
+        }
+        double tests = 0.0;
+        for (int i = 0; i < n; i += stride) {
+            if (w[i] > cap) continue;
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        auto it = cnt.find(key(cx[i] + dx, cy[i] + dy, cz[i] + dz));
+                        if (it != cnt.end()) tests += it->second;
+                    }
+        }
+        tests *= (double)stride * stride;
+        const double cost = tests + 1.5 * (double)N * (double)off;
+        if (best_cost < 0.0 || cost < best_cost) { best_cost = cost; best = cap; }
+    }
+    *below_widest = best < caps[0];
+    return best;
+}
+
+}  // namespace
 
 using namespace pabd;
 
@@ -344,18 +426,10 @@ pabd_status finalize_scene(pabd_scene* s) {
     }
     for (int g = 1; g <= d.G; ++g) if (group_off[g] < group_off[g - 1]) group_off[g] = group_off[g - 1];
     d.Nlarge = (int)large.size();
-    // cap of the grid cell: 1.25 x the widest box of a grid body at rest (any orientation:
-    // twice the half-extent norm, plus twice dhat + margin); faster bodies whose inflated box
-    // outgrows it leave the grid for that step
-    double cell = 0.0;
-    for (int b = 0; b < N; ++b) {
-        if (flags[b] & BF_LARGE) continue;
-        const pabd_body_desc& bd = s->bodies[b];
-        const double hn = std::sqrt(bd.he[0] * bd.he[0] + bd.he[1] * bd.he[1] + bd.he[2] * bd.he[2]);
-        const double dh = ds.d_hat_rel * 2.0 * std::min(std::min(bd.he[0], bd.he[1]), bd.he[2]);
-        cell = std::max(cell, 2.0 * hn + 2.0 * (dh + ds.margin));
-    }
-    p.cell = (float)(1.25 * cell);
+    bool cap_below_widest = false;
+    p.cell = (float)grid_cell_cap(s->bodies, flags, ds, &cap_below_widest);
+    // scenes with off-grid bodies by design take their pairs from a block-parallel kernel
+    d.offgrid_sep = ds.body_contacts && (d.Nlarge > 0 || cap_below_widest);
     // Expansion point of each body's system (sys_init): x_s = sum w x / (m + sum w) over the
     // ends of its static bonds (w = h^2 kappa; a drive's moving anchor at its rest angle).
     // Static extended-precision flag (reading R18): the FP64 Cholesky of the diagonally scaled

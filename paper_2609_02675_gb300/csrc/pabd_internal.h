@@ -65,6 +65,7 @@ struct Dev {
     int N, Nc, Ndrive, G, Nlarge;
     int cap_pairs, cap_contacts, cap_bonds, cap_ends;
     int table_bits;             // grid hash table has 1 << table_bits buckets
+    int offgrid_sep;            // pairs of off-grid bodies from their own kernel (k_offgrid_pairs)
     // bodies
     float4 *qn, *qa, *qb, *sq;  // 3 float4 per body each
     float4 *vel, *omg, *quat, *qstar;
