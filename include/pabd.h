@@ -121,9 +121,11 @@ typedef struct {
                                  sweeps); the loop ends on the device (a conditional graph node)
                                  once every scene has stopped.  Runs the one-launch-per-sweep
                                  mode; not with AL_DISTANCE bonds (PABD_ERR_ARG). */
-    int broadphase;           /* 0: uniform grid hash (cell = widest grid box of the step, capped;
-                                 wider boxes tested against all bodies); 1: linear BVH over the
-                                 boxes' Morton codes (Sec. 5).  Both give the same pair list. */
+    int broadphase;           /* 0: uniform grid hash (cell = widest grid box of the step under a
+                                 cap chosen at creation; in scenes of very different widths, three
+                                 grid levels with caps 1, 4 and 16 times it, and wider boxes tested
+                                 against all bodies); 1: linear BVH over the boxes' Morton codes
+                                 (Sec. 5).  Both give the same pair list. */
     void* stream;             /* cudaStream_t on which all work is enqueued (NULL: default) */
     /* optional device allocator (e.g. a framework's caching allocator); NULL: cudaMalloc */
     void* (*alloc)(size_t bytes, void* ctx);
@@ -171,10 +173,13 @@ typedef struct {
     int64_t coop_fallbacks;   /* steps whose cooperative sweep launch was refused and ran as
                                  two launches per sweep instead */
     int64_t heavy_bodies;     /* bodies of the last step with more than 64 bond ends, each
-                                 gathered and solved by a block of 256 threads */
+                                 gathered and solved by a warp (up to 256 ends) or a block of
+                                 128 threads */
     int64_t fp64_dynamic;     /* bodies that took the extended-precision redo in the last sweep
                                  of the last step because of a small FP32 pivot */
     int64_t last_sweeps;      /* sweeps the last step ran (n_iter unless resid_tol ended it) */
+    int64_t offgrid_bodies;   /* bodies the last step's grid broad phase took off the grid
+                                 (flagged large, or a box wider than the cell cap) */
 } pabd_info;
 
 /* Create an empty scene on the current CUDA device.  *out receives the handle. */

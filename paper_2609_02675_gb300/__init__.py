@@ -69,7 +69,7 @@ class pabd_info(ctypes.Structure):
         "n_bodies", "n_groups", "n_static_bonds", "n_bonds", "n_pairs", "n_contacts", "step_index",
         "max_pairs", "max_contacts", "graph_nodes", "launches", "fp64_bodies", "device_bytes",
         "sweep_mode", "sweep_lanes", "sweep_block", "sweep_grid", "coop_fallbacks", "heavy_bodies",
-        "fp64_dynamic", "last_sweeps")]
+        "fp64_dynamic", "last_sweeps", "offgrid_bodies")]
 
 
 _P = ctypes.c_void_p

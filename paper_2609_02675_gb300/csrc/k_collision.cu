@@ -3,14 +3,16 @@
 // Broad phase: uniform grid hash.  Every body's inflated AABB is computed in IEEE single
 // precision with a fixed operation order.  The cell size is the widest grid box of the step
 // (times 1.01), so two overlapping grid boxes always sit in the same or in adjacent cells.
-// A scene caps it at creation from its grid bodies' extents (with an allowance for their
-// motion): a body whose inflated box is wider than the cap this step -- one flagged larger
-// than the scene's `large_he`, or one moving fast -- goes off the grid and is tested against
-// all bodies instead of widening every cell.  Bodies are counting-sorted into hash
-// buckets; each body scans the 27 cells around its own and keeps the neighbours j > i whose
-// boxes overlap, whose cell really is the visited one (so hash collisions never duplicate a
-// pair), that share its group and are not joined to it by a user bond.  Each body's partner list is sorted, so the
-// final list is the sorted set of overlapping pairs -- independent of bucket order.
+// A scene caps it at creation (grid_cell_cap: the widest box at rest, or below it when a few
+// much wider boxes make that cheaper): a body whose inflated box is wider than the cap this
+// step -- one flagged larger than the scene's `large_he`, or one moving fast -- goes off the
+// grid and is tested against all bodies instead of widening every cell.  Scenes with such
+// bodies by design use a multilevel grid instead (below), where a fast body moves up a level
+// rather than off the grid.  Bodies are counting-sorted into hash buckets; each body scans
+// the 27 cells around its own and keeps the neighbours j > i whose boxes overlap, whose cell
+// really is the visited one (so hash collisions never duplicate a pair), that share its group
+// and are not joined to it by a user bond.  Each body's partner list is sorted, so the final
+// list is the sorted set of overlapping pairs -- independent of bucket order.
 //
 // Narrow phase: box-box contact manifold (reference face by separating axis over the six
 // face normals, incident face clipped against the reference face's side planes) and
@@ -21,6 +23,7 @@
 // All arithmetic here that decides an integer (overlap, inside, face) uses __fmul_rn /
 // __fadd_rn / __fsub_rn so that no multiply-add is contracted into an FMA.
 #include "pair_filter.cuh"
+#include "sort_slices.cuh"
 
 namespace pabd {
 
@@ -29,6 +32,8 @@ namespace pabd {
 #define FS(a, b) __fsub_rn((a), (b))
 
 constexpr int CT = 256;  // threads per block for per-body / per-pair kernels
+constexpr int NLEV = 3;           // levels of the multilevel grid
+constexpr float LEV_RATIO = 4.f;  // cap ratio of consecutive levels
 
 struct FBox {
     float c[3], A[9], he[3], infl;
@@ -79,12 +84,23 @@ __global__ void k_aabb(Dev d) {
     // wider than the cap leaves the grid instead of widening every cell.
     const float w = fmaxf(fmaxf(FS(hi[0], lo[0]), FS(hi[1], lo[1])), FS(hi[2], lo[2]));
     bool large = d.bflags[b] & BF_LARGE;
-    if (d.p.cell > 0.f) large = large || !(w <= d.p.cell);
+    int lv = 0;
+    if (d.p.cell > 0.f) {
+        if (d.multilevel) {  // the first level whose cap (cell cap x 4^level) holds the box
+            float cap = d.p.cell;
+            while (lv < NLEV - 1 && !(w <= cap)) { cap *= LEV_RATIO; ++lv; }
+            large = large || !(w <= cap);
+        } else {
+            large = large || !(w <= d.p.cell);
+        }
+    }
     if (!large) {
         const float wc = w * 1.01f + 1e-6f;
-        if (wc < 1e30f) atomicMax(&d.ctr[C_CELLBITS], __float_as_int(wc));  // positive floats order as ints
+        // positive floats order as ints
+        if (wc < 1e30f) atomicMax(&d.ctr[lv == 0 ? C_CELLBITS : C_CELLBITS1 + lv - 1], __float_as_int(wc));
     }
     d.cell[b] = make_int4(0, 0, 0, large ? -1 : 0);
+    if (d.blevel) d.blevel[b] = large ? -1 : lv;
     if (large && d.large_ids) d.large_ids[atomicAdd(&d.ctr[C_NLARGE], 1)] = b;
 }
 
@@ -102,15 +118,31 @@ __device__ __forceinline__ int cell_hash(int x, int y, int z, int bits) {
     return (int)(h & ((1u << bits) - 1u));
 }
 
+// Cell size of grid level lv: the widest box of that level or any finer one (times 1.01), so
+// that a box of one level and a box of a coarser level that overlap sit in the same or in
+// adjacent cells of the coarser level.
+__device__ __forceinline__ float level_cell(const Dev& d, int lv) {
+    float cs = __int_as_float(d.ctr[C_CELLBITS]);
+    if (lv >= 1) cs = fmaxf(cs, __int_as_float(d.ctr[C_CELLBITS1]));
+    if (lv >= 2) cs = fmaxf(cs, __int_as_float(d.ctr[C_CELLBITS2]));
+    return cs;
+}
+
+// bucket of cell (x, y, z) of level lv (levels apart: coordinates stay within +-2^20)
+__device__ __forceinline__ int level_hash(int x, int y, int z, int lv, int bits) {
+    return cell_hash(x + (lv << 22), y, z, bits);
+}
+
 __global__ void k_cells(Dev d) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= d.N) return;
     if (d.cell[b].w < 0) return;  // off the grid (k_aabb)
-    const float cs = __int_as_float(d.ctr[C_CELLBITS]);
+    const int lv = d.blevel ? d.blevel[b] : 0;
+    const float cs = level_cell(d, lv);
     float inv = 1.0f / cs;
     float4 a = d.qn[3 * b];
     int x = cell_coord(a.x, inv), y = cell_coord(a.y, inv), z = cell_coord(a.z, inv);
-    int hb = cell_hash(x, y, z, d.table_bits);
+    int hb = level_hash(x, y, z, lv, d.table_bits);
     d.cell[b] = make_int4(x, y, z, hb);
     atomicAdd(&d.bucket_cnt[hb], 1);
 }
@@ -128,7 +160,7 @@ __global__ void k_bucket_fill(Dev d) {
         const float4 lo = d.lo[b], hi = d.hi[b];
         d.brec_lo[pos] = make_float4(lo.x, lo.y, lo.z, __int_as_float(b));
         d.brec_hi[pos] = make_float4(hi.x, hi.y, hi.z, __int_as_float(d.group[b]));
-        d.brec_cell[pos] = make_int4(c.x, c.y, c.z, d.bflags[b]);
+        d.brec_cell[pos] = make_int4(c.x, c.y, c.z, d.bflags[b] | ((d.blevel ? d.blevel[b] : 0) << 8));
     }
 }
 
@@ -171,9 +203,12 @@ __device__ __forceinline__ int lane_partners(const Dev& d, int i, int lane, F&& 
         }
     }
     const int nl = d.large_ids ? d.ctr[C_NLARGE] : 0;
-    for (int k = lane; k < nl; k += 32) {
-        const int j = d.large_ids[k];
-        if (j > i && pair_ok(d, i, j, gi, fi)) { f(j, n); ++n; }
+    if (nl > 0) {
+        const float4 li = d.lo[i], hi_ = d.hi[i];
+        for (int k = lane; k < nl; k += 32) {
+            const int j = d.large_ids[k];
+            if (j > i && pair_ok(d, i, j, gi, fi, li, hi_)) { f(j, n); ++n; }
+        }
     }
     return n;
 }
@@ -201,10 +236,10 @@ __global__ void k_pair_count(Dev d) {
     if (d.p.body_contacts) {
         const int gi = d.group[i], fi = d.bflags[i];
         if (d.cell[i].w < 0) {
-            if (d.offgrid_sep) return;  // counted by k_offgrid_pairs
+            const float4 li = d.lo[i], hi_ = d.hi[i];
             for (int j0 = i + 1; j0 < d.N; j0 += 32) {
                 const int j = j0 + lane;
-                n += (j < d.N && pair_ok(d, i, j, gi, fi)) ? 1 : 0;
+                n += (j < d.N && pair_ok(d, i, j, gi, fi, li, hi_)) ? 1 : 0;
             }
         } else {
             n = lane_partners(d, i, lane, [](int, int) {});
@@ -222,13 +257,12 @@ __global__ void k_pair_write(Dev d) {
     const int cap = d.cap_pairs;
     if (d.p.body_contacts) {
         const int gi = d.group[i], fi = d.bflags[i];
-        if (d.cell[i].w < 0 && d.offgrid_sep) {
-            // written by k_offgrid_pairs
-        } else if (d.cell[i].w < 0) {
+        if (d.cell[i].w < 0) {
             int pos = s;
+            const float4 li = d.lo[i], hi_ = d.hi[i];
             for (int j0 = i + 1; j0 < d.N; j0 += 32) {
                 const int j = j0 + lane;
-                const bool ok = j < d.N && pair_ok(d, i, j, gi, fi);
+                const bool ok = j < d.N && pair_ok(d, i, j, gi, fi, li, hi_);
                 const unsigned bal = __ballot_sync(0xffffffffu, ok);
                 const int at = pos + __popc(bal & ((1u << lane) - 1u));
                 if (ok && at < cap) d.pairs[at] = make_int2(i, j);
@@ -241,8 +275,15 @@ __global__ void k_pair_write(Dev d) {
                 if (base + k < cap) d.pairs[base + k] = make_int2(i, j);
             });
             __syncwarp();
-            if (lane == 0) {
-                const int e = min(d.pair_off[i + 1], cap);
+            const int e = min(d.pair_off[i + 1], cap);
+            if (e - s <= 64) {  // the slice sorted by j in registers
+                const int n = e - s;
+                int v0 = (2 * lane < n) ? d.pairs[s + 2 * lane].y : 0x7fffffff;
+                int v1 = (2 * lane + 1 < n) ? d.pairs[s + 2 * lane + 1].y : 0x7fffffff;
+                warp_sort64(v0, v1, lane);
+                if (2 * lane < n) d.pairs[s + 2 * lane] = make_int2(i, v0);
+                if (2 * lane + 1 < n) d.pairs[s + 2 * lane + 1] = make_int2(i, v1);
+            } else if (lane == 0) {
                 for (int a = s + 1; a < e; ++a) {  // insertion sort of the slice by j
                     int2 v = d.pairs[a];
                     int b = a - 1;
@@ -259,12 +300,108 @@ __global__ void k_pair_write(Dev d) {
     }
 }
 
-// Pairs of the bodies off the grid when a scene has some by design (very wide bodies, or a
-// cell cap below the widest box): body i of the off-grid list against every j > i, one block
-// of OFF_T threads per body.  Warp w takes the w-th of 32 contiguous runs of (i, N), so the
-// warps' hits concatenated in warp order keep the slice sorted by j; the runs' loads are
-// independent, so a body's scan costs about N / OFF_T dependent rounds instead of N / 32.
-// WRITE = false counts (pair_cnt[i], and each warp's count in lane_cnt[32 i + w]); true stores.
+// ---- multilevel grid (Dev::multilevel: scenes with bodies of very different widths) ----
+//
+// A grid body sits at the first level l whose cap, cell cap x 4^l, holds its box (NLEV
+// levels); a wider one, or one flagged large, goes off the grid.  Level l's cell is the widest
+// box of that level or a finer one, so a body meets every overlapping body of its own or a
+// coarser level in the 27 cells around its centre at that level.  Each body therefore scans
+// its own level (keeping partners j > i, as the single-level grid does) and every non-empty
+// coarser level (keeping all partners): a partner j > i joins i's slice, a partner j < i is
+// delivered to j's slice (counted, then placed, with atomics).  The off-grid bodies take all
+// j > i by a block-parallel sweep (k_offgrid_pairs) and the grid bodies test the off-grid
+// list for j > i.  Every slice is then sorted (launch_pair_sort), so the list is again the
+// sorted set of overlapping pairs whatever the order of the atomics.
+
+template <class Own, class Deliver>
+__device__ __forceinline__ int lane_partners_ml(const Dev& d, int i, int lane, Own&& own, Deliver&& deliver) {
+    const int gi = d.group[i], fi = d.bflags[i];
+    const int lvi = d.blevel[i];
+    const float4 li = d.lo[i], hi_ = d.hi[i];
+    const int4 ci = d.cell[i];
+    const float4 pos = d.qn[3 * i];
+    // the levels to scan: its own, then each coarser one that holds any body
+    unsigned lvmask = 1u << lvi;
+    for (int l = lvi + 1; l < NLEV; ++l)
+        if (d.ctr[C_CELLBITS1 + l - 1] != 0) lvmask |= 1u << l;
+    const int nscan = 27 * __popc(lvmask);
+    int n = 0;
+    for (int t = lane; t < nscan; t += 32) {
+        int rank = t / 27, l = 0;
+        for (unsigned m = lvmask;; m &= m - 1) {  // the rank-th set bit
+            if (rank-- == 0) { l = __ffs(m) - 1; break; }
+        }
+        int bx = ci.x, by = ci.y, bz = ci.z;
+        if (l != lvi) {
+            const float inv = 1.0f / level_cell(d, l);
+            bx = cell_coord(pos.x, inv); by = cell_coord(pos.y, inv); bz = cell_coord(pos.z, inv);
+        }
+        const int c = t % 27;
+        const int x = bx + c % 3 - 1, y = by + (c / 3) % 3 - 1, z = bz + c / 9 - 1;
+        const int hb = level_hash(x, y, z, l, d.table_bits);
+        const int s = d.bucket_off[hb], e = d.bucket_off[hb + 1];
+        for (int k = s; k < e; ++k) {
+            const int4 cj = d.brec_cell[k];
+            const float4 lj = d.brec_lo[k], hj = d.brec_hi[k];
+            const int j = __float_as_int(lj.w);
+            if (cj.x != x || cj.y != y || cj.z != z || (cj.w >> 8) != l || j == i) continue;
+            if (l == lvi && j < i) continue;  // same level: found by the smaller id
+            if (__float_as_int(hj.w) != gi || ((fi & BF_PINNED) && (cj.w & BF_PINNED))) continue;
+            if (!overlap(li, hi_, lj, hj)) continue;
+            if (adj_has(d, i, j)) continue;
+            if (j > i) { own(j, n); ++n; }
+            else deliver(j);
+        }
+    }
+    const int nl = d.ctr[C_NLARGE];
+    for (int k = lane; k < nl; k += 32) {
+        const int j = d.large_ids[k];
+        if (j > i && pair_ok(d, i, j, gi, fi, li, hi_)) { own(j, n); ++n; }
+    }
+    return n;
+}
+
+// counts: pair_cnt (zeroed before) gains each body's own partners and the deliveries to it
+__global__ void k_ml_pair_count(Dev d) {
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (i >= d.N || !d.p.body_contacts || d.cell[i].w < 0) return;
+    int n = lane_partners_ml(d, i, lane, [](int, int) {}, [&](int j) { atomicAdd(&d.pair_cnt[j], 1); });
+    d.lane_cnt[32 * i + lane] = n;
+    n = warp_sum(n);
+    if (lane == 0) {
+        d.pair_own[i] = n;
+        atomicAdd(&d.pair_cnt[i], n);
+    }
+}
+
+// partner ids into pair_j: own partners at per-lane offsets, deliveries after the receiver's
+// own ones through its cursor (pair_cur, zeroed before)
+__global__ void k_ml_pair_write(Dev d) {
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (i >= d.N) return;
+    const int cap = d.cap_pairs;
+    if (d.p.body_contacts && d.cell[i].w >= 0) {
+        const int base = d.pair_off[i] + warp_excl(d.lane_cnt[32 * i + lane], lane);
+        lane_partners_ml(d, i, lane,
+            [&](int j, int k) { if (base + k < cap) d.pair_j[base + k] = j; },
+            [&](int j) {
+                const int at = d.pair_off[j] + d.pair_own[j] + atomicAdd(&d.pair_cur[j], 1);
+                if (at < cap) d.pair_j[at] = i;
+            });
+    }
+    if (i == d.N - 1 && lane == 0) {
+        const int tot = d.pair_off[d.N];
+        if (tot > cap) atomicOr(&d.ctr[C_STATUS], ST_CAPACITY);
+        d.ctr[C_NPAIRS] = min(tot, cap);
+    }
+}
+
+// Pairs of the off-grid bodies: body i of the off-grid list against every j > i, one block of
+// OFF_T threads per body.  Warp w takes the w-th of 32 contiguous runs of (i, N), so the warps'
+// hits concatenated in warp order keep the slice sorted by j; the runs' loads are
+// independent, so a body's sweep costs about N / OFF_T dependent rounds instead of N / 32.
+// WRITE = false counts (into pair_cnt[i], and each warp's count in lane_cnt[32 i + w]); true
+// stores the partners into pair_j.
 constexpr int OFF_T = 1024;
 constexpr int OFF_BLOCKS = 152;
 
@@ -278,13 +415,14 @@ __global__ void __launch_bounds__(OFF_T) k_offgrid_pairs(Dev d) {
     for (int h = blockIdx.x; h < nl; h += gridDim.x) {
         const int i = d.large_ids[h];
         const int gi = d.group[i], fi = d.bflags[i];
+        const float4 li = d.lo[i], hi_ = d.hi[i];
         const int len = (((d.N - i - 1) + 31) / 32 + 31) & ~31;  // per warp, a multiple of 32
         const int j_beg = i + 1 + w * len, j_end = min(d.N, j_beg + len);
         if (!WRITE) {
             int n = 0;
             for (int j0 = j_beg; j0 < j_end; j0 += 32) {
                 const int j = j0 + lane;
-                n += (j < j_end && pair_ok(d, i, j, gi, fi)) ? 1 : 0;
+                n += (j < j_end && pair_ok(d, i, j, gi, fi, li, hi_)) ? 1 : 0;
             }
             n = warp_sum(n);
             if (lane == 0) { d.lane_cnt[32 * i + w] = n; s_cnt[w] = n; }
@@ -292,7 +430,7 @@ __global__ void __launch_bounds__(OFF_T) k_offgrid_pairs(Dev d) {
             if (threadIdx.x == 0) {
                 int t = 0;
                 for (int k = 0; k < OFF_T / 32; ++k) t += s_cnt[k];
-                d.pair_cnt[i] = t;
+                atomicAdd(&d.pair_cnt[i], t);
             }
             __syncthreads();
         } else {
@@ -300,10 +438,10 @@ __global__ void __launch_bounds__(OFF_T) k_offgrid_pairs(Dev d) {
             for (int k = 0; k < w; ++k) pos += d.lane_cnt[32 * i + k];
             for (int j0 = j_beg; j0 < j_end; j0 += 32) {
                 const int j = j0 + lane;
-                const bool ok = j < j_end && pair_ok(d, i, j, gi, fi);
+                const bool ok = j < j_end && pair_ok(d, i, j, gi, fi, li, hi_);
                 const unsigned bal = __ballot_sync(0xffffffffu, ok);
                 const int at = pos + __popc(bal & ((1u << lane) - 1u));
-                if (ok && at < cap) d.pairs[at] = make_int2(i, j);
+                if (ok && at < cap) d.pair_j[at] = j;
                 pos += __popc(bal);
             }
         }
@@ -541,6 +679,7 @@ void launch_broadphase(const Dev& d, cudaStream_t st, long long* launches) {
 void launch_collision(const Dev& d, cudaStream_t st, long long* launches) {
     cudaMemsetAsync(d.ctr + C_CELLBITS, 0, sizeof(int), st);
     cudaMemsetAsync(d.ctr + C_NLARGE, 0, sizeof(int), st);
+    cudaMemsetAsync(d.ctr + C_NPHEAVY, 0, sizeof(int) * (C_COUNT - C_NPHEAVY), st);
     k_aabb<<<nblk(d.N), CT, 0, st>>>(d);
     *launches += 1;
     if (d.p.broadphase == 1) {
@@ -553,12 +692,22 @@ void launch_collision(const Dev& d, cudaStream_t st, long long* launches) {
         scan_exclusive(d.bucket_cnt, d.bucket_off, nullptr, T, d.scan_scratch, st, launches);
         k_bucket_fill<<<nblk(d.N), CT, 0, st>>>(d);
         const int wblk = (d.N * 32 + CT - 1) / CT > 0 ? (d.N * 32 + CT - 1) / CT : 1;  // one warp per body
-        k_pair_count<<<wblk, CT, 0, st>>>(d);
-        if (d.offgrid_sep) k_offgrid_pairs<false><<<OFF_BLOCKS, OFF_T, 0, st>>>(d);
-        scan_exclusive(d.pair_cnt, d.pair_off, nullptr, d.N, d.scan_scratch, st, launches);
-        k_pair_write<<<wblk, CT, 0, st>>>(d);
-        if (d.offgrid_sep) k_offgrid_pairs<true><<<OFF_BLOCKS, OFF_T, 0, st>>>(d);
-        *launches += 4 + (d.offgrid_sep ? 2 : 0);
+        if (d.multilevel) {
+            cudaMemsetAsync(d.pair_cnt, 0, sizeof(int) * d.N, st);
+            cudaMemsetAsync(d.pair_cur, 0, sizeof(int) * d.N, st);
+            k_ml_pair_count<<<wblk, CT, 0, st>>>(d);
+            k_offgrid_pairs<false><<<OFF_BLOCKS, OFF_T, 0, st>>>(d);
+            scan_exclusive(d.pair_cnt, d.pair_off, nullptr, d.N, d.scan_scratch, st, launches);
+            k_ml_pair_write<<<wblk, CT, 0, st>>>(d);
+            k_offgrid_pairs<true><<<OFF_BLOCKS, OFF_T, 0, st>>>(d);
+            *launches += 6;
+            launch_pair_sort(d, st, launches);
+        } else {
+            k_pair_count<<<wblk, CT, 0, st>>>(d);
+            scan_exclusive(d.pair_cnt, d.pair_off, nullptr, d.N, d.scan_scratch, st, launches);
+            k_pair_write<<<wblk, CT, 0, st>>>(d);
+            *launches += 4;
+        }
     }
     const int nt = d.cap_pairs > d.N ? d.cap_pairs : d.N;
     k_narrow_count<<<nblk(nt), CT, 0, st>>>(d);

@@ -242,8 +242,9 @@ __global__ void k_bvh_pair_write(Dev d) {
     }
 }
 
-// each body's partners ascending (a warp each; longer than 64: the block sort below)
-__global__ void k_bvh_pair_sort(Dev d) {
+// each body's partners ascending (a warp each; longer than 64: the block sort below); shared
+// by the LBVH and the multilevel grid
+__global__ void k_pair_sort(Dev d) {
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (i >= d.N) return;
     const int cap = d.cap_pairs;
@@ -257,7 +258,7 @@ __global__ void k_bvh_pair_sort(Dev d) {
     for (int p = s + lane; p < e; p += 32) d.pairs[p] = make_int2(i, d.pair_j[p]);
 }
 
-__global__ void __launch_bounds__(LONG_T) k_bvh_pair_sort_long(Dev d) {
+__global__ void __launch_bounds__(LONG_T) k_pair_sort_long(Dev d) {
     extern __shared__ int key[];
     const int nh = d.ctr[C_NPHEAVY], cap = d.cap_pairs;
     for (int h = blockIdx.x; h < nh; h += gridDim.x) {
@@ -269,9 +270,15 @@ __global__ void __launch_bounds__(LONG_T) k_bvh_pair_sort_long(Dev d) {
     }
 }
 
-cudaError_t setup_lbvh_kernels() {
-    return cudaFuncSetAttribute(k_bvh_pair_sort_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
+cudaError_t setup_pair_sort() {
+    return cudaFuncSetAttribute(k_pair_sort_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 LONG_SMEM * (int)sizeof(int));
+}
+
+void launch_pair_sort(const Dev& d, cudaStream_t st, long long* launches) {
+    k_pair_sort<<<bblk((long long)d.N * 32), BT, 0, st>>>(d);
+    k_pair_sort_long<<<152, LONG_T, LONG_SMEM * sizeof(int), st>>>(d);
+    *launches += 2;
 }
 
 void launch_lbvh_pairs(const Dev& d, cudaStream_t st, long long* launches) {
@@ -300,9 +307,8 @@ void launch_lbvh_pairs(const Dev& d, cudaStream_t st, long long* launches) {
     k_bvh_pair_count<<<bblk(n), BT, 0, st>>>(d);
     scan_exclusive(d.pair_cnt, d.pair_off, nullptr, n, d.scan_scratch, st, launches);
     k_bvh_pair_write<<<bblk(n), BT, 0, st>>>(d);
-    k_bvh_pair_sort<<<bblk((long long)n * 32), BT, 0, st>>>(d);
-    k_bvh_pair_sort_long<<<152, LONG_T, LONG_SMEM * sizeof(int), st>>>(d);
-    *launches += 6;
+    *launches += 4;
+    launch_pair_sort(d, st, launches);
 }
 
 }  // namespace pabd

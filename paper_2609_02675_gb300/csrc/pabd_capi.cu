@@ -428,8 +428,9 @@ pabd_status finalize_scene(pabd_scene* s) {
     d.Nlarge = (int)large.size();
     bool cap_below_widest = false;
     p.cell = (float)grid_cell_cap(s->bodies, flags, ds, &cap_below_widest);
-    // scenes with off-grid bodies by design take their pairs from a block-parallel kernel
-    d.offgrid_sep = ds.body_contacts && (d.Nlarge > 0 || cap_below_widest);
+    // scenes with bodies of very different widths (some flagged large, or a cell cap below the
+    // widest box) use the multilevel grid (k_collision.cu)
+    d.multilevel = ds.body_contacts && ds.broadphase == 0 && (d.Nlarge > 0 || cap_below_widest);
     // Expansion point of each body's system (sys_init): x_s = sum w x / (m + sum w) over the
     // ends of its static bonds (w = h^2 kappa; a drive's moving anchor at its rest angle).
     // Static extended-precision flag (reading R18): the FP64 Cholesky of the diagonally scaled
@@ -591,8 +592,13 @@ pabd_status finalize_scene(pabd_scene* s) {
               alloc_arr(s, d.bvh_id2, N) && alloc_arr(s, d.rx_cnt, 256 * ntile) && alloc_arr(s, d.rx_off, 256 * ntile + 1);
         ok &= alloc_arr(s, d.bvh_kids, N) && alloc_arr(s, d.bvh_parent, 2 * (size_t)N) && alloc_arr(s, d.bvh_lo, N) &&
               alloc_arr(s, d.bvh_hi, N) && alloc_arr(s, d.bvh_visit, N) && alloc_arr(s, d.bvh_bounds, 6);
+    }
+    if (p.broadphase == 1 || d.multilevel) {
         ok &= alloc_arr(s, d.pair_j, d.cap_pairs) && alloc_arr(s, d.pair_tmp, d.cap_pairs) &&
               alloc_arr(s, d.pair_heavy, N);
+    }
+    if (d.multilevel) {
+        ok &= alloc_arr(s, d.blevel, N) && alloc_arr(s, d.pair_own, N) && alloc_arr(s, d.pair_cur, N);
     }
     if (!ok) return PABD_ERR_OOM;
 
@@ -633,7 +639,7 @@ pabd_status finalize_scene(pabd_scene* s) {
 
     // lanes per body from the descriptor; fused sweep block / grid from a timing sweep
     CK(setup_csr_kernels());
-    if (p.broadphase == 1) CK(setup_lbvh_kernels());
+    if (p.broadphase == 1 || d.multilevel) CK(setup_pair_sort());
 
     // lanes per body: given, or from the body count -- the largest of 16, 8, 4, 2, 1 lanes
     // with lanes * N <= 2^17 (the measured optimum on piles of 4 k to 1 M bodies and on the
@@ -1174,6 +1180,7 @@ pabd_status pabd_get_info(pabd_scene* s, pabd_info* info) {
     info->coop_fallbacks = s->coop_fallbacks;
     info->heavy_bodies = c[C_NHEAVY];
     info->fp64_dynamic = c[C_FP64DYN];
+    info->offgrid_bodies = c[C_NLARGE];
     info->last_sweeps = s->d.p.n_iter;
     if (s->d.sweep_ctl) {
         int ctl[4] = {0, 0, 0, 0};

@@ -33,7 +33,9 @@ enum Counter {
     C_FP64DYN,         // bodies that switched to FP64 by the pivot test (last sweep)
     C_NHEAVY,          // bodies with more than HEAVY_ENDS bond ends this step (list in Dev::heavy)
     C_NLARGE,          // bodies off the grid this step (list in Dev::large_ids)
-    C_NPHEAVY,         // bodies with more than 64 LBVH partners this step (list in Dev::pair_heavy)
+    C_NPHEAVY,         // bodies with more than 64 partners this step (list in Dev::pair_heavy)
+    C_CELLBITS1,       // float bits of the widest box of grid level 1 (multilevel grid)
+    C_CELLBITS2,       // ... of grid level 2
     C_COUNT
 };
 
@@ -65,7 +67,7 @@ struct Dev {
     int N, Nc, Ndrive, G, Nlarge;
     int cap_pairs, cap_contacts, cap_bonds, cap_ends;
     int table_bits;             // grid hash table has 1 << table_bits buckets
-    int offgrid_sep;            // pairs of off-grid bodies from their own kernel (k_offgrid_pairs)
+    int multilevel;             // grid of NLEV levels (k_collision.cu); off-grid pairs by k_offgrid_pairs
     // bodies
     float4 *qn, *qa, *qb, *sq;  // 3 float4 per body each
     float4 *vel, *omg, *quat, *qstar;
@@ -116,6 +118,9 @@ struct Dev {
     int *bvh_bounds;                // box of the centres (order-preserving int bits: min xyz, max xyz)
     int *pair_j, *pair_tmp;         // partner slices while they are sorted
     int *pair_heavy;                // bodies with more than 64 partners
+    // multilevel grid (Dev::multilevel)
+    int *blevel;                    // grid level of each body this step (-1: off the grid)
+    int *pair_own, *pair_cur;       // partners a body finds itself; cursor of those delivered to it
     // misc
     int *ctr;                   // Counter array
     // sweeps under a residual threshold: (sweeps done, scenes still active, loop on, -) and
@@ -136,7 +141,9 @@ int scan_scratch_ints(int n_cap);
 void launch_collision(const Dev& d, cudaStream_t st, long long* launches);
 // LBVH pairs from this step's boxes (after k_aabb): the same output as the grid's pair stage
 void launch_lbvh_pairs(const Dev& d, cudaStream_t st, long long* launches);
-cudaError_t setup_lbvh_kernels();
+cudaError_t setup_pair_sort();
+// each body's partner slice of Dev::pair_j sorted ascending into Dev::pairs
+void launch_pair_sort(const Dev& d, cudaStream_t st, long long* launches);
 void launch_broadphase(const Dev& d, cudaStream_t st, long long* launches);
 void launch_csr(const Dev& d, cudaStream_t st, long long* launches);
 // opt the CSR block sort into its 128 KB of dynamic shared memory (once per process and device)

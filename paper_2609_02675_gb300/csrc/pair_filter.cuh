@@ -24,13 +24,20 @@ __device__ __forceinline__ bool adj_has(const Dev& d, int a, int b) {
     return false;
 }
 
-__device__ __forceinline__ bool pair_ok(const Dev& d, int i, int j, int gi, int fi) {
-    if (d.group[j] != gi) return false;
-    int fj = d.bflags[j];
+// (j's group, flags and box are loaded together, one round trip rather than three)
+__device__ __forceinline__ bool pair_ok(const Dev& d, int i, int j, int gi, int fi, const float4& li,
+                                        const float4& hi) {
+    const int gj = d.group[j], fj = d.bflags[j];
+    const float4 lj = d.lo[j], hj = d.hi[j];
+    if (gj != gi) return false;
     if ((fi & BF_PINNED) && (fj & BF_PINNED)) return false;
-    if (!overlap(d.lo[i], d.hi[i], d.lo[j], d.hi[j])) return false;
+    if (!overlap(li, hi, lj, hj)) return false;
     if (adj_has(d, i, j)) return false;
     return true;
+}
+
+__device__ __forceinline__ bool pair_ok(const Dev& d, int i, int j, int gi, int fi) {
+    return pair_ok(d, i, j, gi, fi, d.lo[i], d.hi[i]);
 }
 
 }  // namespace pabd

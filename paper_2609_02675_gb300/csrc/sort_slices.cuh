@@ -1,7 +1,8 @@
 // Sorting of short integer slices in place (ascending, keys unique within a slice): a warp's
 // bitonic network in registers for up to 64 keys, and a block's for longer slices -- runs of up
 // to LONG_SMEM keys in shared memory, then merge passes through a scratch slice.  Used for
-// the CSR of bond ends (k_step.cu) and for the LBVH pair lists (k_collision.cu).
+// the CSR of bond ends (k_step.cu) and for the pair lists of both broad phases (k_collision.cu,
+// k_lbvh.cu).
 #pragma once
 #include "pabd_internal.h"
 
@@ -10,11 +11,9 @@ namespace pabd {
 constexpr int LONG_T = 1024;
 constexpr int LONG_SMEM = 32768;  // ints of dynamic shared memory (128 KB)
 
-// slice v[0..n), n <= 64, by the 32 lanes of a warp (element k in lane k / 2, slot k % 2;
-// padding INT_MAX)
-__device__ __forceinline__ void warp_sort_slice64(int* v, int n, int lane) {
-    int v0 = (2 * lane < n) ? v[2 * lane] : 0x7fffffff;
-    int v1 = (2 * lane + 1 < n) ? v[2 * lane + 1] : 0x7fffffff;
+// 64 keys held two per lane (key k in lane k / 2, slot k % 2) sorted ascending by the 32
+// lanes of a warp: a bitonic network of shuffles
+__device__ __forceinline__ void warp_sort64(int& v0, int& v1, int lane) {
     for (int size = 2; size <= 64; size <<= 1) {
         const bool up = ((2 * lane) & size) == 0;       // ascending block (same for both slots)
         for (int stride = size >> 1; stride > 1; stride >>= 1) {
@@ -28,6 +27,13 @@ __device__ __forceinline__ void warp_sort_slice64(int* v, int n, int lane) {
         v0 = up ? mn : mx;
         v1 = up ? mx : mn;
     }
+}
+
+// slice v[0..n), n <= 64, by the 32 lanes of a warp (padding INT_MAX)
+__device__ __forceinline__ void warp_sort_slice64(int* v, int n, int lane) {
+    int v0 = (2 * lane < n) ? v[2 * lane] : 0x7fffffff;
+    int v1 = (2 * lane + 1 < n) ? v[2 * lane + 1] : 0x7fffffff;
+    warp_sort64(v0, v1, lane);
     if (2 * lane < n) v[2 * lane] = v0;
     if (2 * lane + 1 < n) v[2 * lane + 1] = v1;
 }
