@@ -63,6 +63,7 @@ __device__ __forceinline__ float body_infl(const Dev& d, int b) {
 }
 
 __global__ void k_aabb(Dev d) {
+    pdl_enter();
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= d.N) return;
     float c[3], A[9];
@@ -134,6 +135,7 @@ __device__ __forceinline__ int level_hash(int x, int y, int z, int lv, int bits)
 }
 
 __global__ void k_cells(Dev d) {
+    pdl_enter();
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= d.N) return;
     if (d.cell[b].w < 0) return;  // off the grid (k_aabb)
@@ -150,6 +152,7 @@ __global__ void k_cells(Dev d) {
 // Bodies into their buckets, with a compact copy of what the pair test reads (box, id, group,
 // flags, cell) so that a candidate costs one contiguous record read.
 __global__ void k_bucket_fill(Dev d) {
+    pdl_enter();
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= d.N) return;
     const int4 c = d.cell[b];
@@ -230,6 +233,7 @@ __device__ __forceinline__ int warp_excl(int v, int lane) {
 }
 
 __global__ void k_pair_count(Dev d) {
+    pdl_enter();
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (i >= d.N) return;
     int n = 0;
@@ -251,6 +255,7 @@ __global__ void k_pair_count(Dev d) {
 }
 
 __global__ void k_pair_write(Dev d) {
+    pdl_enter();
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (i >= d.N) return;
     const int s = d.pair_off[i];
@@ -363,6 +368,7 @@ __device__ __forceinline__ int lane_partners_ml(const Dev& d, int i, int lane, O
 
 // counts: pair_cnt (zeroed before) gains each body's own partners and the deliveries to it
 __global__ void k_ml_pair_count(Dev d) {
+    pdl_enter();
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (i >= d.N || !d.p.body_contacts || d.cell[i].w < 0) return;
     int n = lane_partners_ml(d, i, lane, [](int, int) {}, [&](int j) { atomicAdd(&d.pair_cnt[j], 1); });
@@ -377,6 +383,7 @@ __global__ void k_ml_pair_count(Dev d) {
 // partner ids into pair_j: own partners at per-lane offsets, deliveries after the receiver's
 // own ones through its cursor (pair_cur, zeroed before)
 __global__ void k_ml_pair_write(Dev d) {
+    pdl_enter();
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (i >= d.N) return;
     const int cap = d.cap_pairs;
@@ -407,6 +414,7 @@ constexpr int OFF_BLOCKS = 152;
 
 template <bool WRITE>
 __global__ void __launch_bounds__(OFF_T) k_offgrid_pairs(Dev d) {
+    pdl_enter();
     __shared__ int s_cnt[OFF_T / 32];
     if (!d.p.body_contacts) return;
     const int nl = d.ctr[C_NLARGE];
@@ -582,6 +590,7 @@ __device__ int ground_corners(const Dev& d, const FBox& fa, int a, Emit&& emit) 
 }
 
 __global__ void k_narrow_count(Dev d) {
+    pdl_enter();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int np = d.ctr[C_NPAIRS];
     if (t < np) {
@@ -626,6 +635,7 @@ __device__ __forceinline__ void write_contact(const Dev& d, int slot, int type, 
 }
 
 __global__ void k_narrow_write(Dev d) {
+    pdl_enter();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int np = d.ctr[C_NPAIRS];
     const int npc = d.npc_off[np];
@@ -665,55 +675,49 @@ void launch_broadphase(const Dev& d, cudaStream_t st, long long* launches) {
     cudaMemsetAsync(d.bucket_cnt, 0, sizeof(int) * T, st);
     cudaMemsetAsync(d.bucket_cur, 0, sizeof(int) * T, st);
     cudaMemsetAsync(d.ctr, 0, sizeof(int) * C_COUNT, st);
-    k_aabb<<<nblk(d.N), CT, 0, st>>>(d);
-    k_cells<<<nblk(d.N), CT, 0, st>>>(d);
+    launch_pdl(k_aabb, dim3(nblk(d.N)), dim3(CT), 0, st, d);
+    launch_pdl(k_cells, dim3(nblk(d.N)), dim3(CT), 0, st, d);
     scan_exclusive(d.bucket_cnt, d.bucket_off, nullptr, T, d.scan_scratch, st, launches);
-    k_bucket_fill<<<nblk(d.N), CT, 0, st>>>(d);
+    launch_pdl(k_bucket_fill, dim3(nblk(d.N)), dim3(CT), 0, st, d);
     const int wblk = (d.N * 32 + CT - 1) / CT > 0 ? (d.N * 32 + CT - 1) / CT : 1;
-    k_pair_count<<<wblk, CT, 0, st>>>(d);
+    launch_pdl(k_pair_count, dim3(wblk), dim3(CT), 0, st, d);
     scan_exclusive(d.pair_cnt, d.pair_off, nullptr, d.N, d.scan_scratch, st, launches);
-    k_pair_write<<<wblk, CT, 0, st>>>(d);
+    launch_pdl(k_pair_write, dim3(wblk), dim3(CT), 0, st, d);
     *launches += 5;
 }
 
+// (the counters and buckets it accumulates into are zeroed by launch_step_reset)
 void launch_collision(const Dev& d, cudaStream_t st, long long* launches) {
-    cudaMemsetAsync(d.ctr + C_CELLBITS, 0, sizeof(int), st);
-    cudaMemsetAsync(d.ctr + C_NLARGE, 0, sizeof(int), st);
-    cudaMemsetAsync(d.ctr + C_NPHEAVY, 0, sizeof(int) * (C_COUNT - C_NPHEAVY), st);
-    k_aabb<<<nblk(d.N), CT, 0, st>>>(d);
+    launch_pdl(k_aabb, dim3(nblk(d.N)), dim3(CT), 0, st, d);
     *launches += 1;
     if (d.p.broadphase == 1) {
         launch_lbvh_pairs(d, st, launches);
     } else {
         const int T = 1 << d.table_bits;
-        cudaMemsetAsync(d.bucket_cnt, 0, sizeof(int) * T, st);
-        cudaMemsetAsync(d.bucket_cur, 0, sizeof(int) * T, st);
-        k_cells<<<nblk(d.N), CT, 0, st>>>(d);
+        launch_pdl(k_cells, dim3(nblk(d.N)), dim3(CT), 0, st, d);
         scan_exclusive(d.bucket_cnt, d.bucket_off, nullptr, T, d.scan_scratch, st, launches);
-        k_bucket_fill<<<nblk(d.N), CT, 0, st>>>(d);
+        launch_pdl(k_bucket_fill, dim3(nblk(d.N)), dim3(CT), 0, st, d);
         const int wblk = (d.N * 32 + CT - 1) / CT > 0 ? (d.N * 32 + CT - 1) / CT : 1;  // one warp per body
         if (d.multilevel) {
-            cudaMemsetAsync(d.pair_cnt, 0, sizeof(int) * d.N, st);
-            cudaMemsetAsync(d.pair_cur, 0, sizeof(int) * d.N, st);
-            k_ml_pair_count<<<wblk, CT, 0, st>>>(d);
-            k_offgrid_pairs<false><<<OFF_BLOCKS, OFF_T, 0, st>>>(d);
+            launch_pdl(k_ml_pair_count, dim3(wblk), dim3(CT), 0, st, d);
+            launch_pdl(k_offgrid_pairs<false>, dim3(OFF_BLOCKS), dim3(OFF_T), 0, st, d);
             scan_exclusive(d.pair_cnt, d.pair_off, nullptr, d.N, d.scan_scratch, st, launches);
-            k_ml_pair_write<<<wblk, CT, 0, st>>>(d);
-            k_offgrid_pairs<true><<<OFF_BLOCKS, OFF_T, 0, st>>>(d);
+            launch_pdl(k_ml_pair_write, dim3(wblk), dim3(CT), 0, st, d);
+            launch_pdl(k_offgrid_pairs<true>, dim3(OFF_BLOCKS), dim3(OFF_T), 0, st, d);
             *launches += 6;
             launch_pair_sort(d, st, launches);
         } else {
-            k_pair_count<<<wblk, CT, 0, st>>>(d);
+            launch_pdl(k_pair_count, dim3(wblk), dim3(CT), 0, st, d);
             scan_exclusive(d.pair_cnt, d.pair_off, nullptr, d.N, d.scan_scratch, st, launches);
-            k_pair_write<<<wblk, CT, 0, st>>>(d);
+            launch_pdl(k_pair_write, dim3(wblk), dim3(CT), 0, st, d);
             *launches += 4;
         }
     }
     const int nt = d.cap_pairs > d.N ? d.cap_pairs : d.N;
-    k_narrow_count<<<nblk(nt), CT, 0, st>>>(d);
+    launch_pdl(k_narrow_count, dim3(nblk(nt)), dim3(CT), 0, st, d);
     scan_exclusive(d.npc, d.npc_off, d.ctr + C_NPAIRS, d.cap_pairs, d.scan_scratch, st, launches);
     scan_exclusive(d.gnd_cnt, d.gnd_off, nullptr, d.N, d.scan_scratch, st, launches);
-    k_narrow_write<<<nblk(nt), CT, 0, st>>>(d);
+    launch_pdl(k_narrow_write, dim3(nblk(nt)), dim3(CT), 0, st, d);
     *launches += 2;
 }
 

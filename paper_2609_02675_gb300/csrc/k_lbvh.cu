@@ -245,6 +245,7 @@ __global__ void k_bvh_pair_write(Dev d) {
 // each body's partners ascending (a warp each; longer than 64: the block sort below); shared
 // by the LBVH and the multilevel grid
 __global__ void k_pair_sort(Dev d) {
+    pdl_enter();
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (i >= d.N) return;
     const int cap = d.cap_pairs;
@@ -259,6 +260,7 @@ __global__ void k_pair_sort(Dev d) {
 }
 
 __global__ void __launch_bounds__(LONG_T) k_pair_sort_long(Dev d) {
+    pdl_enter();
     extern __shared__ int key[];
     const int nh = d.ctr[C_NPHEAVY], cap = d.cap_pairs;
     for (int h = blockIdx.x; h < nh; h += gridDim.x) {
@@ -276,8 +278,8 @@ cudaError_t setup_pair_sort() {
 }
 
 void launch_pair_sort(const Dev& d, cudaStream_t st, long long* launches) {
-    k_pair_sort<<<bblk((long long)d.N * 32), BT, 0, st>>>(d);
-    k_pair_sort_long<<<152, LONG_T, LONG_SMEM * sizeof(int), st>>>(d);
+    launch_pdl(k_pair_sort, dim3(bblk((long long)d.N * 32)), dim3(BT), 0, st, d);
+    launch_pdl(k_pair_sort_long, dim3(152), dim3(LONG_T), LONG_SMEM * sizeof(int), st, d);
     *launches += 2;
 }
 

@@ -165,6 +165,7 @@ void launch_sweep_one(const Dev& d, const float4* qi, float4* qo, int it, int L,
 
 // copy of every bond end's record into CSR order (once per step, after the CSR sort)
 __global__ void k_end_records(Dev d) {
+    pdl_enter();
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= d.end_off[d.N]) return;
     const int bond = d.end_id[p] >> 1;
@@ -205,7 +206,7 @@ int fused_max_blocks(int L, int block, bool fp64) {
 
 void launch_end_records(const Dev& d, cudaStream_t st, long long* launches) {
     const int nrec = d.cap_ends > 0 ? d.cap_ends : 1;
-    k_end_records<<<(nrec + 255) / 256, 256, 0, st>>>(d);
+    launch_pdl(k_end_records, dim3((nrec + 255) / 256), dim3(256), 0, st, d);
     *launches += 1;
 }
 

@@ -41,6 +41,7 @@ __device__ __forceinline__ int block_incl_scan(int v, int* smem, int* total) {
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_chunks(const int* __restrict__ in, int* __restrict__ out,
                                                               const int* n_dev, int n_cap, int* block_sums,
                                                               int single) {
+    pdl_enter();
     __shared__ int smem[32];
     const int n = n_dev ? min(*n_dev, n_cap) : n_cap;
     const int base = blockIdx.x * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
@@ -67,6 +68,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_chunks(const int* __restr
 
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_totals(int* block_sums, int nb, int* out, const int* n_dev,
                                                               int n_cap) {
+    pdl_enter();
     __shared__ int smem[32];
     const int n = n_dev ? min(*n_dev, n_cap) : n_cap;
     const int base = threadIdx.x * SCAN_ITEMS;
@@ -90,6 +92,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_totals(int* block_sums, i
 
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_add(int* out, const int* n_dev, int n_cap,
                                                            const int* block_sums) {
+    pdl_enter();
     const int n = n_dev ? min(*n_dev, n_cap) : n_cap;
     if (blockIdx.x == 0) return;
     const int add = block_sums[blockIdx.x];
@@ -105,6 +108,7 @@ constexpr int SCAN_LOOP_MAX = 16 * SCAN_CHUNK;
 
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_loop(const int* __restrict__ in, int* __restrict__ out,
                                                             const int* n_dev, int n_cap) {
+    pdl_enter();
     __shared__ int smem[32];
     const int n = n_dev ? min(*n_dev, n_cap) : n_cap;
     int carry = 0;
@@ -137,19 +141,19 @@ void scan_exclusive(const int* in, int* out, const int* n_dev, int n_cap, int* s
                     long long* launches) {
     const int nb = n_cap > 0 ? (n_cap + SCAN_CHUNK - 1) / SCAN_CHUNK : 1;
     if (nb == 1) {
-        k_scan_chunks<<<1, SCAN_THREADS, 0, st>>>(in, out, n_dev, n_cap, scratch, 1);
+        launch_pdl(k_scan_chunks, dim3(1), dim3(SCAN_THREADS), 0, st, in, out, n_dev, n_cap, scratch, 1);
         *launches += 1;
         return;
     }
     if (n_cap <= SCAN_LOOP_MAX) {
-        k_scan_loop<<<1, SCAN_THREADS, 0, st>>>(in, out, n_dev, n_cap);
+        launch_pdl(k_scan_loop, dim3(1), dim3(SCAN_THREADS), 0, st, in, out, n_dev, n_cap);
         *launches += 1;
         return;
     }
     // the level-2 scan handles up to SCAN_CHUNK block totals (n_cap <= 16.7 M)
-    k_scan_chunks<<<nb, SCAN_THREADS, 0, st>>>(in, out, n_dev, n_cap, scratch, 0);
-    k_scan_totals<<<1, SCAN_THREADS, 0, st>>>(scratch, nb, out, n_dev, n_cap);
-    k_scan_add<<<nb, SCAN_THREADS, 0, st>>>(out, n_dev, n_cap, scratch);
+    launch_pdl(k_scan_chunks, dim3(nb), dim3(SCAN_THREADS), 0, st, in, out, n_dev, n_cap, scratch, 0);
+    launch_pdl(k_scan_totals, dim3(1), dim3(SCAN_THREADS), 0, st, scratch, nb, out, n_dev, n_cap);
+    launch_pdl(k_scan_add, dim3(nb), dim3(SCAN_THREADS), 0, st, out, n_dev, n_cap, scratch);
     *launches += 3;
 }
 

@@ -24,6 +24,7 @@ __device__ __forceinline__ void store_q(float4* q, int b, const float* c, const 
 // Predictor (Alg. 1): v* = v + h g; c* = c + h v*; Q* = normalise(Q + h/2 [w, 0] Q);
 // A* = R(Q*); s = q^0 = (c*, A*).  Pinned bodies keep q^n.
 __global__ void k_predict(Dev d) {
+    pdl_enter();
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= d.N) return;
     if (d.bflags[b] & BF_PINNED) {
@@ -76,6 +77,7 @@ __device__ __forceinline__ float4 mat_to_quat(const float* R) {
 // Velocity recovery (Alg. 1, Sec. 4.4): v = (c^{n+1} - c^n)/h;
 // [w]x = skew part of (A^{n+1} - A^n)(A^n)^T / h; Q^{n+1} = quat(A^{n+1}), sign-continuous.
 __global__ void k_finalize(Dev d, const float4* __restrict__ qf, int dyn) {
+    pdl_enter();
     // under a residual threshold the last iterate sits in the buffer of the sweep count's parity
     if (dyn) qf = (d.sweep_ctl[0] & 1) ? d.qb : d.qa;
     int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -117,6 +119,7 @@ __global__ void k_finalize(Dev d, const float4* __restrict__ qf, int dyn) {
 // Drive anchors at t = (step + 1) h: x_i = x_i0 + arm (cos th r + sin th (u x r)),
 // th = amp sin(2 pi t / period + phase).
 __global__ void k_drive_update(Dev d) {
+    pdl_enter();
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= d.Ndrive) return;
     const double t = (double)(*d.step_index + 1) * d.p.h_d;
@@ -138,6 +141,7 @@ __device__ __forceinline__ bool end_live(const Dev& d, int body) {
 }
 
 __global__ void k_csr_count(Dev d) {
+    pdl_enter();
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= d.ctr[C_NBONDS]) return;
     int4 m = d.bmeta[b];
@@ -146,6 +150,7 @@ __global__ void k_csr_count(Dev d) {
 }
 
 __global__ void k_csr_fill(Dev d) {
+    pdl_enter();
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= d.ctr[C_NBONDS]) return;
     int4 m = d.bmeta[b];
@@ -161,6 +166,7 @@ __global__ void k_csr_fill(Dev d) {
 // body goes on the heavy list, whose slices k_csr_sort_long sorts.  Either way the slice ends
 // up in ascending end id.
 __global__ void k_csr_sort(Dev d) {
+    pdl_enter();
     const int body = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (body >= d.N) return;
     const int s = d.end_off[body], e = d.end_off[body + 1], n = e - s;
@@ -182,6 +188,7 @@ __global__ void k_csr_sort(Dev d) {
 // The heavy bodies' slices, one block per body (block_sort_slice), the end-record buffer
 // (unused at this stage) as scratch.
 __global__ void __launch_bounds__(LONG_T) k_csr_sort_long(Dev d) {
+    pdl_enter();
     extern __shared__ int key[];
     const int nheavy = d.ctr[C_NHEAVY];
     for (int h = blockIdx.x; h < nheavy; h += gridDim.x) {
@@ -209,6 +216,7 @@ cudaError_t setup_csr_kernels() {
 // order by thread 0 (deterministic)
 constexpr int RES_T = 128;
 __global__ void __launch_bounds__(RES_T) k_group_resid(Dev d) {
+    pdl_enter();
     __shared__ double part[RES_T / 32];
     const int g = blockIdx.x;
     if (g >= d.G) return;
@@ -227,31 +235,61 @@ __global__ void __launch_bounds__(RES_T) k_group_resid(Dev d) {
 }
 
 void launch_predict(const Dev& d, cudaStream_t st, long long* launches) {
-    k_predict<<<nblk(d.N), ST_T, 0, st>>>(d);
+    launch_pdl(k_predict, dim3(nblk(d.N)), dim3(ST_T), 0, st, d);
     *launches += 1;
 }
 
 void launch_drive_update(const Dev& d, cudaStream_t st, long long* launches) {
     if (d.Ndrive == 0) return;
-    k_drive_update<<<nblk(d.Ndrive), ST_T, 0, st>>>(d);
+    launch_pdl(k_drive_update, dim3(nblk(d.Ndrive)), dim3(ST_T), 0, st, d);
+    *launches += 1;
+}
+
+// The per-step counters and scratch that the collision and CSR stages accumulate into, zeroed
+// by one kernel at the head of the step: no memset nodes between the step's kernels, so each
+// of them may launch while its predecessor runs.
+__global__ void k_step_reset(Dev d) {
+    pdl_enter();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0) {
+        d.ctr[C_CELLBITS] = 0;
+        d.ctr[C_NLARGE] = 0;
+        d.ctr[C_NHEAVY] = 0;
+        d.ctr[C_FP64DYN] = 0;
+        for (int k = C_NPHEAVY; k < C_COUNT; ++k) d.ctr[k] = 0;
+    }
+    if (d.p.broadphase == 0 && t < (1 << d.table_bits)) {
+        d.bucket_cnt[t] = 0;
+        d.bucket_cur[t] = 0;
+    }
+    if (t < d.N) {
+        d.end_cnt[t] = 0;
+        d.end_cur[t] = 0;
+        if (d.multilevel) {
+            d.pair_cnt[t] = 0;
+            d.pair_cur[t] = 0;
+        }
+    }
+}
+
+void launch_step_reset(const Dev& d, cudaStream_t st, long long* launches) {
+    const long long n = std::max<long long>(1ll << d.table_bits, d.N);
+    launch_pdl(k_step_reset, dim3((unsigned)((n + ST_T - 1) / ST_T)), dim3(ST_T), 0, st, d);
     *launches += 1;
 }
 
 void launch_csr(const Dev& d, cudaStream_t st, long long* launches) {
-    cudaMemsetAsync(d.ctr + C_NHEAVY, 0, sizeof(int), st);
-    cudaMemsetAsync(d.end_cnt, 0, sizeof(int) * d.N, st);
-    cudaMemsetAsync(d.end_cur, 0, sizeof(int) * d.N, st);
-    k_csr_count<<<nblk(d.cap_bonds), ST_T, 0, st>>>(d);
+    launch_pdl(k_csr_count, dim3(nblk(d.cap_bonds)), dim3(ST_T), 0, st, d);
     scan_exclusive(d.end_cnt, d.end_off, nullptr, d.N, d.scan_scratch, st, launches);
-    k_csr_fill<<<nblk(d.cap_bonds), ST_T, 0, st>>>(d);
-    k_csr_sort<<<nblk(d.N * 32), ST_T, 0, st>>>(d);
-    k_csr_sort_long<<<152, LONG_T, LONG_SMEM * sizeof(int), st>>>(d);
+    launch_pdl(k_csr_fill, dim3(nblk(d.cap_bonds)), dim3(ST_T), 0, st, d);
+    launch_pdl(k_csr_sort, dim3(nblk(d.N * 32)), dim3(ST_T), 0, st, d);
+    launch_pdl(k_csr_sort_long, dim3(152), dim3(LONG_T), LONG_SMEM * sizeof(int), st, d);
     *launches += 4;
 }
 
 void launch_finalize(const Dev& d, const float4* q_fin, cudaStream_t st, long long* launches) {
-    k_finalize<<<nblk(d.N), ST_T, 0, st>>>(d, q_fin, 0);
-    k_group_resid<<<d.G > 0 ? d.G : 1, RES_T, 0, st>>>(d);
+    launch_pdl(k_finalize, dim3(nblk(d.N)), dim3(ST_T), 0, st, d, q_fin, 0);
+    launch_pdl(k_group_resid, dim3(d.G > 0 ? d.G : 1), dim3(RES_T), 0, st, d);
     *launches += 2;
 }
 
@@ -322,7 +360,7 @@ void launch_sweep_check(const Dev& d, unsigned long long handle, cudaStream_t st
 }
 
 void launch_finalize_dynamic(const Dev& d, cudaStream_t st, long long* launches) {
-    k_finalize<<<nblk(d.N), ST_T, 0, st>>>(d, nullptr, 1);
+    launch_pdl(k_finalize, dim3(nblk(d.N)), dim3(ST_T), 0, st, d, nullptr, 1);
     *launches += 1;
 }
 

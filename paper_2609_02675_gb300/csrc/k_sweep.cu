@@ -106,6 +106,7 @@ namespace pabd {
 // previous step ended with (parity n_iter): kappa <- max(gamma kappa, kappa_start),
 // lambda <- alpha gamma lambda, into the parity-0 buffer read by the first sweep
 __global__ void k_al_warm(Dev d) {
+    pdl_enter();
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= d.Nc || d.bmeta[b].z != K_AL) return;
     const float2 kl = (d.p.n_iter & 1) ? d.al_st1[b] : d.al_st0[b];
@@ -143,7 +144,7 @@ __global__ void k_al_final(Dev d, const float4* __restrict__ q) {
 
 void launch_al_warm(const Dev& d, cudaStream_t st, long long* launches) {
     if (d.Nal == 0) return;
-    k_al_warm<<<(d.Nc + 255) / 256, 256, 0, st>>>(d);
+    launch_pdl(k_al_warm, dim3((d.Nc + 255) / 256), dim3(256), 0, st, d);
     *launches += 1;
 }
 

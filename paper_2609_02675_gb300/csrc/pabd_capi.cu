@@ -207,6 +207,7 @@ void enqueue_step(pabd_scene* s, long long* launches, const cudaEvent_t* ev = nu
         if (ev) cudaEventRecordWithFlags(ev[e++], s->st, cudaEventRecordExternal);
     };
     mark();
+    launch_step_reset(d, s->st, launches);
     launch_drive_update(d, s->st, launches);
     launch_collision(d, s->st, launches);
     mark();
@@ -278,11 +279,10 @@ void enqueue_step(pabd_scene* s, long long* launches, const cudaEvent_t* ev = nu
         cur = nullptr;  // the last iterate's buffer is known on the device only
     } else if (s->mode == 2) {
         launch_end_records(d, s->st, launches);
-        // the counter of run-time extended-precision redos is reset before the sweeps (it counts
-        // the last sweep's): the sweeps then follow each other as programmatic dependents
-        cudaMemsetAsync(d.ctr + C_FP64DYN, 0, sizeof(int), s->st);
+        // (the counter of run-time extended-precision redos, which counts the last sweep's, was
+        // reset at the head of the step): the sweeps follow each other as programmatic dependents
         for (int it = 0; it < d.p.n_iter; ++it) {
-            launch_sweep_one(d, cur, nxt, it, s->lanes, s->st, launches, it > 0);
+            launch_sweep_one(d, cur, nxt, it, s->lanes, s->st, launches, true);
             float4* t = cur; cur = nxt; nxt = t;
         }
     } else {
@@ -303,6 +303,7 @@ void enqueue_step(pabd_scene* s, long long* launches, const cudaEvent_t* ev = nu
 pabd_status autotune_sweep(pabd_scene* s) {
     Dev& d = s->d;
     long long lc = 0;
+    launch_step_reset(d, s->st, &lc);
     launch_drive_update(d, s->st, &lc);
     launch_collision(d, s->st, &lc);
     launch_csr(d, s->st, &lc);
@@ -979,6 +980,7 @@ pabd_status pabd_detect(pabd_scene* s) {
     if (!s) return PABD_ERR_ARG;
     pabd_status r = finalize_scene(s);
     if (r != PABD_OK) return r;
+    launch_step_reset(s->d, s->st, &s->launches);
     launch_drive_update(s->d, s->st, &s->launches);
     launch_collision(s->d, s->st, &s->launches);
     CK(cudaGetLastError());

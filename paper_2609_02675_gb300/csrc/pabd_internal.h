@@ -131,6 +131,32 @@ struct Dev {
     int *scan_scratch;          // block sums of the scans
 };
 
+// ---- programmatic dependent launch ----
+// A kernel launched by launch_pdl may start while its predecessor on the stream is still
+// running: every kernel of the step calls pdl_enter() first, which lets its own successor
+// launch at once and then waits until its predecessor has completed and its writes are
+// visible (both are no-ops for a launch without the attribute).
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <class... KArgs, class... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, ((KArgs)args)...);
+}
+
 // ---- launchers (all asynchronous on `st`) ----
 // scan: out[0..n] exclusive prefix sums of in[0..n-1], n read from *n_dev (or n_cap if
 // n_dev is null), out[n] = total; grid sized for n_cap.
@@ -138,6 +164,8 @@ void scan_exclusive(const int* in, int* out, const int* n_dev, int n_cap, int* s
                     long long* launches);
 int scan_scratch_ints(int n_cap);
 
+// zeroes the step's counters and accumulation scratch; precedes launch_collision / launch_csr
+void launch_step_reset(const Dev& d, cudaStream_t st, long long* launches);
 void launch_collision(const Dev& d, cudaStream_t st, long long* launches);
 // LBVH pairs from this step's boxes (after k_aabb): the same output as the grid's pair stage
 void launch_lbvh_pairs(const Dev& d, cudaStream_t st, long long* launches);
