@@ -95,10 +95,16 @@ __global__ void k_aabb(Dev d) {
             large = large || !(w <= d.p.cell);
         }
     }
-    if (!large) {
-        const float wc = w * 1.01f + 1e-6f;
-        // positive floats order as ints
-        if (wc < 1e30f) atomicMax(&d.ctr[lv == 0 ? C_CELLBITS : C_CELLBITS1 + lv - 1], __float_as_int(wc));
+    // the widest box of each level (positive floats order as ints): a warp's maximum first, then
+    // one atomic per warp and level -- one per body on a single word serialises in L2
+    const float wc = w * 1.01f + 1e-6f;
+    const int bits = (!large && wc < 1e30f) ? __float_as_int(wc) : 0;
+    const int wbase = b - (int)(threadIdx.x & 31);  // the warp's lanes below N (those above returned)
+    const unsigned act = d.N - wbase >= 32 ? 0xffffffffu : ((1u << (d.N - wbase)) - 1u);
+    const bool leader = (threadIdx.x & 31) == 0;
+    for (int l = 0; l < (d.multilevel ? NLEV : 1); ++l) {
+        const int m = __reduce_max_sync(act, lv == l ? bits : 0);
+        if (leader && m > 0) atomicMax(&d.ctr[l == 0 ? C_CELLBITS : C_CELLBITS1 + l - 1], m);
     }
     d.cell[b] = make_int4(0, 0, 0, large ? -1 : 0);
     if (d.blevel) d.blevel[b] = large ? -1 : lv;
@@ -281,7 +287,13 @@ __global__ void k_pair_write(Dev d) {
             });
             __syncwarp();
             const int e = min(d.pair_off[i + 1], cap);
-            if (e - s <= 64) {  // the slice sorted by j in registers
+            if (e - s <= 32) {  // the slice sorted by j: each partner's rank among the slice
+                const int n = e - s;
+                const int j = lane < n ? d.pairs[s + lane].y : 0x7fffffff;
+                const int r = warp_rank32(j, n, lane);
+                __syncwarp();
+                if (r >= 0) d.pairs[s + r] = make_int2(i, j);
+            } else if (e - s <= 64) {  // by the bitonic network in registers
                 const int n = e - s;
                 int v0 = (2 * lane < n) ? d.pairs[s + 2 * lane].y : 0x7fffffff;
                 int v1 = (2 * lane + 1 < n) ? d.pairs[s + 2 * lane + 1].y : 0x7fffffff;
@@ -589,18 +601,21 @@ __device__ int ground_corners(const Dev& d, const FBox& fa, int a, Emit&& emit) 
     return cnt;
 }
 
+// Threads [0, cap_pairs) take the pairs, threads cap_pairs + b the ground corners of body b
+// (apart, so that no thread runs both manifolds in series).
 __global__ void k_narrow_count(Dev d) {
     pdl_enter();
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int tt = blockIdx.x * blockDim.x + threadIdx.x;
     const int np = d.ctr[C_NPAIRS];
-    if (t < np) {
-        int2 pr = d.pairs[t];
+    if (tt < np) {
+        int2 pr = d.pairs[tt];
         FBox fa, fb;
         load_box(d, pr.x, fa);
         load_box(d, pr.y, fb);
-        d.npc[t] = box_box(fa, fb, pr.x, pr.y, [](int, int, const float*, const float*, const float*, int) {});
+        d.npc[tt] = box_box(fa, fb, pr.x, pr.y, [](int, int, const float*, const float*, const float*, int) {});
     }
-    if (t < d.N) {
+    const int t = tt - d.cap_pairs;
+    if (t >= 0 && t < d.N) {
         int n = 0;
         if (d.p.has_ground && !(d.bflags[t] & BF_PINNED)) {
             FBox fa;
@@ -634,22 +649,24 @@ __device__ __forceinline__ void write_contact(const Dev& d, int slot, int type, 
     d.bn[b] = make_float4(N[0], N[1], N[2], d.p.mu);
 }
 
+// (the threads split as in k_narrow_count)
 __global__ void k_narrow_write(Dev d) {
     pdl_enter();
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int tt = blockIdx.x * blockDim.x + threadIdx.x;
     const int np = d.ctr[C_NPAIRS];
     const int npc = d.npc_off[np];
-    if (t < np) {
-        int2 pr = d.pairs[t];
+    if (tt < np) {
+        int2 pr = d.pairs[tt];
         FBox fa, fb;
         load_box(d, pr.x, fa);
         load_box(d, pr.y, fb);
-        const int base = d.npc_off[t];
+        const int base = d.npc_off[tt];
         box_box(fa, fb, pr.x, pr.y, [&](int i, int j, const float* xi, const float* xj, const float* N, int k) {
             write_contact(d, base + k, K_CONTACT, i, j, xi, xj, N);
         });
     }
-    if (t < d.N && d.gnd_cnt[t] > 0) {
+    const int t = tt - d.cap_pairs;
+    if (t >= 0 && t < d.N && d.gnd_cnt[t] > 0) {
         FBox fa;
         load_box(d, t, fa);
         const int base = npc + d.gnd_off[t];
@@ -657,7 +674,7 @@ __global__ void k_narrow_write(Dev d) {
             write_contact(d, base + k, K_GROUND, i, j, xi, xj, N);
         });
     }
-    if (t == 0) {
+    if (tt == 0) {
         int nk = npc + d.gnd_off[d.N];
         if (nk > d.cap_contacts) { atomicOr(&d.ctr[C_STATUS], ST_CAPACITY); nk = d.cap_contacts; }
         d.ctr[C_NPC] = min(npc, d.cap_contacts);
@@ -713,7 +730,7 @@ void launch_collision(const Dev& d, cudaStream_t st, long long* launches) {
             *launches += 4;
         }
     }
-    const int nt = d.cap_pairs > d.N ? d.cap_pairs : d.N;
+    const int nt = d.cap_pairs + d.N;
     launch_pdl(k_narrow_count, dim3(nblk(nt)), dim3(CT), 0, st, d);
     scan_exclusive(d.npc, d.npc_off, d.ctr + C_NPAIRS, d.cap_pairs, d.scan_scratch, st, launches);
     scan_exclusive(d.gnd_cnt, d.gnd_off, nullptr, d.N, d.scan_scratch, st, launches);

@@ -132,12 +132,13 @@ struct Dev {
 };
 
 // ---- programmatic dependent launch ----
-// A kernel launched by launch_pdl may start while its predecessor on the stream is still
-// running: every kernel of the step calls pdl_enter() first, which lets its own successor
-// launch at once and then waits until its predecessor has completed and its writes are
-// visible (both are no-ops for a launch without the attribute).
+// A kernel launched by launch_pdl may be launched while its predecessor on the stream is still
+// finishing: every kernel of the step calls pdl_enter() first, which waits until its
+// predecessor has completed and its writes are visible (a no-op for a launch without the
+// attribute).  The kernels do not signal their successors early (blocks signal as they exit):
+// measured, an early signal let waiting blocks of the successor take SM slots and made the
+// step slower.
 __device__ __forceinline__ void pdl_enter() {
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 

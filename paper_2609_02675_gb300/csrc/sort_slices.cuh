@@ -1,5 +1,6 @@
 // Sorting of short integer slices in place (ascending, keys unique within a slice): a warp's
-// bitonic network in registers for up to 64 keys, and a block's for longer slices -- runs of up
+// ranking for up to 32 keys, its bitonic network in registers for up to 64, and a block's for
+// longer slices -- runs of up
 // to LONG_SMEM keys in shared memory, then merge passes through a scratch slice.  Used for
 // the CSR of bond ends (k_step.cu) and for the pair lists of both broad phases (k_collision.cu,
 // k_lbvh.cu).
@@ -29,8 +30,27 @@ __device__ __forceinline__ void warp_sort64(int& v0, int& v1, int lane) {
     }
 }
 
-// slice v[0..n), n <= 64, by the 32 lanes of a warp (padding INT_MAX)
+// up to 32 unique keys, one per lane (lanes >= n hold nothing): each key's rank among the n,
+// counted through n broadcasts -- independent shuffles, no dependent network
+__device__ __forceinline__ int warp_rank32(int v, int n, int lane) {
+    int r = 0;
+    for (int k = 0; k < n; ++k) {
+        const int o = __shfl_sync(0xffffffffu, v, k);
+        r += (o < v) ? 1 : 0;
+    }
+    return lane < n ? r : -1;
+}
+
+// slice v[0..n), n <= 64, by the 32 lanes of a warp: by rank up to 32 keys, else the bitonic
+// network (padding INT_MAX)
 __device__ __forceinline__ void warp_sort_slice64(int* v, int n, int lane) {
+    if (n <= 32) {
+        const int x = lane < n ? v[lane] : 0x7fffffff;
+        const int r = warp_rank32(x, n, lane);
+        __syncwarp();
+        if (r >= 0) v[r] = x;
+        return;
+    }
     int v0 = (2 * lane < n) ? v[2 * lane] : 0x7fffffff;
     int v1 = (2 * lane + 1 < n) ? v[2 * lane + 1] : 0x7fffffff;
     warp_sort64(v0, v1, lane);
