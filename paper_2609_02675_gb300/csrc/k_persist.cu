@@ -86,11 +86,10 @@ __global__ void __launch_bounds__(HEAVY_T, 4) k_sweep_fused(Dev d) {
 template <int L, class X>
 __global__ void __launch_bounds__(128, 4) k_sweep_one(Dev d, const float4* __restrict__ qi, float4* __restrict__ qo,
                                                    int it, int light) {
-    // Programmatic dependent launch: this block lets the next sweep's launch proceed, then waits
-    // until the previous sweep has completed and its writes are visible (no-ops when launched
-    // without the attribute)
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    asm volatile("griddepcontrol.wait;" ::: "memory");
+    // Programmatic dependent launch: wait until the previous sweep has completed and its writes
+    // are visible (a no-op when launched without the attribute); no early signal to the next
+    // sweep, whose waiting blocks would take SM slots (measured slower)
+    pdl_enter();
     int last = it == d.p.n_iter - 1;
     if (it < 0) {
         // under a residual threshold: the sweep index and buffers from the device, the
