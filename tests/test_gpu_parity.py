@@ -576,6 +576,51 @@ def test_lbvh_pairs_match_grid_and_oracle(P, make, steps):
     bvh.close()
 
 
+def _mixed_pile():
+    """The small pile with boxes of very different widths and one fast body: eight boxes three
+    times wider, two eight times wider, one flagged large (large_he 2.5) and one thrown at
+    40 m/s, so the multilevel grid holds bodies on several levels and off the grid."""
+    sc = S.box_pile(nx=6, ny=6, nz=6, spacing=2.3, n_steps=12)
+    b = sc.bodies
+    idx = np.random.default_rng(7).choice(len(b), 12, replace=False)
+    b["he"][idx[:8]] *= 3.0
+    b["he"][idx[8:10]] *= 8.0
+    b["he"][idx[10]] = (3.0, 3.0, 3.0)
+    b["mass"][idx[:11]] *= 30.0
+    b["v"][idx[11]] = (40.0, 0.0, 0.0)
+    sc.params = dict(sc.params, large_he=2.5)
+    return sc
+
+
+def test_multilevel_grid_pairs_bit_exact(P):
+    """Pairs across grid levels, and with off-grid bodies, equal the oracle's brute-force list
+    (and the LBVH's) bit for bit; so do the contacts."""
+    sc = _mixed_pile()
+    ref = O.OracleScene(sc)
+    grid = P.Scene(sc)
+    bvh = P.Scene(sc, broadphase=1)
+    checked, offgrid = 0, 0
+    for k in range(sc.n_steps):
+        if k % 4 == 0:
+            st = ref.state()
+            for g in (grid, bvh):
+                g.set_state(st)
+                g.set_step_index(ref.step_index)
+                g.detect()
+            ref.detect()
+            rp = ref.pairs()
+            assert np.array_equal(grid.pairs(), rp), (k, len(grid.pairs()), len(rp))
+            assert np.array_equal(bvh.pairs(), rp)
+            same_contacts(grid.contacts(), ref.contacts())
+            checked += len(rp)
+            offgrid = max(offgrid, grid.info()["offgrid_bodies"])
+        ref.step(1)
+    assert checked > 300
+    assert offgrid >= 1  # the flagged body at least
+    grid.close()
+    bvh.close()
+
+
 def test_lbvh_and_grid_steps_identical(P):
     """Same pairs, so the same contacts and the same steps, bit for bit."""
     sc = S.quadruped_bed_rod(bed=(12, 2, 12), n_rod=16)
