@@ -107,11 +107,13 @@ typedef struct {
                                  runs all n_iter sweeps; 0: the library's choice (2).  All modes
                                  give the same results for the same sweep_lanes */
     int sweep_lanes;          /* lanes per body in the per-body solve: 1, 2, 4, 8 or 16; 0 = from
-                                 the body count N: the largest of 16, 8, 4, 2, 1 with lanes * N
-                                 <= 2^17 (1 at least).  Fixes the summation order (results depend on
-                                 it, not on the block / grid sizes, which the library autotunes).
-                                 A body with more than 64 bond ends is summed by a block of 128
-                                 threads in every mode. */
+                                 the scene: the largest of 16, 8, 4, 2, 1 with lanes * N <= 2^17,
+                                 but 2 instead of 1 when N <= 2^18 and fewer than half the bodies
+                                 are flagged for the extended solve.  Fixes the summation order
+                                 (results depend on it, not on the block / grid sizes, which the
+                                 library autotunes).  A body with more than 64 bond ends is
+                                 summed by a warp (up to 256 ends) or a block of 128 threads in
+                                 every mode. */
     size_t max_pairs;         /* capacities: at most 16 M pairs, 0 = 16 per body (clamped to 16 M) */
     size_t max_contacts;      /* at most 60 M, 0 = 32 per body (clamped to 60 M); at most 8 M bodies.
                                  Exceeding one in a step latches PABD_ERR_CAPACITY. */
