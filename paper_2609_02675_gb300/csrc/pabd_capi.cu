@@ -63,22 +63,23 @@ double grid_cell_cap(const std::vector<pabd_body_desc>& bodies, const std::vecto
         auto key = [&](long long x, long long y, long long z) {
             return (uint64_t)((x & 0x1fffff) | ((y & 0x1fffff) << 21) | ((z & 0x1fffff) << 42));
         };
+        // the sampled grid bodies' cells (bodies i = 0, stride, 2 stride, ...)
+        std::vector<long long> cxyz;
         std::unordered_map<uint64_t, int> cnt;
-        std::vector<long long> cx(n), cy(n), cz(n);
-        for (int i = 0; i < n; ++i) {
-            const double* c = bodies[ids[i]].c;
-            cx[i] = (long long)std::floor(c[0] / cell);
-            cy[i] = (long long)std::floor(c[1] / cell);
-            cz[i] = (long long)std::floor(c[2] / cell);
-            if (i % stride == 0 && w[i] <= cap) ++cnt[key(cx[i], cy[i], cz[i])];
-        }
-        double tests = 0.0;
         for (int i = 0; i < n; i += stride) {
             if (w[i] > cap) continue;
+            const double* c = bodies[ids[i]].c;
+            const long long x = (long long)std::floor(c[0] / cell), y = (long long)std::floor(c[1] / cell),
+                            z = (long long)std::floor(c[2] / cell);
+            cxyz.insert(cxyz.end(), {x, y, z});
+            ++cnt[key(x, y, z)];
+        }
+        double tests = 0.0;
+        for (size_t k = 0; k < cxyz.size(); k += 3) {
             for (int dz = -1; dz <= 1; ++dz)
                 for (int dy = -1; dy <= 1; ++dy)
                     for (int dx = -1; dx <= 1; ++dx) {
-                        auto it = cnt.find(key(cx[i] + dx, cy[i] + dy, cz[i] + dz));
+                        auto it = cnt.find(key(cxyz[k] + dx, cxyz[k + 1] + dy, cxyz[k + 2] + dz));
                         if (it != cnt.end()) tests += it->second;
                     }
         }
