@@ -601,28 +601,29 @@ __device__ int ground_corners(const Dev& d, const FBox& fa, int a, Emit&& emit) 
     return cnt;
 }
 
-// Threads [0, cap_pairs) take the pairs, threads cap_pairs + b the ground corners of body b
-// (apart, so that no thread runs both manifolds in series).
+// Items [0, np) are this step's pairs, items np + b the ground corners of body b (apart, so
+// that no item runs both manifolds in series); the threads stride over them.
 __global__ void k_narrow_count(Dev d) {
     pdl_enter();
-    const int tt = blockIdx.x * blockDim.x + threadIdx.x;
     const int np = d.ctr[C_NPAIRS];
-    if (tt < np) {
-        int2 pr = d.pairs[tt];
-        FBox fa, fb;
-        load_box(d, pr.x, fa);
-        load_box(d, pr.y, fb);
-        d.npc[tt] = box_box(fa, fb, pr.x, pr.y, [](int, int, const float*, const float*, const float*, int) {});
-    }
-    const int t = tt - d.cap_pairs;
-    if (t >= 0 && t < d.N) {
-        int n = 0;
-        if (d.p.has_ground && !(d.bflags[t] & BF_PINNED)) {
-            FBox fa;
-            load_box(d, t, fa);
-            n = ground_corners(d, fa, t, [](int, int, const float*, const float*, const float*, int) {});
+    const int items = np + d.N;
+    for (int tt = blockIdx.x * blockDim.x + threadIdx.x; tt < items; tt += gridDim.x * blockDim.x) {
+        if (tt < np) {
+            int2 pr = d.pairs[tt];
+            FBox fa, fb;
+            load_box(d, pr.x, fa);
+            load_box(d, pr.y, fb);
+            d.npc[tt] = box_box(fa, fb, pr.x, pr.y, [](int, int, const float*, const float*, const float*, int) {});
+        } else {
+            const int t = tt - np;
+            int n = 0;
+            if (d.p.has_ground && !(d.bflags[t] & BF_PINNED)) {
+                FBox fa;
+                load_box(d, t, fa);
+                n = ground_corners(d, fa, t, [](int, int, const float*, const float*, const float*, int) {});
+            }
+            d.gnd_cnt[t] = n;
         }
-        d.gnd_cnt[t] = n;
     }
 }
 
@@ -649,32 +650,35 @@ __device__ __forceinline__ void write_contact(const Dev& d, int slot, int type, 
     d.bn[b] = make_float4(N[0], N[1], N[2], d.p.mu);
 }
 
-// (the threads split as in k_narrow_count)
+// (the items as in k_narrow_count)
 __global__ void k_narrow_write(Dev d) {
     pdl_enter();
-    const int tt = blockIdx.x * blockDim.x + threadIdx.x;
     const int np = d.ctr[C_NPAIRS];
     const int npc = d.npc_off[np];
-    if (tt < np) {
-        int2 pr = d.pairs[tt];
-        FBox fa, fb;
-        load_box(d, pr.x, fa);
-        load_box(d, pr.y, fb);
-        const int base = d.npc_off[tt];
-        box_box(fa, fb, pr.x, pr.y, [&](int i, int j, const float* xi, const float* xj, const float* N, int k) {
-            write_contact(d, base + k, K_CONTACT, i, j, xi, xj, N);
-        });
+    const int items = np + d.N;
+    for (int tt = blockIdx.x * blockDim.x + threadIdx.x; tt < items; tt += gridDim.x * blockDim.x) {
+        if (tt < np) {
+            int2 pr = d.pairs[tt];
+            FBox fa, fb;
+            load_box(d, pr.x, fa);
+            load_box(d, pr.y, fb);
+            const int base = d.npc_off[tt];
+            box_box(fa, fb, pr.x, pr.y, [&](int i, int j, const float* xi, const float* xj, const float* N, int k) {
+                write_contact(d, base + k, K_CONTACT, i, j, xi, xj, N);
+            });
+        } else {
+            const int t = tt - np;
+            if (d.gnd_cnt[t] > 0) {
+                FBox fa;
+                load_box(d, t, fa);
+                const int base = npc + d.gnd_off[t];
+                ground_corners(d, fa, t, [&](int i, int j, const float* xi, const float* xj, const float* N, int k) {
+                    write_contact(d, base + k, K_GROUND, i, j, xi, xj, N);
+                });
+            }
+        }
     }
-    const int t = tt - d.cap_pairs;
-    if (t >= 0 && t < d.N && d.gnd_cnt[t] > 0) {
-        FBox fa;
-        load_box(d, t, fa);
-        const int base = npc + d.gnd_off[t];
-        ground_corners(d, fa, t, [&](int i, int j, const float* xi, const float* xj, const float* N, int k) {
-            write_contact(d, base + k, K_GROUND, i, j, xi, xj, N);
-        });
-    }
-    if (tt == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         int nk = npc + d.gnd_off[d.N];
         if (nk > d.cap_contacts) { atomicOr(&d.ctr[C_STATUS], ST_CAPACITY); nk = d.cap_contacts; }
         d.ctr[C_NPC] = min(npc, d.cap_contacts);
@@ -730,11 +734,11 @@ void launch_collision(const Dev& d, cudaStream_t st, long long* launches) {
             *launches += 4;
         }
     }
-    const int nt = d.cap_pairs + d.N;
-    launch_pdl(k_narrow_count, dim3(nblk(nt)), dim3(CT), 0, st, d);
+    const long long nt = (long long)d.cap_pairs + d.N;
+    launch_pdl(k_narrow_count, dim3(stride_grid(nt, CT)), dim3(CT), 0, st, d);
     scan_exclusive(d.npc, d.npc_off, d.ctr + C_NPAIRS, d.cap_pairs, d.scan_scratch, st, launches);
     scan_exclusive(d.gnd_cnt, d.gnd_off, nullptr, d.N, d.scan_scratch, st, launches);
-    launch_pdl(k_narrow_write, dim3(nblk(nt)), dim3(CT), 0, st, d);
+    launch_pdl(k_narrow_write, dim3(stride_grid(nt, CT)), dim3(CT), 0, st, d);
     *launches += 2;
 }
 

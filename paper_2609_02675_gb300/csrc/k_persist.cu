@@ -165,13 +165,14 @@ void launch_sweep_one(const Dev& d, const float4* qi, float4* qo, int it, int L,
 // copy of every bond end's record into CSR order (once per step, after the CSR sort)
 __global__ void k_end_records(Dev d) {
     pdl_enter();
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= d.end_off[d.N]) return;
-    const int bond = d.end_id[p] >> 1;
-    const int4 m = d.bmeta[bond];
-    d.rec_m[p] = make_int4(m.x, m.y, m.z, bond);
-    d.rec_a[p] = d.bxi[bond];
-    d.rec_b[p] = d.bxj[bond];
+    const int ne = d.end_off[d.N];
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < ne; p += gridDim.x * blockDim.x) {
+        const int bond = d.end_id[p] >> 1;
+        const int4 m = d.bmeta[bond];
+        d.rec_m[p] = make_int4(m.x, m.y, m.z, bond);
+        d.rec_a[p] = d.bxi[bond];
+        d.rec_b[p] = d.bxj[bond];
+    }
 }
 
 using FusedFn = void (*)(Dev);
@@ -205,7 +206,7 @@ int fused_max_blocks(int L, int block, bool fp64) {
 
 void launch_end_records(const Dev& d, cudaStream_t st, long long* launches) {
     const int nrec = d.cap_ends > 0 ? d.cap_ends : 1;
-    launch_pdl(k_end_records, dim3((nrec + 255) / 256), dim3(256), 0, st, d);
+    launch_pdl(k_end_records, dim3(stride_grid(nrec, 256)), dim3(256), 0, st, d);
     *launches += 1;
 }
 

@@ -140,24 +140,27 @@ __device__ __forceinline__ bool end_live(const Dev& d, int body) {
     return body >= 0 && !(d.bflags[body] & BF_PINNED);
 }
 
+// (both stride over this step's bonds, C_NBONDS of them)
 __global__ void k_csr_count(Dev d) {
     pdl_enter();
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= d.ctr[C_NBONDS]) return;
-    int4 m = d.bmeta[b];
-    if (end_live(d, m.x)) atomicAdd(&d.end_cnt[m.x], 1);
-    if (end_live(d, m.y)) atomicAdd(&d.end_cnt[m.y], 1);
+    const int nb = d.ctr[C_NBONDS];
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+        int4 m = d.bmeta[b];
+        if (end_live(d, m.x)) atomicAdd(&d.end_cnt[m.x], 1);
+        if (end_live(d, m.y)) atomicAdd(&d.end_cnt[m.y], 1);
+    }
 }
 
 __global__ void k_csr_fill(Dev d) {
     pdl_enter();
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= d.ctr[C_NBONDS]) return;
-    int4 m = d.bmeta[b];
-    if (end_live(d, m.x)) d.end_id[d.end_off[m.x] + atomicAdd(&d.end_cur[m.x], 1)] = 2 * b;
-    else d.end_pos[2 * b] = -1;
-    if (end_live(d, m.y)) d.end_id[d.end_off[m.y] + atomicAdd(&d.end_cur[m.y], 1)] = 2 * b + 1;
-    else d.end_pos[2 * b + 1] = -1;
+    const int nb = d.ctr[C_NBONDS];
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+        int4 m = d.bmeta[b];
+        if (end_live(d, m.x)) d.end_id[d.end_off[m.x] + atomicAdd(&d.end_cur[m.x], 1)] = 2 * b;
+        else d.end_pos[2 * b] = -1;
+        if (end_live(d, m.y)) d.end_id[d.end_off[m.y] + atomicAdd(&d.end_cur[m.y], 1)] = 2 * b + 1;
+        else d.end_pos[2 * b + 1] = -1;
+    }
 }
 
 // Sort each body's slice of end ids (one warp per body), then record every end's slot and
@@ -279,9 +282,9 @@ void launch_step_reset(const Dev& d, cudaStream_t st, long long* launches) {
 }
 
 void launch_csr(const Dev& d, cudaStream_t st, long long* launches) {
-    launch_pdl(k_csr_count, dim3(nblk(d.cap_bonds)), dim3(ST_T), 0, st, d);
+    launch_pdl(k_csr_count, dim3(stride_grid(d.cap_bonds, ST_T)), dim3(ST_T), 0, st, d);
     scan_exclusive(d.end_cnt, d.end_off, nullptr, d.N, d.scan_scratch, st, launches);
-    launch_pdl(k_csr_fill, dim3(nblk(d.cap_bonds)), dim3(ST_T), 0, st, d);
+    launch_pdl(k_csr_fill, dim3(stride_grid(d.cap_bonds, ST_T)), dim3(ST_T), 0, st, d);
     launch_pdl(k_csr_sort, dim3(nblk(d.N * 32)), dim3(ST_T), 0, st, d);
     launch_pdl(k_csr_sort_long, dim3(152), dim3(LONG_T), LONG_SMEM * sizeof(int), st, d);
     *launches += 4;

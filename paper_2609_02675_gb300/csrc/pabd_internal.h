@@ -142,6 +142,15 @@ __device__ __forceinline__ void pdl_enter() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+// Grid of a kernel that strides over a device-counted range sized for `cap` items: one
+// block per BLOCK items, at most GS_BLOCKS blocks (enough to fill every SM), so that a large
+// capacity with few live items does not dispatch thousands of idle blocks.
+constexpr int GS_BLOCKS = 152 * 8;
+inline int stride_grid(long long cap, int block) {
+    const long long b = (cap + block - 1) / block;
+    return (int)(b < 1 ? 1 : (b > GS_BLOCKS ? GS_BLOCKS : b));
+}
+
 template <class... KArgs, class... Args>
 inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                        Args... args) {
