@@ -79,10 +79,10 @@ __global__ void __launch_bounds__(HEAVY_T, 4) k_sweep_fused(Dev d) {
 }
 
 // One sweep per launch: the same per-body work as the fused kernel, with the launch boundary
-// (a graph edge) in place of the grid barrier.  Capped at 128 registers (4 blocks per SM):
-// the heavy role and the extended-precision paths, which alone need more, spill a little.  The first `light` blocks take the bodies with
-// at most HEAVY_ENDS ends (L lanes each); the HEAVY_BLOCKS blocks after them take the heavy
-// bodies, a block each.
+// (a graph edge) in place of the grid barrier.  Capped at 128 registers (4 blocks per SM),
+// without spills (the fused kernel, which loops over the sweeps, spills a few bytes).  The
+// first `light` blocks take the bodies with at most HEAVY_ENDS ends (L lanes each); the
+// HEAVY_BLOCKS blocks after them take the heavy bodies.
 template <int L, class X>
 __global__ void __launch_bounds__(128, 4) k_sweep_one(Dev d, const float4* __restrict__ qi, float4* __restrict__ qo,
                                                    int it, int light) {
