@@ -131,3 +131,51 @@ def test_zero_threshold_changes_nothing():
     a.step(5)
     b.step(5)
     assert np.array_equal(a.state(), b.state()) and a.last_sweeps() == 40
+
+
+def _corner_dev(a, b, he):
+    """max corner distance between two states / scene diagonal (no GPU helpers here)."""
+    signs = np.array([[sx, sy, sz] for sx in (-1, 1) for sy in (-1, 1) for sz in (-1, 1)], dtype=float)
+
+    def corners(st):
+        x = signs[None, :, :] * he[:, None, :]
+        A = st[:, 3:12].reshape(-1, 3, 3)
+        return st[:, None, 0:3] + np.einsum("nij,nkj->nki", A, x)
+
+    ca, cb = corners(a), corners(b)
+    y = cb.reshape(-1, 3)
+    diag = max(float(np.linalg.norm(y.max(0) - y.min(0))), 1.0)
+    return float(np.linalg.norm(ca - cb, axis=-1).max()) / diag
+
+
+def test_unconverged_sweeps_amplify_input_rounding():
+    """Where a scene's sweeps do not converge, the step amplifies a perturbation of its input:
+    on the batched trees at step 17, a group runs all 40 sweeps without reaching the 1e-3
+    threshold, and rounding the start state to single precision moves the result about 30
+    times more after 40 sweeps than after 10 (1.0e-5 against 3.1e-7 of the scene diagonal).  This is the map's own sensitivity (the oracle
+    against itself), which bounds how closely any single-precision path can follow it there."""
+    def mk(n_iter, tol):
+        sc = S.batched_trees(n_scenes=24, n_steps=30)
+        sc.params = dict(sc.params, n_iter=n_iter, resid_tol=tol)
+        return sc
+
+    sc = mk(40, 1e-3)
+    he = np.asarray(sc.bodies["he"], dtype=float)
+    ref = O.OracleScene(sc)
+    ref.step(17)
+    st0, k0 = ref.state(), ref.step_index
+    sens = {}
+    for n_iter in (10, 40):
+        a = O.OracleScene(mk(n_iter, 0.0))
+        a.set_state(st0)
+        a.step_index = k0
+        a.step(1)
+        b = O.OracleScene(mk(n_iter, 0.0))
+        b.set_state(st0.astype(np.float32).astype(np.float64))
+        b.step_index = k0
+        b.step(1)
+        sens[n_iter] = _corner_dev(b.state(), a.state(), he)
+    ref.step(1)
+    assert ref.last_sweeps() == 40  # some group never reached the threshold
+    assert sens[10] < 1e-6
+    assert sens[40] > 3e-6 and sens[40] > 10.0 * sens[10], sens
