@@ -1,23 +1,30 @@
 """Benchmark of the projective affine body step on GB300.
 
-Workload (default): the 4096-box pile -- boxes with edges U[0.5, 2], density U[500, 2000],
-dropped from a jittered 16^3 grid (spacing 3.5) onto the ground, contacts rebuilt every
-step by the grid-hash broad phase, mu = 0.5, h = 1/60, 30 sweeps per step.  A timed "step"
-is one whole time step of Algorithm 1 (collision detection, predictor, 30 bond + solve
-sweeps, velocity recovery).  The K timed steps are steps 0..K-1 of the pile's trajectory
-(warm-up steps are run first and then the initial state is restored).
+Headline workload (default): 4096 independent articulated trees of U{4..64} boxes (139 690
+bodies; spherical, revolute and nonlinear elastic joints; ground contact), batched into one
+scene, h = 1/120, 10 sweeps per step.  A timed "step" is one whole time step of Algorithm 1
+(collision detection, predictor, the sweeps of the global and local solves, velocity
+recovery).  The timed window is steps S..S+K-1 with S = 60 by default (0.5 s: the trees have
+landed and stand on the ground, so every sweep carries bonds and ground contacts); the lead-in
+steps 0..S-1 run untimed, and warm-up steps are run from step S and then undone by restoring
+the step-S state.
 
-Metric: body-iterations per second (bodies x sweeps per step x steps / time), with steps/s,
-the plain (eager, kernel-by-kernel) path's throughput and the end-to-end number through the
-C-ABI with host buffers.  L2 is flushed between timed steps (a 256 MB write).
+Metric: body-iterations per second (bodies x sweeps per step x steps / time) with steps/s, the
+plain (eager, kernel-by-kernel) path, the end-to-end number through the C-ABI with host
+buffers, the roofline of the sweep kernel measured inside the same window, and -- with the
+headline only -- the 4096-box pile on a landed window, the quadruped on its granular bed, the
+trees run one scene at a time on the plain path, and a short served run (p50/p99 step latency).
+L2 is flushed between timed steps (a 256 MB write).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload trees|pile|quadruped|served|stack|spring|net] [--start-step S]
 
---impl reference times the FP64 CPU oracle (test infrastructure) on the same workload:
-each step is one oracle step of the pile; only rank 0 runs it.
-Under torchrun (N > 1) every rank steps its own replica of the scene: the path does not
-shard, so there is no collective in the data path; the barrier and the max over ranks of
-the timed region come from torch.distributed.
+--impl reference times the FP64 CPU oracle (test infrastructure) on a bounded sample of the
+same workload and window (a subset of the trees: the trees are independent scenes, so a
+subset steps exactly as it does inside the batch); only rank 0 runs it and it never loads the
+CUDA library.  Under torchrun (N > 1) every rank steps its own replica: the path does not
+shard, so there is no collective in the data path; the barrier and the max over ranks of the
+timed region come from torch.distributed.
 """
 from __future__ import annotations
 
@@ -39,6 +46,9 @@ import scenes as S  # noqa: E402
 
 METRIC = "body-iterations/s"
 UNIT = "body-iter/s"
+L2_NOTE = "flushed between timed steps (256 MB write)"
+# relative per-step position tolerance of the single-precision path against the FP64 oracle
+REL_TOL = 1e-5
 
 
 def _peaks():
@@ -96,63 +106,66 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-ARGS = None
+# ---------------------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------------------
+
+# untimed lead-in steps before the timed window: the trees have landed by 0.5 s; the lower
+# layers of the 4096 pile by step 150; the quadruped's legs reach the bed by step 30
+DEFAULT_START = {"trees": 60, "pile": 150, "quadruped": 30}
 
 
-def workload():
-    sc = _workload()
-    if ARGS is not None and ARGS.resid_tol > 0:
-        sc.params = dict(sc.params, resid_tol=ARGS.resid_tol)
+def make_workload(name: str, bodies: int = 4096, stacked: bool = False, resid_tol: float = 0.0):
+    if name == "trees":
+        sc = S.batched_trees()
+    elif name == "quadruped":
+        sc = S.quadruped_bed_rod()
+    elif name == "stack":
+        sc = S.mass_ratio_stack()
+    elif name == "spring":
+        sc = S.two_box_spring()
+    elif name == "net":
+        sc = S.spring_net()
+    elif bodies == 4096 and not stacked:
+        sc = S.box_pile()
+    else:
+        sc = S.box_pile_n(bodies, stacked=stacked)
+    if resid_tol > 0:
+        sc.params = dict(sc.params, resid_tol=resid_tol)
     return sc
 
 
-def _workload():
-    if ARGS is not None and ARGS.workload == "trees":
-        return S.batched_trees()
-    if ARGS is not None and ARGS.workload == "quadruped":
-        return S.quadruped_bed_rod()
-    if ARGS is not None and ARGS.workload == "stack":
-        return S.mass_ratio_stack()
-    if ARGS is not None and ARGS.workload == "spring":
-        return S.two_box_spring()
-    if ARGS is not None and ARGS.workload == "net":
-        return S.spring_net()
-    n = ARGS.bodies if ARGS is not None else 4096
-    if n == 4096 and not (ARGS is not None and ARGS.stacked):
-        return S.box_pile()
-    return S.box_pile_n(n, stacked=bool(ARGS is not None and ARGS.stacked))
+def start_step(name: str, stacked: bool, bodies: int, given: int) -> int:
+    if given >= 0:
+        return given
+    if name == "pile" and (stacked or bodies != 4096):
+        return 0  # stacked columns touch from step 0
+    return DEFAULT_START.get(name, 0)
 
 
-def config_of(sc, K):
-    start = ARGS.start_step if ARGS is not None else 0
-    if ARGS is not None and ARGS.workload in ("stack", "spring", "net"):
-        desc = {"stack": "six-cube stack, each cube 10x heavier than the one below",
-                "spring": "two unit cubes joined by a spring stretched to twice its rest length",
-                "net": "11 x 11 net of cubes joined by 220 pre-stretched springs, top corners pinned"}[ARGS.workload]
-        return {"workload": desc + f" ({sc.n_bodies} bodies), {sc.params['n_iter']} sweeps, steps {start}..{start + K - 1}",
-                "n_bodies": sc.n_bodies, "n_iter": sc.params["n_iter"], "l2": "flushed between timed steps (256 MB write)",
-                "parallelism": "replicas", **_tol_cfg()}
-    if ARGS is not None and ARGS.workload in ("trees", "quadruped"):
-        if ARGS.workload == "trees":
-            desc = (f"{sc.n_groups} independent trees of 4-64 boxes ({sc.n_bodies} bodies), ground contact, "
-                    f"{sc.params['n_iter']} sweeps, h=1/120, one batched scene")
-        else:
-            desc = (f"driven 13-body quadruped on a bed of {sc.meta['n_bed']} cubes + {sc.meta['n_rod']}-segment "
-                    f"elastic rod ({sc.n_bodies} bodies), {sc.params['n_iter']} sweeps, h=1/60")
-        return {"workload": desc + f", steps {start}..{start + K - 1}", "n_bodies": sc.n_bodies,
-                "n_iter": sc.params["n_iter"], "l2": "flushed between timed steps (256 MB write)",
-                "parallelism": "replicas", **_tol_cfg()}
-    kind = "stacked columns" if (ARGS is not None and ARGS.stacked) else "jittered grid, spacing 3.5"
-    return {"workload": f"box pile {sc.n_bodies} ({kind}), {sc.params['n_iter']} sweeps, "
-                        f"h=1/60, steps {start}..{start + K - 1} of the trajectory",
-            "n_bodies": sc.n_bodies, "n_iter": sc.params["n_iter"], "l2": "flushed between timed steps (256 MB write)",
-            "parallelism": "replicas", **_tol_cfg()}
+def describe(name: str, sc, start: int, K: int, stacked: bool = False) -> str:
+    win = f"steps {start}..{start + K - 1}"
+    it = sc.params["n_iter"]
+    if name == "trees":
+        return (f"{sc.n_groups} independent trees of 4-64 boxes ({sc.n_bodies} bodies), spherical/revolute/"
+                f"nonlinear-elastic joints, ground contact, {it} sweeps, h=1/120, one batched scene, {win} "
+                f"(landed)")
+    if name == "quadruped":
+        return (f"driven 13-body quadruped on a bed of {sc.meta['n_bed']} cubes + {sc.meta['n_rod']}-segment "
+                f"elastic rod ({sc.n_bodies} bodies), {it} sweeps, h=1/60, {win}")
+    if name in ("stack", "spring", "net"):
+        d = {"stack": "six-cube stack, each cube 10x heavier than the one below",
+             "spring": "two unit cubes joined by a spring stretched to twice its rest length",
+             "net": "11 x 11 net of cubes joined by 220 pre-stretched springs, top corners pinned"}[name]
+        return f"{d} ({sc.n_bodies} bodies), {it} sweeps, {win}"
+    kind = "stacked columns" if stacked else "jittered grid, spacing 3.5"
+    return f"box pile {sc.n_bodies} ({kind}), {it} sweeps, h=1/60, {win} of the trajectory"
 
 
-def _tol_cfg():
-    if ARGS is None or ARGS.resid_tol <= 0:
+def tol_cfg(resid_tol: float) -> dict:
+    if resid_tol <= 0:
         return {}
-    return {"resid_tol": ARGS.resid_tol,
+    return {"resid_tol": resid_tol,
             "note": "each scene stops at its first sweep with residual <= resid_tol (at most n_iter); "
                     "body-iterations count the sweeps actually run (mean_sweeps_per_step)"}
 
@@ -161,21 +174,28 @@ def _kernel_hash():
     """Hash of the sources of the sweep kernels (their arithmetic and memory accesses)."""
     h = hashlib.sha256()
     for f in ("k_sweep.cu", "k_persist.cu", "sweep_math.cuh", "dfloat.cuh"):
-        with open(os.path.join(ROOT, "paper_2609_02675_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        p = os.path.join(ROOT, "paper_2609_02675_gb300", "csrc", f)
+        if os.path.exists(p):
+            with open(p, "rb") as fh:
+                h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def _ncu_traffic(kernel: str, workload: str):
-    """dram bytes per launch of `kernel` on `workload` from the committed ncu summary, if it
-    was taken on the current kernel source (else None)."""
+def window_key(name: str, n_bodies: int, start: int, stacked: bool = False) -> str:
+    """Key of a measured window in profiles/traffic.json: workload, size and first step."""
+    return f"{name}|{'stacked' if stacked else 'default'}|{n_bodies}|start{start}"
+
+
+def _ncu_traffic(kernel: str, key: str):
+    """DRAM bytes per launch of `kernel` on the window `key` from the committed ncu summary,
+    if it was taken on the current sweep source (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
             t = json.load(f)
         if t.get("source_hash") != _kernel_hash():
             return None
-        return t["entries"].get(f"{kernel}|{workload}")
+        return t["entries"].get(f"{kernel}|{key}")
     except Exception:
         return None
 
@@ -212,64 +232,132 @@ def host_cpu() -> str:
     return f"{model} ({os.cpu_count()} logical cores)"
 
 
-def cpu_baseline(budget_s: float = 15.0, max_steps: int = 300):
-    """The FP64 oracle (as it stands) on the same pile, steps 0..M-1 within the time budget."""
+# ---------------------------------------------------------------------------------------
+# error measure of a step against the oracle (same definition as the parity tests)
+# ---------------------------------------------------------------------------------------
+
+_SIGNS = np.array([[sx, sy, sz] for sz in (-1, 1) for sy in (-1, 1) for sx in (-1, 1)], dtype=np.float64)
+
+
+def _corners(st: np.ndarray, he: np.ndarray) -> np.ndarray:
+    x = _SIGNS[None, :, :] * he[:, None, :]
+    A = st[:, 3:12].reshape(-1, 3, 3)
+    return st[:, None, 0:3] + np.einsum("nij,nkj->nki", A, x)
+
+
+def rel_err(st_gpu: np.ndarray, st_ref: np.ndarray, he: np.ndarray) -> float:
+    """max over bodies and box corners |y_gpu - y_ref| / the bounding-box diagonal (>= 1)."""
+    y = _corners(st_ref, he).reshape(-1, 3)
+    scale = max(float(np.linalg.norm(y.max(0) - y.min(0))), 1.0)
+    d = np.linalg.norm(_corners(st_gpu, he) - _corners(st_ref, he), axis=-1)
+    return float(d.max()) / scale
+
+
+# ---------------------------------------------------------------------------------------
+# oracle legs: the CPU baseline (and the sampled parity check it enables), the reference arm
+# ---------------------------------------------------------------------------------------
+
+def oracle_sample(name: str, sc):
+    """A bounded sample of the workload for the FP64 oracle: for the trees the groups
+    0, 16, 32, ... (256 of the 4096 independent trees), else the whole scene."""
+    if name == "trees" and sc.n_groups > 256:
+        groups = np.arange(0, sc.n_groups, sc.n_groups // 256)[:256]
+        sub = S.select_groups(sc, groups)
+        return sub, groups, f"{len(groups)} of the {sc.n_groups} trees (every {sc.n_groups // 256}th, " \
+                            f"{sub.n_bodies} bodies)"
+    return sc, None, f"the whole scene ({sc.n_bodies} bodies)"
+
+
+def cpu_baseline(name: str, sc, start: int, K: int, budget_s: float = 15.0, gpu_check=None):
+    """The FP64 oracle (as it stands, one thread) on a sample of the same workload: an
+    untimed lead-in to step `start`, then steps start..start+M-1 timed (M <= K, within the
+    budget).  With gpu_check(sample_state, groups, k) -> gpu next-step rows of the sample,
+    also the per-step error of the GPU step started from the oracle's state at step k
+    (teacher-forced) on that sample."""
     import oracle as O
-    sc = workload()
-    o = O.OracleScene(sc)
+    sub, groups, what = oracle_sample(name, sc)
+    o = O.OracleScene(sub)
+    t_lead = time.perf_counter()
+    if start:
+        o.step(start)
+    t_lead = time.perf_counter() - t_lead
+    st_start, k_start = o.state(), o.step_index
     t0 = time.perf_counter()
     m = 0
-    while m < max_steps and time.perf_counter() - t0 < budget_s:
+    while m < K and time.perf_counter() - t0 < budget_s:
         o.step(1)
         m += 1
     dt = time.perf_counter() - t0
-    return {"value": sc.n_bodies * sc.params["n_iter"] * m / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle steps 0..{m - 1} of the {sc.n_bodies}-box pile ({m} steps, {dt:.1f} s, single thread)",
-            "host": host_cpu()}
+    out = {"value": sub.n_bodies * sub.params["n_iter"] * m / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"oracle on {what}, steps {start}..{start + m - 1} timed ({m} steps, {dt:.1f} s) after an "
+                     f"untimed lead-in of {start} steps ({t_lead:.1f} s), single thread",
+           "host": host_cpu()}
+    parity = None
+    if gpu_check is not None:
+        # teacher-forced: the GPU runs the full workload (same launch configuration as the
+        # timed window) from the oracle's step-`start` state on the sampled rows
+        ref = O.OracleScene(sub)
+        ref.set_state(st_start)
+        ref.step_index = k_start
+        ref.step(1)
+        g_rows = gpu_check(st_start, groups, k_start)
+        he = np.ascontiguousarray(sub.bodies["he"], dtype=np.float64)
+        e = rel_err(g_rows, ref.state(), he)
+        parity = {"max_rel_err": e, "tol": REL_TOL, "pass": bool(e < REL_TOL),
+                  "kind": "one teacher-forced step: the GPU (full workload, timed launch configuration) starts "
+                          "from the oracle's state; max over bodies and box corners of |y_gpu - y_ref| / scene "
+                          "diagonal",
+                  "sample": f"{what}, step {k_start}"}
+    return out, parity
 
 
 def run_reference(args, rank, world):
+    """The oracle as the reference arm, on the same window of a bounded sample of the same
+    workload (it never imports the CUDA library)."""
     if rank != 0:
         return
     import oracle as O
-    sc = workload()
-    o = O.OracleScene(sc)
-    for _ in range(args.warmup):
-        o.step(1)
-    o = O.OracleScene(sc)
+    name = args.workload
+    sc = make_workload(name, args.bodies, args.stacked, args.resid_tol)
+    start = start_step(name, args.stacked, args.bodies, args.start_step)
+    sub, _, what = oracle_sample(name, sc)
+    o = O.OracleScene(sub)
+    if start:
+        o.step(start)
+    st0, k0 = o.state(), o.step_index
+    o.step(args.warmup)
+    o.set_state(st0)
+    o.step_index = k0
     t0 = time.perf_counter()
     o.step(args.steps)
     dt = time.perf_counter() - t0
-    v = sc.n_bodies * sc.params["n_iter"] * args.steps / dt
+    v = sub.n_bodies * sub.params["n_iter"] * args.steps / dt
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_of(sc, args.steps),
+            "config": {"workload": describe(name, sc, start, args.steps, args.stacked), "n_bodies": sc.n_bodies,
+                       "n_iter": sc.params["n_iter"], "l2": L2_NOTE, "parallelism": "replicas",
+                       **tol_cfg(args.resid_tol)},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"oracle steps 0..{args.steps - 1} of the pile, single thread",
-                             "host": host_cpu()},
+                             "sample": f"oracle on {what}, steps {start}..{start + args.steps - 1} after an untimed "
+                                       f"lead-in, single thread", "host": host_cpu()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def run_ours(args, rank, world, local_rank):
-    import torch
-    import paper_2609_02675_gb300 as P
+# ---------------------------------------------------------------------------------------
+# the CUDA path
+# ---------------------------------------------------------------------------------------
 
-    dev = local_rank
-    torch.cuda.set_device(dev)
-    stream = torch.cuda.Stream(dev)
-    sc = workload()
-    K, W = args.steps, args.warmup
-    # a settled granular bed reaches about 13 candidate pairs and 30 contact points per grain
-    cap = dict(max_pairs=32 * sc.n_bodies, max_contacts=64 * sc.n_bodies) if args.workload == "quadruped" else {}
-    g = P.Scene(sc, device=dev, stream=stream, sweep_mode=args.sweep_mode, sweep_lanes=args.lanes, **cap)
-    st0 = g.state()
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
-
-    def reset():
-        g.set_state(st0)
-        g.set_step_index(args.start_step)
+def measure(P, torch, sc, name, start, K, W, dev, stream, world=1, flush=None, sweep_mode=0, lanes=0,
+            stacked=False, plain=True, e2e=True, keep=False):
+    """Time K graph steps of `sc` from step `start` (after an untimed lead-in and W warm-up
+    steps that are undone), then the same steps with the stage events, on the plain path and
+    end to end.  Returns a dict of the measurements (and the scene if keep)."""
+    cap = dict(max_pairs=32 * sc.n_bodies, max_contacts=64 * sc.n_bodies) if name == "quadruped" else {}
+    g = P.Scene(sc, device=dev, stream=stream, sweep_mode=sweep_mode, sweep_lanes=lanes, **cap)
+    if flush is None:
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
 
     def l2_flush():
         with torch.cuda.stream(stream):
@@ -280,21 +368,23 @@ def run_ours(args, rank, world, local_rank):
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
 
-    # optional untimed lead-in (part of preparing the input state), then warm-up and restore
-    if args.start_step:
-        g.step(args.start_step)
+    if start:
+        g.step(start)
         g.sync()
-        st0 = g.state()
-    g.set_step_index(args.start_step)
+    st0 = g.state()
+
+    def reset():
+        g.set_state(st0)
+        g.set_step_index(start)
+
     g.step(W)
     g.sync()
     reset()
     n_body_iter = sc.n_bodies * sc.params["n_iter"]
     mean_sweeps = None
     if sc.params.get("resid_tol", 0.0) > 0:
-        # sweeps actually run per step under the threshold, from the same steps (untimed pass)
         counts = []
-        for k in range(K):
+        for _ in range(K):
             g.step(1)
             counts.append(g.info()["last_sweeps"])
         mean_sweeps = float(np.mean(counts))
@@ -315,153 +405,125 @@ def run_ours(args, rank, world, local_rank):
     t_ms = sum(a.elapsed_time(b) for a, b in ev)
     g.sync()
     info1 = g.info()
-    launches = info1["launches"] - info0["launches"]
+    out = {"g": g, "t_ms": t_ms, "n_body_iter": n_body_iter, "mean_sweeps": mean_sweeps, "clocks": clk.summary(),
+           "launches": info1["launches"] - info0["launches"], "info": info1, "K": K, "st0": st0}
 
     # live stage timing of the same K steps (graph with event nodes between the stages)
     reset()
     g.set_profiling(True)
     g.profile(reset=True)
-    for k in range(K):
+    for _ in range(K):
         l2_flush()
         g.step(1)
-    prof = g.profile(reset=True)
+    out["prof"] = g.profile(reset=True)
     g.set_profiling(False)
 
-    # plain path: the same steps launched kernel by kernel
+    if plain:
+        reset()
+        evp = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        barrier()
+        for k in range(K):
+            l2_flush()
+            evp[k][0].record(stream)
+            g.step_eager(1)
+            evp[k][1].record(stream)
+        barrier()
+        out["t_plain"] = sum(a.elapsed_time(b) for a, b in evp)
+
+    if e2e:
+        # end to end through the C-ABI with host buffers: write state (H2D), step, read state (D2H)
+        reset()
+        rows = g.state()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(K):
+            g.set_state(rows)
+            g.step(1)
+            g.state(out=rows)
+        barrier()
+        out["t_e2e_ms"] = (time.perf_counter() - t0) * 1e3
+        out["h2d"] = sc.n_bodies * 96
+        out["d2h"] = sc.n_bodies * 96
     reset()
-    evp = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    barrier()
-    for k in range(K):
-        l2_flush()
-        evp[k][0].record(stream)
-        g.step_eager(1)
-        evp[k][1].record(stream)
-    barrier()
-    t_plain = sum(a.elapsed_time(b) for a, b in evp)
+    if not keep:
+        g.close()
+        out["g"] = None
+    return out
 
-    # batched scenes: the same scenes each run alone on the plain path (a sample, eager launches)
-    alone = None
-    if args.workload == "trees":
-        sizes = sc.meta["sizes"]
-        off = np.concatenate([[0], np.cumsum(sizes)])
-        pick = np.linspace(0, len(sizes) - 1, 32).astype(int)
-        t_alone, body_iter = 0.0, 0
-        for gi in pick:
-            sl = slice(off[gi], off[gi + 1])
-            sub = S.Scene("one", dict(sc.params), sc.bodies[sl].copy(), sc.bonds.copy(), 1)
-            sub.bodies["group"] = 0
-            m = (sc.bonds["i"] >= off[gi]) & (sc.bonds["i"] < off[gi + 1])
-            sub.bonds = sc.bonds[m].copy()
-            sub.bonds["i"] -= off[gi]
-            sub.bonds["j"] = np.where(sub.bonds["j"] >= 0, sub.bonds["j"] - off[gi], -1)
-            one = P.Scene(sub, device=dev, stream=stream)
-            one.step_eager(2)
-            one.sync()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            one.step_eager(min(K, 20))
-            e1.record(stream)
-            e1.synchronize()
-            t_alone += e0.elapsed_time(e1)
-            body_iter += int(sizes[gi]) * sc.params["n_iter"] * min(K, 20)
-            one.close()
-        alone = {"value": body_iter / (t_alone * 1e-3), "unit": UNIT,
-                 "sample": "32 of the scenes, each alone on the plain path (eager launches), 20 steps each"}
 
-    # end to end through the C-ABI with host buffers: write state (H2D), step, read state (D2H)
-    reset()
-    rows = g.state()
-    h2d = sc.n_bodies * 96
-    d2h = sc.n_bodies * 96
-    barrier()
-    t0 = time.perf_counter()
-    for k in range(K):
-        g.set_state(rows)
-        g.step(1)
-        g.state(out=rows)
-    barrier()
-    t_e2e = time.perf_counter() - t0
-
-    # max over ranks
-    t_ms, t_plain, t_e2e_ms = max_over_ranks([t_ms, t_plain, t_e2e * 1e3], world, f"cuda:{dev}")
-    g.close()
-    if rank != 0:
-        return
-    total_body_iter = n_body_iter * K * world
-    value = job_throughput(n_body_iter * K, world, t_ms)
-
-    # roofline of the sweep: per launch of the sweep kernel, algorithmic bytes / average
-    # duration (the sweep stage's events bracket all its launches of a step)
+def roofline(m, sc, name, start, stacked=False):
+    """Roofline of the sweep kernel inside the timed window: algorithmic bytes per launch
+    (164 B per body + 148 B per bond, this window's own mean bond count) / its mean duration
+    (the sweep stage's events bracket all its launches of a step)."""
+    prof, info = m["prof"], m["info"]
     steps = max(prof["steps"], 1)
     n_it = sc.params["n_iter"]
     bonds_avg = prof["bonds_sum"] / steps
     N = sc.n_bodies
-    mode = info1["sweep_mode"]
-    # per sweep: each body moves q in / out, s, mass, flags, CSR offsets and its residual
-    # (176 B); each bond its two CSR-ordered end records (2 x 48 B) and, for a contact, its
-    # normal twice (2 x 16 B); the two-launch mode also writes and re-reads the end records
-    per_sweep = 176.0 * N + 128.0 * bonds_avg
+    mode = info["sweep_mode"]
+    per_sweep = 164.0 * N + 148.0 * bonds_avg
     if mode == 3:
-        kernel, per_launch_bytes = "k_sweep_fused", n_it * per_sweep
+        kernel, per_launch = "k_sweep_fused", n_it * per_sweep
     elif mode == 2:
-        kernel, per_launch_bytes = "k_sweep_one", per_sweep
+        kernel, per_launch = "k_sweep_one", per_sweep
     else:
-        kernel, per_launch_bytes = "k_bond+k_solve", per_sweep + 64.0 * bonds_avg
-    launches_per_step = prof["sweep_launches"] / steps
+        kernel, per_launch = "k_bond+k_solve", per_sweep
     ms_launch = prof["sweep_ms"] / max(prof["sweep_launches"], 1)
     if mode == 1:
         ms_launch *= 2.0  # one bond + one solve launch per sweep
-    achieved = per_launch_bytes / (ms_launch * 1e-3) / 1e9
+    achieved = per_launch / (ms_launch * 1e-3) / 1e9
     peak, peak_kind = _peaks()
-    wl_key = f"{args.workload}|{'stacked' if args.stacked else 'grid'}|{sc.n_bodies}"
-    tr = _ncu_traffic(kernel, wl_key)
-    roof = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
+    key = window_key(name, N, start, stacked)
+    tr = _ncu_traffic(kernel, key)
+    return {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs (of {peak_kind})",
             "traffic": tr["bytes_per_launch"] if tr else None,
-            "bytes_per_launch": per_launch_bytes, "us_per_launch": ms_launch * 1e3, "bonds_per_step": bonds_avg,
-            "launches_per_step": launches_per_step,
+            "traffic_window": key if tr else None,
+            "bytes_per_launch": per_launch, "bytes_formula": "164 * bodies + 148 * bonds (this window's mean)",
+            "us_per_launch": ms_launch * 1e3, "bonds_per_step": bonds_avg,
+            "launches_per_step": prof["sweep_launches"] / steps,
             "stage_ms_per_step": {k: prof[k] / steps for k in ("collision_ms", "csr_ms", "predict_ms", "sweep_ms",
                                                                  "finalize_ms", "step_ms")}}
-    cfg = config_of(sc, K)
-    cfg["sweep"] = {k: info1[k] for k in ("sweep_mode", "sweep_lanes", "sweep_block", "sweep_grid")}
-    if mean_sweeps is not None:
-        cfg["mean_sweeps_per_step"] = mean_sweeps
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
-        "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic", "config": cfg,
-        "steps_per_s": world * K / (t_ms * 1e-3),
-        "plain_path": {"value": job_throughput(n_body_iter * K, world, t_plain), "unit": UNIT, "ms_per_step": t_plain / K},
-        "e2e": {"value": job_throughput(n_body_iter * K, world, t_e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
-        "gpu_launches": int(launches),
-        **({"scenes_alone_plain_path": alone} if alone else {}),
-        "clocks": clk.summary(),
-        "roofline": roof,
-    }
-    if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
-    print(json.dumps(line), flush=True)
 
 
-def run_served(args, dev):
-    """Poisson stream of step requests over resident pile scenes of 10 to 1e5 bodies (one
-    line per rate), against each scene's step alone on the plain path."""
-    import torch
-    import paper_2609_02675_gb300 as P
+def alone_plain(P, torch, sc, dev, stream, K):
+    """32 of the batched scenes, each alone in its own library scene on the plain path."""
+    sizes = sc.meta["sizes"]
+    pick = np.linspace(0, len(sizes) - 1, 32).astype(int)
+    t_alone, body_iter = 0.0, 0
+    for gi in pick:
+        sub = S.select_groups(sc, [gi])
+        one = P.Scene(sub, device=dev, stream=stream)
+        one.step_eager(2)
+        one.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        one.step_eager(min(K, 20))
+        e1.record(stream)
+        e1.synchronize()
+        t_alone += e0.elapsed_time(e1)
+        body_iter += int(sizes[gi]) * sc.params["n_iter"] * min(K, 20)
+        one.close()
+    return {"value": body_iter / (t_alone * 1e-3), "unit": UNIT, "ms_per_scene_step": t_alone / len(pick) / min(K, 20),
+            "sample": f"{len(pick)} of the trees, each alone in its own scene on the plain path (eager launches), "
+                      f"{min(K, 20)} steps each from step 0"}
+
+
+def served(P, torch, dev, rates, duration, drain=20.0):
+    """Poisson step requests over resident pile scenes of 10 to 1e5 bodies (one entry per
+    rate), against each scene's step alone on the plain path."""
     from paper_2609_02675_gb300.serve import Server, replay
-    torch.cuda.set_device(dev)
 
     def make(n):
         return S.box_pile_n(int(n), seed=S.SEED_BASE + 5, stacked=True, n_iter=30)
 
     out = []
-    for rate in [float(x) for x in args.rates.split(",")]:
-        reqs, sizes = S.request_stream(rate=rate, duration=args.duration, max_scenes=64)
+    for rate in rates:
+        reqs, sizes = S.request_stream(rate=rate, duration=duration, max_scenes=64)
         srv = Server(lambda sid: make(sizes[sid]), hbm_budget=32 << 30, device=dev)
-        t0, t1 = replay(srv, reqs, duration=args.duration, drain_timeout=20.0)
+        t0, t1 = replay(srv, reqs, duration=duration, drain_timeout=drain)
         st = srv.stats(t0, t1)
-        # plain path: each distinct scene size stepped alone (sampled), mean step time
+        srv.close()
         pick = sorted(set(sizes))[:: max(1, len(set(sizes)) // 8)]
         alone_ms = []
         for n in pick:
@@ -473,49 +535,153 @@ def run_served(args, dev):
             g.sync()
             alone_ms.append((time.perf_counter() - t) / 3 * 1e3)
             g.close()
-        srv.close()
         st.update({"rate": rate, "scenes": len(sizes), "plain_path_step_ms_mean": float(np.mean(alone_ms)),
                    "plain_path_sizes": [int(n) for n in pick]})
         out.append(st)
         torch.cuda.empty_cache()
+    return out
+
+
+def side_line(name, sc, m, start, K, stacked=False):
+    """A compact record of a non-headline workload measured in the same run."""
+    n_it = m["n_body_iter"]
+    r = roofline(m, sc, name, start, stacked)
+    d = {"workload": describe(name, sc, start, K, stacked), "value": n_it * K / (m["t_ms"] * 1e-3), "unit": UNIT,
+         "ms_per_step": m["t_ms"] / K, "steps_per_s": K / (m["t_ms"] * 1e-3),
+         "sweep": {k: r[k] for k in ("kernel", "us_per_launch", "bytes_per_launch", "bonds_per_step", "frac",
+                                     "achieved", "traffic")}}
+    if "t_plain" in m:
+        d["plain_path"] = {"value": n_it * K / (m["t_plain"] * 1e-3), "ms_per_step": m["t_plain"] / K}
+    return d
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2609_02675_gb300 as P
+
+    dev = local_rank
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    name = args.workload
+    sc = make_workload(name, args.bodies, args.stacked, args.resid_tol)
+    start = start_step(name, args.stacked, args.bodies, args.start_step)
+    K, W = args.steps, args.warmup
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
+    m = measure(P, torch, sc, name, start, K, W, dev, stream, world, flush, args.sweep_mode, args.lanes,
+                args.stacked, keep=True)
+    g = m["g"]
+    t_ms, t_plain, t_e2e_ms = max_over_ranks([m["t_ms"], m["t_plain"], m["t_e2e_ms"]], world, f"cuda:{dev}")
+    if rank != 0:
+        g.close()
+        return
+    n_body_iter = m["n_body_iter"]
+    info1 = m["info"]
+    cfg = {"workload": describe(name, sc, start, K, args.stacked), "n_bodies": sc.n_bodies,
+           "n_iter": sc.params["n_iter"], "start_step": start, "l2": L2_NOTE, "parallelism": "replicas",
+           **tol_cfg(args.resid_tol)}
+    cfg["sweep"] = {k: info1[k] for k in ("sweep_mode", "sweep_lanes", "sweep_block", "sweep_grid")}
+    if m["mean_sweeps"] is not None:
+        cfg["mean_sweeps_per_step"] = m["mean_sweeps"]
+    line = {
+        "metric": METRIC, "value": job_throughput(n_body_iter * K, world, t_ms), "unit": UNIT, "n_gpus": world,
+        "steps": K, "warmup": W, "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+        "steps_per_s": world * K / (t_ms * 1e-3),
+        "plain_path": {"value": job_throughput(n_body_iter * K, world, t_plain), "unit": UNIT,
+                       "ms_per_step": t_plain / K},
+        "e2e": {"value": job_throughput(n_body_iter * K, world, t_e2e_ms), "unit": UNIT,
+                "h2d_bytes_per_step": m["h2d"], "d2h_bytes_per_step": m["d2h"]},
+        "gpu_launches": int(m["launches"]),
+        "clocks": m["clocks"],
+        "roofline": roofline(m, sc, name, start, args.stacked),
+    }
+    if not args.no_cpu_baseline and world == 1:
+        def gpu_check(st_sample, groups, k):
+            # the oracle's sampled rows written into the full scene's state, one graph step
+            full = m["st0"].copy()
+            rows = S.group_rows(sc, groups) if groups is not None else np.arange(sc.n_bodies)
+            full[rows] = st_sample
+            g.set_state(full)
+            g.set_step_index(k)
+            g.step(1)
+            return g.state()[rows]
+        line["cpu_baseline"], parity = cpu_baseline(name, sc, start, K, gpu_check=gpu_check)
+        if parity is not None:
+            line["parity"] = parity
+    g.close()
+    if name == "trees" and world == 1 and not args.no_extras:
+        extra = {}
+        extra["scenes_alone_plain_path"] = alone_plain(P, torch, sc, dev, stream, K)
+        pile = make_workload("pile")
+        ps = DEFAULT_START["pile"]
+        extra["pile_4096_landed"] = side_line("pile", pile, measure(P, torch, pile, "pile", ps, K, W, dev, stream,
+                                                                     flush=flush, e2e=False), ps, K)
+        del pile
+        qd = make_workload("quadruped")
+        qs = DEFAULT_START["quadruped"]
+        extra["quadruped_bed_rod"] = side_line("quadruped", qd, measure(P, torch, qd, "quadruped", qs, min(K, 10),
+                                                                         W, dev, stream, flush=flush, plain=False,
+                                                                         e2e=False), qs, min(K, 10))
+        del qd
+        del flush
+        torch.cuda.empty_cache()
+        extra["served"] = {"config": "Poisson step requests (1-60 steps each) over at most 64 stacked-pile scenes of "
+                                     f"10-1e5 bodies, {args.served_duration:.0f} s of arrivals per rate, HBM budget "
+                                     "32 GB, one stream per resident scene",
+                           "rates": served(P, torch, dev, [300.0, 3000.0], args.served_duration)}
+        line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def run_served(args, dev):
+    import torch
+    import paper_2609_02675_gb300 as P
+    torch.cuda.set_device(dev)
+    rates = [float(x) for x in args.rates.split(",")]
     line = {"metric": "served step latency", "unit": "ms", "higher_is_better": False, "n_gpus": 1,
             "data": "synthetic", "dtype": "f32",
             "config": {"workload": f"Poisson step requests (1-60 steps) over at most 64 pile scenes of 10-1e5 "
                                    f"bodies, {args.duration:.0f} s of arrivals per rate (then up to 20 s to drain), "
                                    f"HBM budget 32 GB",
                        "parallelism": "one scene per stream, continuous batching"},
-            "rates": out}
+            "rates": served(P, torch, dev, rates, args.duration)}
     print(json.dumps(line), flush=True)
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="pile",
-                    choices=["pile", "trees", "quadruped", "served", "stack", "spring", "net"])
+    ap.add_argument("--no-extras", action="store_true", help="headline workload only")
+    ap.add_argument("--workload", default="trees",
+                    choices=["trees", "pile", "quadruped", "served", "stack", "spring", "net"])
     ap.add_argument("--resid-tol", type=float, default=0.0,
                     help="residual threshold of the sweeps (0: a fixed n_iter sweeps per step)")
     ap.add_argument("--rates", default="100,300,1000,3000,10000", help="served: request rates (req/s)")
     ap.add_argument("--duration", type=float, default=3.0, help="served: seconds of arrivals per rate")
+    ap.add_argument("--served-duration", type=float, default=2.0,
+                    help="seconds of arrivals per rate of the served entry of the headline line")
     ap.add_argument("--bodies", type=int, default=4096, help="pile size (4096 = the 16^3 pile)")
     ap.add_argument("--stacked", action="store_true", help="pile as touching columns (contacts from step 0)")
-    ap.add_argument("--start-step", type=int, default=0, help="untimed lead-in steps before the timed window")
+    ap.add_argument("--start-step", type=int, default=-1,
+                    help="first step of the timed window (untimed lead-in before it); -1: the workload's default")
     ap.add_argument("--sweep-mode", type=int, default=0,
                     help="1: two launches per sweep, 2: one launch per sweep, 3: fused persistent, 0: library choice")
     ap.add_argument("--lanes", type=int, default=0, help="lanes per body in the fused sweep (0: library default)")
     args = ap.parse_args()
-    global ARGS
-    ARGS = args
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
+        import oracle
+        oracle.build()
         run_reference(args, rank, world)
         return
+    import __graft_entry__
+    __graft_entry__.build()
     if args.workload == "served":
         if rank == 0:
             run_served(args, local_rank)
@@ -533,6 +699,4 @@ def main():
 
 
 if __name__ == "__main__":
-    import __graft_entry__
-    __graft_entry__.build()
     main()

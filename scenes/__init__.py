@@ -532,3 +532,29 @@ def request_stream(seed: int = SEED_BASE + 5, rate=1000.0, duration=1.0, p_new=0
             sid = int(rng.integers(0, len(sizes)))
         reqs.append((t, sid, int(rng.integers(1, steps_max + 1))))
     return reqs, sizes
+
+
+def group_rows(sc: Scene, groups) -> np.ndarray:
+    """Body indices of the given groups (independent scenes of a batch), in body order."""
+    g = np.asarray(sc.bodies["group"])
+    return np.nonzero(np.isin(g, np.asarray(groups)))[0]
+
+
+def select_groups(sc: Scene, groups) -> Scene:
+    """The sub-batch made of the given groups (ascending), renumbered 0..len-1, with their
+    bonds; bodies keep their order.  Groups interact only through their own bonds, so the
+    sub-batch steps exactly as those groups do inside the full batch."""
+    groups = np.unique(np.asarray(groups))
+    rows = group_rows(sc, groups)
+    new_id = np.full(sc.n_bodies, -1, dtype=np.int64)
+    new_id[rows] = np.arange(rows.size)
+    b = sc.bodies[rows].copy()
+    b["group"] = np.searchsorted(groups, b["group"])
+    keep = new_id[sc.bonds["i"]] >= 0
+    bo = sc.bonds[keep].copy()
+    bo["i"] = new_id[bo["i"]]
+    bo["j"] = np.where(bo["j"] >= 0, new_id[np.maximum(bo["j"], 0)], -1)
+    meta = dict(sc.meta, groups=groups)
+    if "sizes" in sc.meta:
+        meta["sizes"] = np.asarray(sc.meta["sizes"])[groups]
+    return Scene(sc.name + "_subset", dict(sc.params), b, bo, sc.n_steps, meta)
