@@ -173,7 +173,7 @@ def tol_cfg(resid_tol: float) -> dict:
 def _kernel_hash():
     """Hash of the sources of the sweep kernels (their arithmetic and memory accesses)."""
     h = hashlib.sha256()
-    for f in ("k_sweep.cu", "k_persist.cu", "sweep_math.cuh", "dfloat.cuh"):
+    for f in ("k_sweep.cu", "k_sweep_one.cu", "k_persist.cu", "sweep_math.cuh", "dfloat.cuh"):
         p = os.path.join(ROOT, "paper_2609_02675_gb300", "csrc", f)
         if os.path.exists(p):
             with open(p, "rb") as fh:
@@ -371,6 +371,8 @@ def measure(P, torch, sc, name, start, K, W, dev, stream, world=1, flush=None, s
     if start:
         g.step(start)
         g.sync()
+    if sweep_mode == 0:
+        g.tune()  # the sweep autotuner on the window's first state (results do not depend on it)
     st0 = g.state()
 
     def reset():
@@ -579,7 +581,9 @@ def run_ours(args, rank, world, local_rank):
     cfg = {"workload": describe(name, sc, start, K, args.stacked), "n_bodies": sc.n_bodies,
            "n_iter": sc.params["n_iter"], "start_step": start, "l2": L2_NOTE, "parallelism": "replicas",
            **tol_cfg(args.resid_tol)}
-    cfg["sweep"] = {k: info1[k] for k in ("sweep_mode", "sweep_lanes", "sweep_block", "sweep_grid")}
+    cfg["sweep"] = {k: info1[k] for k in ("sweep_mode", "sweep_lanes", "light_order", "tuned")}
+    cfg["sweep"]["tune_sweep_us"] = {n: info1[f"tune_sweep_ns{k}"] / 1e3 for k, n in enumerate(
+        ("one_launch_ordered", "one_launch_body_order", "two_launch_ordered", "two_launch_body_order"))}
     if m["mean_sweeps"] is not None:
         cfg["mean_sweeps_per_step"] = m["mean_sweeps"]
     line = {

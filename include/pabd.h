@@ -104,8 +104,11 @@ typedef struct {
                                  Other values: PABD_ERR_ARG. */
     int sweep_mode;           /* 1: a bond launch + a solve launch per sweep; 2: one launch per
                                  sweep (the solve evaluates its bonds); 3: one cooperative launch
-                                 runs all n_iter sweeps; 0: the library's choice (2).  All modes
-                                 give the same results for the same sweep_lanes */
+                                 runs all n_iter sweeps; 0: the library's choice -- an autotuner
+                                 times modes 1 and 2, each with the light bodies ordered by end
+                                 count or not, on the state at creation (pabd_tune repeats it on
+                                 a later state) and keeps the fastest.  All modes and orders give
+                                 the same results for the same sweep_lanes */
     int sweep_lanes;          /* lanes per body in the per-body solve: 1, 2, 4, 8 or 16; 0 = from
                                  the scene: the largest of 16, 8, 4, 2, 1 with lanes * N <= 2^17,
                                  but 2 instead of 1 when N <= 2^18 and fewer than half the bodies
@@ -128,6 +131,11 @@ typedef struct {
                                  grid levels with caps 1, 4 and 16 times it, and wider boxes tested
                                  against all bodies); 1: linear BVH over the boxes' Morton codes
                                  (Sec. 5).  Both give the same pair list. */
+    int light_order;          /* bodies with at most 64 bond ends, in each sweep: 1 ordered every
+                                 step by (extended path or not, end count), so a warp's lanes walk
+                                 slices of one length down one path; 2 in body order; 0 the
+                                 library's choice (timed with sweep_mode 0, else ordered).  Other
+                                 values: PABD_ERR_ARG.  Results do not depend on it. */
     void* stream;             /* cudaStream_t on which all work is enqueued (NULL: default) */
     /* optional device allocator (e.g. a framework's caching allocator); NULL: cudaMalloc */
     void* (*alloc)(size_t bytes, void* ctx);
@@ -182,6 +190,13 @@ typedef struct {
     int64_t last_sweeps;      /* sweeps the last step ran (n_iter unless resid_tol ended it) */
     int64_t offgrid_bodies;   /* bodies the last step's grid broad phase took off the grid
                                  (flagged large, or a box wider than the cell cap) */
+    int64_t light_order;      /* 1: each sweep takes the light bodies ordered by (path, end
+                                 count), rebuilt every step; 0: in body order */
+    int64_t tuned;            /* 1 if sweep_mode and light_order were chosen by timing (sweep_mode
+                                 0 in the descriptor, no resid_tol, no AL_DISTANCE bonds) */
+    int64_t tune_sweep_ns[4]; /* the autotuner's mean sweep time per candidate, nanoseconds: one
+                                 launch per sweep ordered / in body order, a bond and a solve
+                                 launch per sweep ordered / in body order (0: not tuned) */
 } pabd_info;
 
 /* Create an empty scene on the current CUDA device.  *out receives the handle. */
@@ -206,6 +221,30 @@ pabd_status pabd_step(pabd_scene* s, int nsteps);
 
 /* Same work launched kernel by kernel without the CUDA graph (the plain path). */
 pabd_status pabd_step_eager(pabd_scene* s, int nsteps);
+
+/* Re-run the sweep autotuner of a scene created with sweep_mode 0 on its current state (for
+ * instance once a pile has landed, when its contacts are in place) and re-capture its step
+ * graph if the choice changed.  Synchronises the scene's stream.  The trial sweeps change no
+ * state; the pair and contact lists afterwards are those of the current state.  Returns
+ * PABD_OK without tuning for scenes whose shape is fixed (sweep_mode 1-3, resid_tol > 0,
+ * AL_DISTANCE bonds); a latched device error is returned first. */
+pabd_status pabd_tune(pabd_scene* s);
+
+/* Batched form of pabd_step over n scenes: scene k advances nsteps[k] steps (0 allowed).
+ * Every scene enqueues on its own stream, so their steps overlap on the device.  The call
+ * checks every handle and count first (PABD_ERR_ARG, nothing enqueued); after that the first
+ * scene whose pabd_step fails stops the loop and its status is returned (the scenes before it
+ * have been enqueued).  Independent scenes that share one launch per sweep are the groups of
+ * one scene (pabd_body_desc.group); this call serves scenes that must stay separate (their
+ * own streams, capacities or parameters). */
+pabd_status pabd_step_many(pabd_scene* const* scenes, int n, const int* nsteps);
+
+/* Bound of the device-side waits of the scene (the grid barrier between the sweeps of the
+ * fused persistent sweep, sweep_mode 3): a wait gives up after `polls` polls (default 2^24,
+ * about a second), latches PABD_ERR_TIMEOUT and ends its kernel, which the next
+ * synchronising call returns; the scene's later steps are not trustworthy.  Tests shorten the
+ * bound to check that a wait that runs out is reported.  polls == 0 is PABD_ERR_ARG. */
+pabd_status pabd_set_wait_limit(pabd_scene* s, uint32_t polls);
 
 /* Stage timing.  With profiling on, pabd_step launches a second captured graph that also
  * records CUDA events at the stage boundaries, waits for each step and accumulates the
@@ -260,29 +299,33 @@ pabd_status pabd_get_info(pabd_scene* s, pabd_info* info);
 /* Release all device memory of the scene (synchronises its stream). */
 pabd_status pabd_destroy_scene(pabd_scene* s);
 
-/* Broad phase for callers that cannot allocate device memory.  Some callers must not
- * call cudaMalloc: code running while a CUDA graph is being captured on its stream (an
- * allocation there is illegal), real-time loops with a fixed memory budget, and hosts whose
- * device memory is handed out by someone else.  This call allocates nothing: its scratch
- * (hash buckets, per-body counts and offsets, the scan's block sums) is a static device
- * array inside the library, sized for PABD_NOALLOC_MAX_BODIES bodies and held by every
- * GPU that loads the library until the process exits.  The paper has no counterpart of
- * this entry point; it returns the same sorted pair list as pabd_detect / pabd_read_pairs
- * for a scene with these bodies and no user bonds.
+/* Broad phase for callers that cannot allocate device memory.  Some callers must not call
+ * cudaMalloc or cudaFree: real-time loops that may not block on the allocator (both calls can
+ * synchronise the device), applications whose device memory is owned and handed out by
+ * another runtime or memory pool, and plug-ins embedded in a host program that holds the
+ * GPU's memory budget.  This call allocates nothing: its scratch (hash buckets, per-body
+ * counts and offsets, the scan's block sums) is a static device array inside the library,
+ * sized for PABD_NOALLOC_MAX_BODIES bodies (about 1.5 MB) and held by every GPU that loads
+ * the library until the process exits.  The paper has no counterpart of this entry point; it
+ * returns the same sorted pair list as pabd_detect / pabd_read_pairs for a scene with these
+ * bodies and no user bonds.
  *
  * Inputs (device pointers, n_bodies rows each): q 12 floats per body (c, then A row-major),
  * vel 4 floats per body (v, unused), he 4 floats per body (half extents, unused), group and
  * flags one int32 per body (flags bit 0 = pinned; no other bit may be set).  h, margin and
- * d_hat_rel are the scene parameters of pabd_scene_desc.  Outputs (device): pairs_out
- * receives up to max_pairs (i, j) int32 pairs, i < j, sorted; *n_pairs_out the number of
- * overlapping pairs found (more than max_pairs means the list was cut).
+ * d_hat_rel are the scene parameters of pabd_scene_desc.  Outputs (device): *n_pairs_out the
+ * number of overlapping pairs found; pairs_out receives min(found, max_pairs) (i, j) int32
+ * pairs, i < j, sorted.  When more than max_pairs are found the list is cut: the pairs written
+ * are max_pairs of the found ones, sorted, but not necessarily the first max_pairs of the
+ * full sorted list.
  * Asynchronous on `stream` (NULL: the legacy default stream).  Returns PABD_ERR_ARG for
- * null pointers, n_bodies < 0 or n_bodies > PABD_NOALLOC_MAX_BODIES.  The first call on a
- * device looks up the device address of the static array (with that device current) and so
- * should happen before any stream capture; later calls only enqueue memsets and kernels.
- * Every call reuses the same array and keeps nothing from the previous call: it clears the
- * buckets and counters it needs first.  Calls that overlap on the GPU (on different streams,
- * or from several threads) race on that array and must be serialised by the caller. */
+ * null pointers, n_bodies < 0 or n_bodies > PABD_NOALLOC_MAX_BODIES.  The first call in a
+ * CUDA context looks up the device address of the static array (with that context's device
+ * current) and should come before any stream capture; later calls in the same context only
+ * enqueue memsets and kernels.  Every call reuses the same array and keeps nothing from the
+ * previous call: it clears the buckets and counters it needs first.  Calls that overlap on the
+ * GPU (on different streams, or from several threads) race on that array and must be
+ * serialised by the caller. */
 #define PABD_NOALLOC_MAX_BODIES 16384
 pabd_status pabd_broadphase_noalloc(const float* q, const float* vel, const float* he, const int32_t* group,
                                     const int32_t* flags, int32_t n_bodies, double h, double margin,

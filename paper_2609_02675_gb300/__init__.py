@@ -42,7 +42,7 @@ class pabd_scene_desc(ctypes.Structure):
         ("margin", ctypes.c_double), ("project", ctypes.c_int), ("body_contacts", ctypes.c_int),
         ("large_he", ctypes.c_double), ("precision_policy", ctypes.c_int),
         ("sweep_mode", ctypes.c_int), ("sweep_lanes", ctypes.c_int), ("max_pairs", ctypes.c_size_t), ("max_contacts", ctypes.c_size_t),
-        ("resid_tol", ctypes.c_double), ("broadphase", ctypes.c_int),
+        ("resid_tol", ctypes.c_double), ("broadphase", ctypes.c_int), ("light_order", ctypes.c_int),
         ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
     ]
 
@@ -69,7 +69,8 @@ class pabd_info(ctypes.Structure):
         "n_bodies", "n_groups", "n_static_bonds", "n_bonds", "n_pairs", "n_contacts", "step_index",
         "max_pairs", "max_contacts", "graph_nodes", "launches", "fp64_bodies", "device_bytes",
         "sweep_mode", "sweep_lanes", "sweep_block", "sweep_grid", "coop_fallbacks", "heavy_bodies",
-        "fp64_dynamic", "last_sweeps", "offgrid_bodies")]
+        "fp64_dynamic", "last_sweeps", "offgrid_bodies", "light_order", "tuned",
+        "tune_sweep_ns0", "tune_sweep_ns1", "tune_sweep_ns2", "tune_sweep_ns3")]
 
 
 _P = ctypes.c_void_p
@@ -87,6 +88,9 @@ _SIGS = {
     "pabd_add_bonds": [_P, _P, ctypes.c_size_t, _PSZ],
     "pabd_step": [_P, ctypes.c_int],
     "pabd_step_eager": [_P, ctypes.c_int],
+    "pabd_step_many": [_P, ctypes.c_int, _PI32],
+    "pabd_set_wait_limit": [_P, ctypes.c_uint32],
+    "pabd_tune": [_P],
     "pabd_detect": [_P],
     "pabd_sync": [_P],
     "pabd_read_state": [_P, _PD, ctypes.c_size_t],
@@ -183,6 +187,22 @@ def pabd_step(s, nsteps: int = 1):
 
 def pabd_step_eager(s, nsteps: int = 1):
     return _check(_lib.pabd_step_eager(s, nsteps), "pabd_step_eager")
+
+
+def pabd_step_many(scenes, nsteps):
+    """Scene k of `scenes` (handles) advances nsteps[k] steps on its own stream."""
+    n = len(scenes)
+    arr = (_P * max(n, 1))(*scenes)
+    cnt = np.ascontiguousarray(nsteps, dtype=np.int32)
+    return _check(_lib.pabd_step_many(ctypes.cast(arr, _P), n, cnt.ctypes.data_as(_PI32)), "pabd_step_many")
+
+
+def pabd_tune(s):
+    return _check(_lib.pabd_tune(s), "pabd_tune")
+
+
+def pabd_set_wait_limit(s, polls: int):
+    return _check(_lib.pabd_set_wait_limit(s, polls), "pabd_set_wait_limit")
 
 
 def pabd_detect(s):
@@ -307,7 +327,8 @@ class _TorchAllocator:
 
 
 def scene_desc(params: dict, stream=0, allocator: _TorchAllocator | None = None, precision_policy=1,
-               max_pairs=0, max_contacts=0, sweep_mode=0, sweep_lanes=0, broadphase=0) -> pabd_scene_desc:
+               max_pairs=0, max_contacts=0, sweep_mode=0, sweep_lanes=0, broadphase=0,
+               light_order=0) -> pabd_scene_desc:
     d = pabd_scene_desc()
     d.h = params["h"]
     d.gravity = D3(*params["gravity"])
@@ -329,6 +350,7 @@ def scene_desc(params: dict, stream=0, allocator: _TorchAllocator | None = None,
     d.max_contacts = int(max_contacts)
     d.resid_tol = float(params.get("resid_tol", 0.0))
     d.broadphase = int(broadphase)
+    d.light_order = int(light_order)
     d.stream = stream or None
     if allocator is not None:
         d.alloc = allocator.alloc_cb
@@ -344,7 +366,7 @@ class Scene:
 
     def __init__(self, scene, device: int = 0, stream=None, torch_memory: bool = True, precision_policy: int = 1,
                  max_pairs: int = 0, max_contacts: int = 0, sweep_mode: int = 0, sweep_lanes: int = 0,
-                 broadphase: int = 0):
+                 broadphase: int = 0, light_order: int = 0):
         import torch
         torch.cuda.set_device(device)
         if stream is None:
@@ -352,7 +374,7 @@ class Scene:
         self.torch_stream = stream
         self._alloc = _TorchAllocator(device, stream.cuda_stream) if torch_memory else None
         self.desc = scene_desc(scene.params, stream.cuda_stream, self._alloc, precision_policy, max_pairs,
-                               max_contacts, sweep_mode, sweep_lanes, broadphase)
+                               max_contacts, sweep_mode, sweep_lanes, broadphase, light_order)
         self.h = pabd_create_scene(self.desc)
         self.n = scene.n_bodies
         self.n_groups = scene.n_groups
@@ -391,6 +413,13 @@ class Scene:
 
     def step_eager(self, n: int = 1):
         pabd_step_eager(self.h, n)
+
+    def set_wait_limit(self, polls: int):
+        pabd_set_wait_limit(self.h, polls)
+
+    def tune(self):
+        """Re-run the sweep autotuner on the current state (see pabd_tune)."""
+        pabd_tune(self.h)
 
     def detect(self):
         pabd_detect(self.h)

@@ -209,6 +209,85 @@ __global__ void __launch_bounds__(LONG_T) k_csr_sort_long(Dev d) {
     }
 }
 
+// ---- light bodies ordered by (class, end count) ----
+
+constexpr int BIN_T = 256;
+
+// bin of body b in the light order, or -1 for a body on the heavy list: the bodies on the
+// extended path (statically flagged) in bins 0..HEAVY_ENDS by end count, the others after them
+__device__ __forceinline__ int light_bin(const Dev& d, int b) {
+    const int fl = d.bflags[b];
+    const int n = d.end_off[b + 1] - d.end_off[b];
+    if (fl & BF_PINNED) return END_BINS;
+    if (n > HEAVY_ENDS) return -1;
+    const bool ext = d.p.precision_policy == 3 || (d.p.precision_policy && (fl & BF_FP64));
+    return (ext ? 0 : END_BINS) + n;
+}
+
+// bodies per bin: a block histogram in shared memory, one global atomic per bin and block
+__global__ void __launch_bounds__(BIN_T) k_bin_count(Dev d) {
+    pdl_enter();
+    __shared__ int h[2 * END_BINS];
+    for (int k = threadIdx.x; k < 2 * END_BINS; k += BIN_T) h[k] = 0;
+    __syncthreads();
+    const int b = blockIdx.x * BIN_T + threadIdx.x;
+    if (b < d.N) {
+        const int k = light_bin(d, b);
+        if (k >= 0) atomicAdd(&h[k], 1);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 2 * END_BINS; k += BIN_T)
+        if (h[k]) atomicAdd(&d.bin_cnt[k], h[k]);
+}
+
+// Each body's slot: the bin's start (prefix of the bin counts), plus the range this block
+// reserved inside the bin, plus the body's rank among the block's bodies of that bin (warps
+// in order, lanes in order: a block's bodies keep their body order inside its range).
+__global__ void __launch_bounds__(BIN_T) k_bin_scatter(Dev d) {
+    pdl_enter();
+    constexpr int NW = BIN_T / 32, NB = 2 * END_BINS;
+    static_assert(NB <= BIN_T, "one thread per bin");
+    __shared__ int cnt[NW][NB];
+    __shared__ int start[NB];
+    __shared__ int incl[NB];
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    for (int k = t; k < NW * NB; k += BIN_T) (&cnt[0][0])[k] = 0;
+    const int b = blockIdx.x * BIN_T + t;
+    const int key = b < d.N ? light_bin(d, b) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    const int gc = t < NB ? d.bin_cnt[t] : 0;
+    if (t < NB) incl[t] = gc;
+    __syncthreads();
+    if (key >= 0 && rank == 0) cnt[w][key] = __popc(peers);
+    // inclusive prefix of the bin counts (Hillis-Steele in shared memory)
+    for (int o = 1; o < NB; o <<= 1) {
+        const int v = (t < NB && t >= o) ? incl[t - o] : 0;
+        __syncthreads();
+        if (t < NB) incl[t] += v;
+        __syncthreads();
+    }
+    if (t < NB) {
+        int run = 0;
+        for (int k = 0; k < NW; ++k) {
+            const int c = cnt[k][t];
+            cnt[k][t] = run;
+            run += c;
+        }
+        start[t] = (incl[t] - gc) + (run ? atomicAdd(&d.bin_cur[t], run) : 0);
+    }
+    if (blockIdx.x == 0 && t == 0) d.ctr[C_NLIGHT] = incl[NB - 1];
+    __syncthreads();
+    if (key >= 0) d.order[start[key] + cnt[w][key] + rank] = b;
+}
+
+void launch_light_order(const Dev& d, cudaStream_t st, long long* launches) {
+    const int g = d.N > 0 ? (d.N + BIN_T - 1) / BIN_T : 1;
+    launch_pdl(k_bin_count, dim3(g), dim3(BIN_T), 0, st, d);
+    launch_pdl(k_bin_scatter, dim3(g), dim3(BIN_T), 0, st, d);
+    *launches += 2;
+}
+
 cudaError_t setup_csr_kernels() {
     return cudaFuncSetAttribute(k_csr_sort_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 LONG_SMEM * (int)sizeof(int));
@@ -264,6 +343,10 @@ __global__ void k_step_reset(Dev d) {
     if (d.p.broadphase == 0 && t < (1 << d.table_bits)) {
         d.bucket_cnt[t] = 0;
         d.bucket_cur[t] = 0;
+    }
+    if (t < 2 * END_BINS) {
+        d.bin_cnt[t] = 0;
+        d.bin_cur[t] = 0;
     }
     if (t < d.N) {
         d.end_cnt[t] = 0;

@@ -61,9 +61,12 @@ __global__ void __launch_bounds__(SOLVE_T, 4) k_solve(Dev d, const float4* __res
             });
         return;
     }
+    // the light bodies in this step's (class, end count) order, or in body order (a body on
+    // the heavy list then returns at once); either way the same arithmetic per body
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int b = tid / L, lane = tid & (L - 1);
-    if (b >= d.N) return;
+    const int slot = tid / L, lane = tid & (L - 1);
+    if (slot >= (d.light_sorted ? d.ctr[C_NLIGHT] : d.N)) return;
+    const int b = d.light_sorted ? d.order[slot] : slot;
     solve_body<L, X>(d, b, lane, lane_mask<L>(), qi, qo, last,
                      [&](auto& s, const float* c, const float* A, const float* xs, int e0, int e1) {
         for (int p = e0 + lane; p < e1; p += L) sys_add(s, d.ends[p], d.end_x[p], xs);
@@ -85,15 +88,15 @@ void launch_solve(const Dev& d, const float4* q_in, float4* q_out, int it, int l
     const bool f64 = d.p.precision_policy == 2;
     switch (lanes) {
         case 1: f64 ? k_solve<1, double><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light)
-                    : k_solve<1, df><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light); break;
+                    : k_solve<1, ca><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light); break;
         case 2: f64 ? k_solve<2, double><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light)
-                    : k_solve<2, df><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light); break;
+                    : k_solve<2, ca><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light); break;
         case 4: f64 ? k_solve<4, double><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light)
-                    : k_solve<4, df><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light); break;
+                    : k_solve<4, ca><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light); break;
         case 8: f64 ? k_solve<8, double><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light)
-                    : k_solve<8, df><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light); break;
+                    : k_solve<8, ca><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light); break;
         default: f64 ? k_solve<16, double><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light)
-                     : k_solve<16, df><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light); break;
+                     : k_solve<16, ca><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light); break;
     }
     *launches += 1;
 }

@@ -1,6 +1,8 @@
 // Allocation-free broad phase (pabd_broadphase_noalloc): the same kernels as a scene's
 // broad phase, run on caller-provided inputs and outputs with their scratch in a static
 // device array of fixed size instead of memory allocated at scene creation.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "../../include/pabd.h"
@@ -28,9 +30,44 @@ constexpr size_t OFF_SCAN = OFF_CTR + al(sizeof(int) * C_COUNT);
 constexpr size_t SCAN_INTS = NA_TABLE / 4096 + 2;  // block totals of the largest scan
 constexpr size_t NA_BYTES = OFF_SCAN + al(sizeof(int) * SCAN_INTS);
 
-constexpr int MAX_DEVICES = 64;
+// Device addresses of the static array, one per CUDA context that has called: the address
+// belongs to the context that looked it up (a device reset or another context on the same
+// device makes it stale), so the cache is keyed by the current context's unique id.
+struct AddrEntry {
+    int dev;
+    unsigned long long ctx;
+    unsigned char* addr;
+};
+constexpr int MAX_ENTRIES = 64;
 std::mutex g_mu;
-unsigned char* g_addr[MAX_DEVICES] = {nullptr};
+AddrEntry g_addr[MAX_ENTRIES];
+int g_n_addr = 0;
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// unique id of the current context (driver entry points looked up through the runtime, so
+// the library needs no link to the driver library)
+bool current_context_id(unsigned long long* id) {
+    static CtxGetCurrentFn get_cur = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!get_cur || !get_id) {
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || !f1)
+            return false;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q2 != cudaDriverEntryPointSuccess || !f2)
+            return false;
+        get_cur = reinterpret_cast<CtxGetCurrentFn>(f1);
+        get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+    CUcontext ctx = nullptr;
+    if (get_cur(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return get_id(ctx, id) == CUDA_SUCCESS;
+}
 
 }  // namespace
 
@@ -45,17 +82,22 @@ extern "C" pabd_status pabd_broadphase_noalloc(const float* q, const float* vel,
     if (n_bodies > 0 && (!q || !vel || !he || !group || !flags)) return PABD_ERR_ARG;
     if (!n_pairs_out || (max_pairs > 0 && !pairs_out)) return PABD_ERR_ARG;
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return PABD_ERR_CUDA;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return PABD_ERR_CUDA;
     unsigned char* base = nullptr;
     {
-        // once per device, with that device current: the device address of the static array
+        // once per device and context, with that device current: the device address of the
+        // static array
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_addr[dev]) {
+        unsigned long long ctx = 0;
+        const bool have_ctx = current_context_id(&ctx);  // false before the runtime made one current
+        for (int k = 0; have_ctx && k < g_n_addr && !base; ++k)
+            if (g_addr[k].dev == dev && g_addr[k].ctx == ctx) base = g_addr[k].addr;
+        if (!base) {
             void* ptr = nullptr;
             if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return PABD_ERR_CUDA;
-            g_addr[dev] = static_cast<unsigned char*>(ptr);
+            base = static_cast<unsigned char*>(ptr);
+            if ((have_ctx || current_context_id(&ctx)) && g_n_addr < MAX_ENTRIES) g_addr[g_n_addr++] = AddrEntry{dev, ctx, base};
         }
-        base = g_addr[dev];
     }
     cudaStream_t st = (cudaStream_t)stream;
     Dev d{};

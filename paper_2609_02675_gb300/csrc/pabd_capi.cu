@@ -164,11 +164,18 @@ struct pabd_scene {
     double prof_acc[PABD_PROFILE_SLOTS] = {0};
     // fused sweep launch shape
     int fused = 0, mode = 1, lanes = 8, sw_block = 128, sw_grid = 1;
+    // the default path's autotuner: whether it chose the mode and light order, and the mean
+    // sweep time it measured for each candidate (mode 2 ordered, mode 2 in body order, mode 1
+    // ordered, mode 1 in body order), nanoseconds
+    int tuned = 0;
+    long long tune_ns[4] = {0, 0, 0, 0};
     long long coop_fallbacks = 0;
     // augmented Lagrangian bonds: (kappa_start, 0) per static bond, the state before the first step
     std::vector<float2> al_init;
     // stream on which the body of the residual-threshold loop is captured into its graph node
     cudaStream_t body_st = nullptr;
+    // polls before a device-side wait gives up (PABD_ERR_TIMEOUT); about a second by default
+    unsigned wait_polls = 1u << 24;
 
     void* dalloc(size_t n) {
         if (n == 0) n = 16;
@@ -213,6 +220,7 @@ void enqueue_step(pabd_scene* s, long long* launches, const cudaEvent_t* ev = nu
     launch_collision(d, s->st, launches);
     mark();
     launch_csr(d, s->st, launches);
+    if (d.light_sorted) launch_light_order(d, s->st, launches);
     mark();
     launch_predict(d, s->st, launches);
     launch_al_warm(d, s->st, launches);
@@ -348,6 +356,93 @@ pabd_status autotune_sweep(pabd_scene* s) {
     int nb0 = d.Nc;
     CK(cudaMemcpyAsync(d.ctr + C_NBONDS, &nb0, sizeof(int), cudaMemcpyHostToDevice, s->st));
     CK(cudaStreamSynchronize(s->st));
+    return PABD_OK;
+}
+
+// The default path's autotuner (sweep_mode 0).  With the current state's collision, CSR,
+// light order, predictor and end records in place (none of them changes the scene's state),
+// time the n_iter sweeps of each candidate launch shape: one launch per sweep or a bond and a
+// solve launch per sweep, each with the light bodies in (class, end count) order or in body
+// order.  Every candidate gives the same results bit for bit (each body's arithmetic depends
+// on its end count and the lane count only), so the fastest is kept.  Scenes with augmented
+// Lagrangian bonds, whose sweeps update the bonds' state, keep one launch per sweep, ordered.
+pabd_status autotune_default(pabd_scene* s) {
+    Dev& d = s->d;
+    const bool tune_mode = s->desc.sweep_mode == 0, tune_order = s->desc.light_order == 0;
+    if (tune_mode) s->mode = 2;
+    if (tune_order) d.light_sorted = 1;
+    if (d.N == 0 || d.Nal > 0 || (!tune_mode && !tune_order)) return PABD_OK;
+    long long lc = 0;
+    Dev dd = d;
+    launch_step_reset(dd, s->st, &lc);
+    launch_drive_update(dd, s->st, &lc);
+    launch_collision(dd, s->st, &lc);
+    launch_csr(dd, s->st, &lc);
+    launch_light_order(dd, s->st, &lc);
+    launch_predict(dd, s->st, &lc);
+    launch_end_records(dd, s->st, &lc);
+    CK(cudaGetLastError());
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int n_it = d.p.n_iter;
+    float best = 1e30f;
+    for (int c = 0; c < 4; ++c) {
+        const int mode = c < 2 ? 2 : 1;
+        dd.light_sorted = (c & 1) ? 0 : 1;
+        if ((!tune_mode && mode != s->mode) || (!tune_order && dd.light_sorted != d.light_sorted)) continue;
+        float tot = 0.f;
+        for (int r = 0; r < 3; ++r) {
+            CK(cudaEventRecord(e0, s->st));
+            float4* cur = dd.qa;
+            float4* nxt = dd.qb;
+            for (int it = 0; it < n_it; ++it) {
+                if (mode == 2) {
+                    launch_sweep_one(dd, cur, nxt, it, s->lanes, s->st, &lc, true);
+                } else {
+                    launch_bond(dd, cur, it, s->st, &lc);
+                    launch_solve(dd, cur, nxt, it, s->lanes, s->st, &lc);
+                }
+                float4* t = cur; cur = nxt; nxt = t;
+            }
+            CK(cudaEventRecord(e1, s->st));
+            CK(cudaEventSynchronize(e1));
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, e0, e1));
+            if (r > 0) tot += t;  // the first pass warms the caches
+        }
+        CK(cudaGetLastError());
+        s->tune_ns[c] = (long long)(1e6 * tot / (2.0 * n_it));
+        if (tot < best) { best = tot; s->mode = mode; d.light_sorted = dd.light_sorted; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    s->tuned = 1;
+    return PABD_OK;
+}
+
+// Capture one step as the scene's graph (if the cooperative sweep cannot be captured, capture
+// the two-launch sweep instead).
+pabd_status capture_step(pabd_scene* s) {
+    cudaStream_t st = s->st;
+    long long lc = 0;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        lc = 0;
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        enqueue_step(s, &lc);
+        cudaError_t ce = cudaStreamEndCapture(st, &s->graph);
+        if (ce == cudaSuccess) ce = cudaGraphInstantiate(&s->exec, s->graph, 0);
+        if (ce == cudaSuccess) break;
+        cudaGetLastError();
+        if (s->graph) { cudaGraphDestroy(s->graph); s->graph = nullptr; }
+        if (!s->fused || attempt == 1) { cuda_ok(ce, "capture of the step graph"); return PABD_ERR_CUDA; }
+        s->fused = 0;
+        s->mode = 1;
+        s->d.light_sorted = 0;
+        s->coop_fallbacks = 0;
+    }
+    CK(cudaGraphGetNodes(s->graph, nullptr, &s->graph_nodes));
+    s->launches_per_step = lc;
     return PABD_OK;
 }
 
@@ -566,9 +661,10 @@ pabd_status finalize_scene(pabd_scene* s) {
     ok &= alloc_arr(s, d.drv, 3 * d.Ndrive) && alloc_arr(s, d.drv_t, d.Ndrive) && alloc_arr(s, d.drv_bond, d.Ndrive);
     ok &= alloc_arr(s, d.end_cnt, N) && alloc_arr(s, d.end_cur, N) && alloc_arr(s, d.end_off, N + 1);
     ok &= alloc_arr(s, d.end_id, d.cap_ends) && alloc_arr(s, d.end_pos, d.cap_ends) && alloc_arr(s, d.heavy, N);
+    ok &= alloc_arr(s, d.order, N) && alloc_arr(s, d.bin_cnt, 2 * END_BINS) && alloc_arr(s, d.bin_cur, 2 * END_BINS);
     ok &= alloc_arr(s, d.ends, d.cap_ends) && alloc_arr(s, d.end_x, d.cap_ends);
     ok &= alloc_arr(s, d.rec_m, d.cap_ends) && alloc_arr(s, d.rec_a, d.cap_ends) && alloc_arr(s, d.rec_b, d.cap_ends);
-    ok &= alloc_arr(s, d.gbar, 2);
+    ok &= alloc_arr(s, d.gbar, 2) && alloc_arr(s, d.wait_limit, 1);
     ok &= alloc_arr(s, d.lo, N) && alloc_arr(s, d.hi, N) && alloc_arr(s, d.cell, N);
     ok &= alloc_arr(s, d.bucket_cnt, T) && alloc_arr(s, d.bucket_cur, T) && alloc_arr(s, d.bucket_off, T + 1) &&
           alloc_arr(s, d.bucket_items, N);
@@ -634,6 +730,8 @@ pabd_status finalize_scene(pabd_scene* s) {
     CK(cudaMemsetAsync(d.resid_group, 0, sizeof(double) * (d.G ? d.G : 1), st));
     CK(cudaMemsetAsync(d.end_pos, 0xff, sizeof(int) * d.cap_ends, st));
     CK(cudaMemsetAsync(d.gbar, 0, 2 * sizeof(unsigned), st));
+    const unsigned wait_polls = s->wait_polls;
+    CK(cudaMemcpyAsync(d.wait_limit, &wait_polls, sizeof(unsigned), cudaMemcpyHostToDevice, st));
     // bonds beyond Nc start counted as zero until the first detection
     int nb0 = Nc;
     CK(cudaMemcpyAsync(d.ctr + C_NBONDS, &nb0, sizeof(int), cudaMemcpyHostToDevice, st));
@@ -661,6 +759,8 @@ pabd_status finalize_scene(pabd_scene* s) {
     // runs one launch per sweep.
     if (ds.sweep_mode < 0 || ds.sweep_mode > 3) return PABD_ERR_ARG;
     s->mode = ds.sweep_mode == 0 ? 2 : ds.sweep_mode;
+    if (ds.light_order < 0 || ds.light_order > 2) return PABD_ERR_ARG;
+    d.light_sorted = s->mode != 3 && ds.light_order != 2;
     if (p.resid_tol > 0) {
         if (d.Nal) return PABD_ERR_ARG;
         s->mode = 2;
@@ -677,6 +777,13 @@ pabd_status finalize_scene(pabd_scene* s) {
         s->lanes = L;
         pabd_status tr = autotune_sweep(s);
         if (tr != PABD_OK) return tr;
+    } else if ((ds.sweep_mode == 0 || ds.light_order == 0) && p.resid_tol <= 0) {
+        pabd_status tr = autotune_default(s);
+        if (tr != PABD_OK) return tr;
+        // leave the counters as a fresh scene has them
+        CK(cudaMemsetAsync(d.ctr, 0, sizeof(int) * C_COUNT, st));
+        CK(cudaMemcpyAsync(d.ctr + C_NBONDS, &nb0, sizeof(int), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
     }
     // the state the first step's warm start reads (the trial sweeps above may have written it)
     if (d.Nal) {
@@ -684,25 +791,8 @@ pabd_status finalize_scene(pabd_scene* s) {
         CK(cudaStreamSynchronize(st));
     }
 
-    // capture one step as a graph (if the cooperative sweep cannot be captured, capture the
-    // two-launch sweep instead)
-    long long lc = 0;
-    for (int attempt = 0; attempt < 2; ++attempt) {
-        lc = 0;
-        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        enqueue_step(s, &lc);
-        cudaError_t ce = cudaStreamEndCapture(st, &s->graph);
-        if (ce == cudaSuccess) ce = cudaGraphInstantiate(&s->exec, s->graph, 0);
-        if (ce == cudaSuccess) break;
-        cudaGetLastError();
-        if (s->graph) { cudaGraphDestroy(s->graph); s->graph = nullptr; }
-        if (!s->fused || attempt == 1) { cuda_ok(ce, "capture of the step graph"); return PABD_ERR_CUDA; }
-        s->fused = 0;
-        s->mode = 1;
-        s->coop_fallbacks = 0;
-    }
-    CK(cudaGraphGetNodes(s->graph, nullptr, &s->graph_nodes));
-    s->launches_per_step = lc;
+    pabd_status cr = capture_step(s);
+    if (cr != PABD_OK) return cr;
     CK(cudaMallocHost(&s->h_status, sizeof(int)));
     *s->h_status = 0;
     CK(cudaEventCreateWithFlags(&s->ev_status, cudaEventDisableTiming));
@@ -969,6 +1059,61 @@ pabd_status pabd_step(pabd_scene* s, int nsteps) {
     return enqueue_status(s);
 }
 
+pabd_status pabd_tune(pabd_scene* s) {
+    if (!s) return PABD_ERR_ARG;
+    pabd_status r = finalize_scene(s);
+    if (r != PABD_OK) return r;
+    if ((s->desc.sweep_mode != 0 && s->desc.light_order != 0) || s->d.p.resid_tol > 0 || s->fused) return PABD_OK;
+    r = poll_status(s, true);
+    if (r != PABD_OK) return r;
+    CK(cudaStreamSynchronize(s->st));
+    const int mode0 = s->mode, sorted0 = s->d.light_sorted;
+    r = autotune_default(s);
+    if (r != PABD_OK) return r;
+    CK(cudaStreamSynchronize(s->st));
+    if (s->mode == mode0 && s->d.light_sorted == sorted0) return PABD_OK;
+    // the step graphs were captured with the old shape: capture them again
+    cudaGraphExecDestroy(s->exec);
+    cudaGraphDestroy(s->graph);
+    s->exec = nullptr;
+    s->graph = nullptr;
+    r = capture_step(s);
+    if (r != PABD_OK) return r;
+    if (s->prof_exec) {
+        cudaGraphExecDestroy(s->prof_exec);
+        cudaGraphDestroy(s->prof_graph);
+        s->prof_exec = nullptr;
+        s->prof_graph = nullptr;
+        const bool on = s->profiling;
+        r = pabd_set_profiling(s, 1);
+        s->profiling = on;
+        if (r != PABD_OK) return r;
+    }
+    return PABD_OK;
+}
+
+pabd_status pabd_step_many(pabd_scene* const* scenes, int n, const int* nsteps) {
+    if (n < 0 || (n > 0 && (!scenes || !nsteps))) return PABD_ERR_ARG;
+    for (int k = 0; k < n; ++k)
+        if (!scenes[k] || nsteps[k] < 0) return PABD_ERR_ARG;
+    // every scene enqueues on its own stream, so the scenes' steps overlap on the device; the
+    // first error stops the loop (the scenes before it have been enqueued)
+    for (int k = 0; k < n; ++k) {
+        pabd_status r = pabd_step(scenes[k], nsteps[k]);
+        if (r != PABD_OK) return r;
+    }
+    return PABD_OK;
+}
+
+pabd_status pabd_set_wait_limit(pabd_scene* s, uint32_t polls) {
+    if (!s || polls == 0) return PABD_ERR_ARG;
+    s->wait_polls = polls;
+    if (!s->ready) return PABD_OK;  // written at finalisation
+    CK(cudaMemcpyAsync(s->d.wait_limit, &s->wait_polls, sizeof(unsigned), cudaMemcpyHostToDevice, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return PABD_OK;
+}
+
 pabd_status pabd_step_eager(pabd_scene* s, int nsteps) {
     if (!s || nsteps < 0) return PABD_ERR_ARG;
     pabd_status r = finalize_scene(s);
@@ -1187,6 +1332,9 @@ pabd_status pabd_get_info(pabd_scene* s, pabd_info* info) {
     info->heavy_bodies = c[C_NHEAVY];
     info->fp64_dynamic = c[C_FP64DYN];
     info->offgrid_bodies = c[C_NLARGE];
+    info->light_order = s->d.light_sorted;
+    info->tuned = s->tuned;
+    for (int k = 0; k < 4; ++k) info->tune_sweep_ns[k] = s->tune_ns[k];
     info->last_sweeps = s->d.p.n_iter;
     if (s->d.sweep_ctl) {
         int ctl[4] = {0, 0, 0, 0};

@@ -36,6 +36,7 @@ enum Counter {
     C_NPHEAVY,         // bodies with more than 64 partners this step (list in Dev::pair_heavy)
     C_CELLBITS1,       // float bits of the widest box of grid level 1 (multilevel grid)
     C_CELLBITS2,       // ... of grid level 2
+    C_NLIGHT,          // bodies on this step's light list (Dev::order)
     C_COUNT
 };
 
@@ -61,6 +62,11 @@ constexpr int HEAVY_T = 128;
 constexpr int WIDE_ENDS = 256;
 // blocks appended to each sweep launch for the heavy bodies (they loop over the heavy list)
 constexpr int HEAVY_BLOCKS = 152;
+// The light bodies (at most HEAVY_ENDS ends) are ordered every step by (class, end count):
+// the bodies on the extended path first, then the rest, each class by its number of ends, so
+// that the lanes of one warp walk slices of the same length down the same path.  2 * END_BINS
+// bins; which lanes take a body never changes its arithmetic.
+constexpr int END_BINS = HEAVY_ENDS + 1;
 
 struct Dev {
     Params p;
@@ -93,10 +99,14 @@ struct Dev {
     int *end_cnt, *end_cur, *end_off, *end_id, *end_pos;
     float4 *ends, *end_x;
     int *heavy;                 // ids of the bodies with more than HEAVY_ENDS ends (C_NHEAVY of them)
+    int light_sorted;           // 1: the sweeps take the light bodies in Dev::order; 0: in body order
+    int *order;                 // this step's light bodies by (class, end count), C_NLIGHT of them
+    int *bin_cnt, *bin_cur;     // per bin of the light order: bodies, and the blocks' reservations
     // bond-end records in CSR order for the fused sweep: (i, j, type, bond), x_i (+w0), x_j (+p1)
     int4 *rec_m;
     float4 *rec_a, *rec_b;
     unsigned *gbar;             // grid barrier: arrival counter, generation
+    unsigned *wait_limit;       // polls before a device-side wait gives up (PABD_ERR_TIMEOUT)
     // collision
     float4 *lo, *hi;            // inflated AABB; lo.w = inflation
     int4 *cell;                 // cell coords (.w = bucket)
@@ -184,6 +194,8 @@ cudaError_t setup_pair_sort();
 void launch_pair_sort(const Dev& d, cudaStream_t st, long long* launches);
 void launch_broadphase(const Dev& d, cudaStream_t st, long long* launches);
 void launch_csr(const Dev& d, cudaStream_t st, long long* launches);
+// the light bodies ordered by (class, end count) into Dev::order (after launch_csr)
+void launch_light_order(const Dev& d, cudaStream_t st, long long* launches);
 // opt the CSR block sort into its 128 KB of dynamic shared memory (once per process and device)
 cudaError_t setup_csr_kernels();
 void launch_predict(const Dev& d, cudaStream_t st, long long* launches);

@@ -2,6 +2,8 @@
 // k_persist.cu: the fused persistent sweep): bond split forces, the per-body 4x4 system
 // and the rotation of the local solve.  One copy, so both paths compute identical bonds.
 #pragma once
+#include <type_traits>
+
 #include "dfloat.cuh"
 #include "pabd_internal.h"
 
@@ -214,6 +216,59 @@ struct Sys {
     T r[4][3];
 };
 
+// Compensated accumulator of the extended path (precision policy 1): the float running sum s
+// and the float sum e of the rounding errors of every addition (TwoSum) and of every product
+// (TwoProd) that entered it -- Ogita, Rump and Oishi's Sum2 / Dot2 ("Accurate sum and dot
+// product", SIAM J. Sci. Comput. 2005).  s + e is the sum as accurate as if it had been
+// accumulated in twice the working precision and rounded, at about a third of the cost of
+// double-float additions; the total is turned into a double-float (ca_to_df) for the
+// factorisation.
+struct ca {
+    float s, e;
+    ca() = default;
+    __host__ __device__ constexpr ca(float v) : s(v), e(0.f) {}
+    __host__ __device__ constexpr ca(float a, float b) : s(a), e(b) {}
+};
+
+__device__ __forceinline__ void ca_add(ca& a, float x) {
+    const df t = two_sum(a.s, x);
+    a.s = t.hi;
+    a.e = __fadd_rn(a.e, t.lo);
+}
+// add hi + lo, where hi is the rounded value and lo a small correction (a product's error)
+__device__ __forceinline__ void ca_add(ca& a, float hi, float lo) {
+    const df t = two_sum(a.s, hi);
+    a.s = t.hi;
+    a.e = __fadd_rn(a.e, __fadd_rn(t.lo, lo));
+}
+__device__ __forceinline__ ca& operator+=(ca& a, ca b) {
+    const df t = two_sum(a.s, b.s);
+    a.s = t.hi;
+    a.e = __fadd_rn(__fadd_rn(a.e, b.e), t.lo);
+    return a;
+}
+__device__ __forceinline__ ca shfl_xor(unsigned mask, ca v, int o) {
+    return ca{__shfl_xor_sync(mask, v.s, o), __shfl_xor_sync(mask, v.e, o)};
+}
+__device__ __forceinline__ ca ca_of(df v) { return ca{v.hi, v.lo}; }
+__device__ __forceinline__ df ca_to_df(ca v) { return two_sum(v.s, v.e); }
+
+// the extended system as it is factored: double-float from the compensated sums, FP64 as
+// summed under policy 2
+__device__ __forceinline__ Sys<df> ext_sys(const Sys<ca>& s) {
+    Sys<df> t;
+#pragma unroll
+    for (int k = 0; k < 10; ++k) t.g[k] = ca_to_df(s.g[k]);
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) t.r[r][k] = ca_to_df(s.r[r][k]);
+    return t;
+}
+__device__ __forceinline__ const Sys<double>& ext_sys(const Sys<double>& s) { return s; }
+template <class X> struct ext_type { using T = X; };
+template <> struct ext_type<ca> { using T = df; };
+
 // The system is assembled about a per-body expansion point x_s (Dev::xs; zero for most
 // bodies): with z = x - x_s the unknowns are c' = c + A x_s and A, so G = diag(m, Pi) +
 // sum w [1; x][1; x]^T becomes, exactly, T^-1 G T^-T = [m, -m x_s^T; -m x_s, Pi + m x_s x_s^T]
@@ -236,6 +291,18 @@ __device__ __forceinline__ void sys_init(Sys<T>& s, float4 mass, const float* dc
 #pragma unroll
         for (int l = 0; l < 3; ++l) s.r[1 + l][k] = pm[1 + l] * (T)dA[3 * k + l] - mx[l] * (T)dc[k];
     }
+}
+
+// the same initial system for the compensated accumulator, formed in double-float
+__device__ __forceinline__ void sys_init(Sys<ca>& s, float4 mass, const float* dc, const float* dA, const float* xs) {
+    Sys<df> t;
+    sys_init(t, mass, dc, dA, xs);
+#pragma unroll
+    for (int k = 0; k < 10; ++k) s.g[k] = ca_of(t.g[k]);
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) s.r[r][k] = ca_of(t.r[r][k]);
 }
 
 // the exact difference a - b of two floats in the extended type
@@ -263,6 +330,36 @@ __device__ __forceinline__ void sys_add_t(Sys<T>& s, float w, const float* f, fl
             s.r[1][k] += z1 * f[k];
             s.r[2][k] += z2 * f[k];
             s.r[3][k] += z3 * f[k];
+        }
+    } else if constexpr (std::is_same<T, ca>::value) {
+        // compensated: z = x - x_s exact (TwoSum), w z_a as hi + lo to twice the precision,
+        // every product's rounding error carried into the accumulator's error sum
+        const df z[3] = {two_sum(x.x, -xs[0]), two_sum(x.y, -xs[1]), two_sum(x.z, -xs[2])};
+        df wz[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const df p = two_prod(w, z[a].hi);
+            wz[a] = df(p.hi, __fmaf_rn(w, z[a].lo, p.lo), 0);
+        }
+        ca_add(s.g[0], w);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) ca_add(s.g[1 + a], wz[a].hi, wz[a].lo);
+        int k = 4;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = a; b < 3; ++b, ++k) {
+                const df p = two_prod(wz[a].hi, z[b].hi);
+                ca_add(s.g[k], p.hi, __fmaf_rn(wz[a].hi, z[b].lo, __fmaf_rn(wz[a].lo, z[b].hi, p.lo)));
+            }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            ca_add(s.r[0][c], f[c]);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const df p = two_prod(z[a].hi, f[c]);
+                ca_add(s.r[1 + a][c], p.hi, __fmaf_rn(z[a].lo, f[c], p.lo));
+            }
         }
     } else {
         const T z1 = ext_diff(x.x, xs[0], (T*)nullptr), z2 = ext_diff(x.y, xs[1], (T*)nullptr),
@@ -574,8 +671,9 @@ __device__ __forceinline__ void solve_body(const Dev& d, int b, int lane, unsign
         else sys_zero(s);
         gather(s, c, A, xs, e0, e1);
         sys_reduce<L>(s, mask);
-        X Xd[4][3];
-        sys_solve(s, Xd);
+        const auto se = ext_sys(s);
+        typename ext_type<X>::T Xd[4][3];
+        sys_solve(se, Xd);
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -725,8 +823,9 @@ __device__ __forceinline__ void solve_heavy(const Dev& d, int b, const float4* _
         gather(s, c, A, xs, e0, e1);
         block_reduce(s, reinterpret_cast<Sys<X>*>(buf_raw));
         if (t == 0) {
-            X Xd[4][3];
-            sys_solve(s, Xd);
+            const auto se = ext_sys(s);
+            typename ext_type<X>::T Xd[4][3];
+            sys_solve(se, Xd);
 #pragma unroll
             for (int r = 0; r < 4; ++r)
 #pragma unroll

@@ -82,3 +82,44 @@ def same_contacts(gpu_c, ref_c):
     assert np.array_equal(gm, rm)
     assert np.array_equal(gd[:, :9], rd[:, :9].astype(np.float32))
     np.testing.assert_allclose(gd[:, 9:11], rd[:, 9:11], rtol=2e-7, atol=0)
+
+
+def body_corner_err(st_gpu: np.ndarray, st_ref: np.ndarray, he: np.ndarray) -> np.ndarray:
+    """Per body: max over its box corners of |y_gpu - y_ref| (absolute)."""
+    return np.linalg.norm(corners(st_gpu, he) - corners(st_ref, he), axis=-1).max(axis=1)
+
+
+def velocity_ratios(st_gpu: np.ndarray, st_ref: np.ndarray, he: np.ndarray, h: float) -> dict:
+    """v, omega and Q of a teacher-forced step against the oracle's (a9, Sec. 4.4), each as
+    the worst ratio of its error to what the body's own position error e and single-precision
+    rounding allow through the velocity recovery: v = (c1 - c0)/h moves by at most
+    (2 e + 2^-23 |c|)/h; A1 by e/he_min per entry (plus its rounding 2^-22), so
+    omega = vee(skew((A1 - A0) A0^T))/h by 4 (e/he_min + 2^-21)/h and Q = quat(A1) by
+    4 (e/he_min + 2^-21).  Every ratio must stay below 1."""
+    e = body_corner_err(st_gpu, st_ref, he)
+    hmin = he.min(axis=1)
+    cnorm = np.abs(st_ref[:, 0:3]).max(axis=1)
+    dv = np.linalg.norm(st_gpu[:, 16:19] - st_ref[:, 16:19], axis=1)
+    dw = np.linalg.norm(st_gpu[:, 19:22] - st_ref[:, 19:22], axis=1)
+    qg, qr = st_gpu[:, 12:16], st_ref[:, 12:16]
+    dq = np.minimum(np.linalg.norm(qg - qr, axis=1), np.linalg.norm(qg + qr, axis=1))
+    rot = e / hmin + 2.0 ** -21
+    return {"v": float((dv / ((2 * e + 2.0 ** -23 * cnorm) / h)).max()),
+            "omega": float((dw / (4 * rot / h)).max()),
+            "quat": float((dq / (4 * rot)).max())}
+
+
+def residual_ratio(r_gpu: np.ndarray, r_ref: np.ndarray, st_gpu: np.ndarray, st_ref: np.ndarray, he: np.ndarray,
+                   group: np.ndarray) -> float:
+    """Per-group residual sqrt(sum |q^{k+1} - q^k|^2) of the last sweep (a8, Sec. 4.2) against
+    the oracle's: each of the two iterates it differences is off by about the body's final
+    error (e on c, e/he_min on A) plus its single-precision rounding, so the residual may move
+    by twice that summed over the group's 12 coordinates per body; 1% of the residual on top
+    covers iterates whose errors exceed the final one.  Returns the worst ratio (< 1)."""
+    e = body_corner_err(st_gpu, st_ref, he)
+    hmin = he.min(axis=1)
+    cnorm = np.abs(st_ref[:, 0:3]).max(axis=1)
+    per = 3 * (e + 2.0 ** -23 * cnorm) ** 2 + 9 * (e / hmin + 2.0 ** -22) ** 2
+    ng = len(r_ref)
+    allow = 2 * np.sqrt(np.bincount(group, weights=per, minlength=ng)) + 0.01 * np.abs(r_ref)
+    return float((np.abs(r_gpu - r_ref) / allow).max()) if ng else 0.0

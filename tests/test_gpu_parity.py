@@ -6,8 +6,8 @@ import pytest
 
 import oracle as O
 import scenes as S
-from tests.gpu_helpers import (REL_TOL, activation_envelope_err, corners, rel_err, same_contacts, scene_scale,
-                               teacher_forced_step, worst_body)
+from tests.gpu_helpers import (REL_TOL, activation_envelope_err, corners, rel_err, residual_ratio, same_contacts,
+                               scene_scale, teacher_forced_step, velocity_ratios, worst_body)
 
 pytestmark = pytest.mark.gpu
 
@@ -64,11 +64,17 @@ def test_chain_pendulum_teacher_forced_every_step(P):
     ref = O.OracleScene(sc)
     g = P.Scene(sc)
     assert g.info()["fp64_bodies"] == 7
-    worst = 0.0
+    worst, vel, res = 0.0, {"v": 0.0, "omega": 0.0, "quat": 0.0}, 0.0
+    grp = sc.bodies["group"]
     for k in range(sc.n_steps):
         a, b = teacher_forced_step(g, ref)
         worst = max(worst, rel_err(a, b, _he(sc)))
+        # the velocity recovery (v, omega, Q) and the last sweep's residual, element by element
+        vel = {q: max(vel[q], r) for q, r in velocity_ratios(a, b, _he(sc), sc.params["h"]).items()}
+        res = max(res, residual_ratio(g.residual(), ref.residual(), a, b, _he(sc), grp))
     assert worst < REL_TOL, worst
+    assert max(vel.values()) < 1.0, vel
+    assert res < 1.0, res
     g.close()
 
 
@@ -173,6 +179,72 @@ def test_pile_full_size_sampled(P):
     g.close()
 
 
+def test_trees_full_size_sampled(P):
+    """All 4096 batched trees (139 690 bodies) in the launch configuration the bench times:
+    the oracle steps every 64th tree (a tree steps alone exactly as inside the batch) to the
+    landed window; for three steps the GPU's full scene starts each step from the oracle's
+    state on those trees.  Positions within tolerance; v, omega, Q and the per-tree residual
+    element by element."""
+    sc = S.batched_trees()
+    groups = np.arange(0, sc.n_groups, 64)
+    sub = S.select_groups(sc, groups)
+    rows = S.group_rows(sc, groups)
+    he = _he(sub)
+    ref = O.OracleScene(sub)
+    ref.step(60)
+    g = P.Scene(sc)
+    g.step(60)
+    worst, vel, res = 0.0, {"v": 0.0, "omega": 0.0, "quat": 0.0}, 0.0
+    for k in range(3):
+        full = g.state()
+        st0, k0 = ref.state(), ref.step_index
+        full[rows] = st0
+        g.set_state(full)
+        g.set_step_index(k0)
+        ref.step(1)
+        g.step(1)
+        a, b = g.state()[rows], ref.state()
+        e = rel_err(a, b, he)
+        if e >= REL_TOL:
+            e, body, e0 = activation_envelope_err(sub, st0, k0, a, b, he, O)
+        else:
+            vel = {q: max(vel[q], r) for q, r in velocity_ratios(a, b, he, sc.params["h"]).items()}
+            res = max(res, residual_ratio(g.residual()[groups], ref.residual(), a, b, he, sub.bodies["group"]))
+        worst = max(worst, e)
+    assert g.info()["n_contacts"] > 1000
+    assert worst < REL_TOL, worst
+    assert max(vel.values()) < 1.0, vel
+    assert res < 1.0, res
+    g.close()
+
+
+def test_quadruped_full_size_landed_step(P):
+    """The full quadruped scene (13-body driven quadruped, 50 000-cube bed, 64-segment rod):
+    after the oracle's first four steps the bed's layers have landed on each other; the
+    pair list and the contacts of that state are bit-exact and one teacher-forced step of the
+    bench's launch configuration is within tolerance."""
+    sc = S.quadruped_bed_rod()
+    ref = O.OracleScene(sc)
+    ref.step(4)
+    g = P.Scene(sc, max_pairs=32 * sc.n_bodies, max_contacts=64 * sc.n_bodies)
+    g.set_state(ref.state())
+    g.set_step_index(ref.step_index)
+    g.detect()
+    ref.detect()
+    rp = ref.pairs()
+    assert len(rp) > 100000
+    assert np.array_equal(g.pairs(), rp)
+    same_contacts(g.contacts(), ref.contacts())
+    he = _he(sc)
+    st0, k0 = ref.state(), ref.step_index
+    a, b = teacher_forced_step(g, ref)
+    e = rel_err(a, b, he)
+    if e >= REL_TOL:
+        e, body, e0 = activation_envelope_err(sc, st0, k0, a, b, he, O)
+    assert e < REL_TOL, e
+    g.close()
+
+
 def test_graph_and_eager_paths_identical_and_deterministic(P):
     sc = _pile_small()
     outs = []
@@ -195,11 +267,15 @@ def test_batched_trees_parity_and_alone_vs_in_mix(P):
     ref = O.OracleScene(sc)
     g = P.Scene(sc)
     worst, where, switched = 0.0, None, []
+    vel, res = {"v": 0.0, "omega": 0.0, "quat": 0.0}, 0.0
     he = _he(sc)
     for k in range(sc.n_steps):
         st0, k0 = ref.state(), ref.step_index
         a, b = teacher_forced_step(g, ref)
         e = rel_err(a, b, he)
+        if e < REL_TOL:  # (a step whose contacts switched branch is compared by the envelope below)
+            vel = {q: max(vel[q], r) for q, r in velocity_ratios(a, b, he, sc.params["h"]).items()}
+            res = max(res, residual_ratio(g.residual(), ref.residual(), a, b, he, sc.bodies["group"]))
         if e >= REL_TOL:
             # landing trees: a ground contact at its activation threshold may switch the other
             # way in single precision (compare with the oracle at thresholds moved by rounding)
@@ -208,6 +284,8 @@ def test_batched_trees_parity_and_alone_vs_in_mix(P):
         if e > worst:
             worst, where = e, (k, worst_body(a, b, he))
     assert worst < REL_TOL, (worst, where, switched, g.info()["fp64_bodies"])
+    assert max(vel.values()) < 1.0, vel
+    assert res < 1.0, res
     # each scene alone gives bit-identical results to the same scene inside the batch
     full = P.Scene(sc)
     full.step(20)
@@ -295,7 +373,7 @@ def test_capacity_overflow_is_reported(P):
 # the two sweep implementations and the fused sweep's lane counts
 # --------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("mode,lanes", [(1, 0), (2, 0), (3, 1), (3, 8), (2, 16)])
+@pytest.mark.parametrize("mode,lanes", [(1, 0), (2, 0), (3, 1), (3, 8), (2, 1), (2, 2), (2, 4), (2, 8), (2, 16)])
 def test_sweep_variants_match_oracle(P, mode, lanes):
     """Two launches per sweep (mode 1), one launch per sweep (mode 2) and the fused
     persistent sweep (mode 3) with several lane counts all stay within tolerance of the
@@ -329,18 +407,31 @@ def test_fused_sweep_deterministic_and_shape_independent(P):
 
 
 def test_sweep_modes_bit_identical(P):
-    """Same lanes per body: the three sweep modes compute the same bonds and the same
-    per-body sums in the same order, so their states are identical bit for bit."""
-    sc = _pile_small()
-    outs = []
-    for mode in (1, 2, 3):
-        g = P.Scene(sc, sweep_mode=mode, sweep_lanes=8)
-        assert g.info()["sweep_mode"] == mode
-        g.step(60)
+    """Same lanes per body: the three sweep modes, with the light bodies ordered by end count
+    or in body order, compute the same bonds and the same per-body sums in the same order, so
+    their states are identical bit for bit -- and so is the autotuned default, re-tuned
+    mid-run on a later state."""
+    for sc, lanes, n in ((_pile_small(), 8, 60), (S.batched_trees(n_scenes=24), 2, 40)):
+        outs = []
+        for mode, order in ((1, 1), (1, 2), (2, 1), (2, 2), (3, 0)):
+            g = P.Scene(sc, sweep_mode=mode, sweep_lanes=lanes, light_order=order)
+            info = g.info()
+            assert info["sweep_mode"] == mode
+            assert info["light_order"] == (order == 1)
+            g.step(n)
+            outs.append(g.state())
+            g.close()
+        g = P.Scene(sc, sweep_lanes=lanes)
+        info = g.info()
+        assert info["tuned"] == 1 and info["sweep_mode"] in (1, 2)
+        assert all(info[f"tune_sweep_ns{k}"] > 0 for k in range(4))
+        g.step(n // 2)
+        g.tune()
+        g.step(n - n // 2)
         outs.append(g.state())
         g.close()
-    assert np.array_equal(outs[0], outs[1])
-    assert np.array_equal(outs[0], outs[2])
+        for o in outs[1:]:
+            assert np.array_equal(outs[0], o)
 
 
 # --------------------------------------------------------------------------------------
