@@ -239,6 +239,18 @@ pabd_status pabd_tune(pabd_scene* s);
  * own streams, capacities or parameters). */
 pabd_status pabd_step_many(pabd_scene* const* scenes, int n, const int* nsteps);
 
+/* Hold groups still: from the next step on (ordered on the scene's stream), every body of a
+ * group g with hold[g] != 0 keeps its state (q, v, omega, Q) through each step, as if pinned
+ * for the step, while the other groups step; a held group's bodies still take part in
+ * collision detection, whose contacts stay within the group.  hold has n_groups bytes
+ * (n_groups must equal pabd_info.n_groups); NULL releases every group.  A group's step
+ * depends only on its own bodies and bonds, so a group stepped k times among held groups ends
+ * where it ends stepped k times alone with the same sweep_lanes.  The mask is copied through
+ * the library's pinned staging, so the caller may reuse its buffer at once.  Scenes with
+ * DRIVE or AL_DISTANCE bonds (whose state moves with the step) return PABD_ERR_ARG.  This is
+ * how a server steps only the resident scenes that have work, packed as groups of one scene. */
+pabd_status pabd_set_group_hold(pabd_scene* s, const uint8_t* hold, size_t n_groups);
+
 /* Bound of the device-side waits of the scene (the grid barrier between the sweeps of the
  * fused persistent sweep, sweep_mode 3): a wait gives up after `polls` polls (default 2^24,
  * about a second), latches PABD_ERR_TIMEOUT and ends its kernel, which the next
@@ -268,6 +280,18 @@ pabd_status pabd_sync(pabd_scene* s);
  * Reads synchronise; writes are ordered on the stream before later steps. */
 pabd_status pabd_read_state(pabd_scene* s, double* host_rows, size_t n_bodies);
 pabd_status pabd_write_state(pabd_scene* s, const double* host_rows, size_t n_bodies);
+
+/* The same state in the device's own single-precision layout, for callers that move it every
+ * step (no conversion, no validation, asynchronous): host holds 24 * n_bodies floats, the four
+ * device arrays one after the other -- q (12 floats per body: c, then A row-major), then the
+ * quaternion (x, y, z, w), then v (x, y, z, unused), then omega (x, y, z, unused), each
+ * n_bodies rows.  Both calls only enqueue copies on the scene's stream and return: the host
+ * buffer must stay untouched until the stream has passed them (pabd_sync), and should be
+ * page-locked for the copies to run at full speed.  v and omega of pinned bodies are ignored
+ * by the step; a non-finite value written surfaces as PABD_ERR_DIVERGED after the next step.
+ * n_bodies must equal the scene's body count (else PABD_ERR_ARG). */
+pabd_status pabd_read_state_f32(pabd_scene* s, float* host, size_t n_bodies);
+pabd_status pabd_write_state_f32(pabd_scene* s, const float* host, size_t n_bodies);
 
 /* Set the index n of the next step (its end time is (n + 1) h, used by DRIVE bonds);
  * ordered on the stream like a state write. */

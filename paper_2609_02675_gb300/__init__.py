@@ -91,10 +91,13 @@ _SIGS = {
     "pabd_step_many": [_P, ctypes.c_int, _PI32],
     "pabd_set_wait_limit": [_P, ctypes.c_uint32],
     "pabd_tune": [_P],
+    "pabd_set_group_hold": [_P, _P, ctypes.c_size_t],
     "pabd_detect": [_P],
     "pabd_sync": [_P],
     "pabd_read_state": [_P, _PD, ctypes.c_size_t],
     "pabd_write_state": [_P, _PD, ctypes.c_size_t],
+    "pabd_read_state_f32": [_P, _P, ctypes.c_size_t],
+    "pabd_write_state_f32": [_P, _P, ctypes.c_size_t],
     "pabd_read_bond_state": [_P, _PD, ctypes.c_size_t],
     "pabd_write_bond_state": [_P, _PD, ctypes.c_size_t],
     "pabd_set_step_index": [_P, ctypes.c_int64],
@@ -197,6 +200,15 @@ def pabd_step_many(scenes, nsteps):
     return _check(_lib.pabd_step_many(ctypes.cast(arr, _P), n, cnt.ctypes.data_as(_PI32)), "pabd_step_many")
 
 
+def pabd_set_group_hold(s, hold, n_groups: int):
+    """hold: None (release all) or n_groups bytes, nonzero = group held still."""
+    if hold is None:
+        return _check(_lib.pabd_set_group_hold(s, None, n_groups), "pabd_set_group_hold")
+    h = np.ascontiguousarray(hold, dtype=np.uint8)
+    assert h.shape == (n_groups,)
+    return _check(_lib.pabd_set_group_hold(s, h.ctypes.data, n_groups), "pabd_set_group_hold")
+
+
 def pabd_tune(s):
     return _check(_lib.pabd_tune(s), "pabd_tune")
 
@@ -235,6 +247,17 @@ def pabd_read_bond_state(s, n_static_bonds: int) -> np.ndarray:
 def pabd_write_bond_state(s, st: np.ndarray):
     st = np.ascontiguousarray(st, dtype=np.float64).reshape(-1, 2)
     _check(_lib.pabd_write_bond_state(s, st.ctypes.data_as(_PD), st.shape[0]), "pabd_write_bond_state")
+
+
+def pabd_read_state_f32(s, host: int, n_bodies: int):
+    """Enqueue the device-layout state (24 floats per body) into the host buffer at address
+    `host` (see include/pabd.h); the buffer is valid after pabd_sync."""
+    return _check(_lib.pabd_read_state_f32(s, host, n_bodies), "pabd_read_state_f32")
+
+
+def pabd_write_state_f32(s, host: int, n_bodies: int):
+    """Enqueue the device-layout state from the host buffer at address `host`."""
+    return _check(_lib.pabd_write_state_f32(s, host, n_bodies), "pabd_write_state_f32")
 
 
 def pabd_set_step_index(s, k: int):
@@ -417,6 +440,10 @@ class Scene:
     def set_wait_limit(self, polls: int):
         pabd_set_wait_limit(self.h, polls)
 
+    def set_group_hold(self, hold):
+        """Hold the groups with hold[g] != 0 still from the next step on (None: release all)."""
+        pabd_set_group_hold(self.h, hold, self.n_groups)
+
     def tune(self):
         """Re-run the sweep autotuner on the current state (see pabd_tune)."""
         pabd_tune(self.h)
@@ -432,6 +459,12 @@ class Scene:
 
     def set_state(self, rows: np.ndarray):
         pabd_write_state(self.h, rows)
+
+    def read_state_f32(self, host_ptr: int):
+        pabd_read_state_f32(self.h, host_ptr, self.n)
+
+    def write_state_f32(self, host_ptr: int):
+        pabd_write_state_f32(self.h, host_ptr, self.n)
 
     def set_step_index(self, k: int):
         pabd_set_step_index(self.h, k)

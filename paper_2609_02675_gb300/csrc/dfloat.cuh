@@ -103,6 +103,26 @@ __device__ __forceinline__ df sqrt(df x) {
 
 __device__ __forceinline__ df inv_sqrt(df x) { return df(1.f) / sqrt(x); }
 
+// Fused multiply-add a * b + c of double-words in the "sloppy" form (the products' and the
+// sum's rounding errors added in single precision, one renormalisation): its error is a few
+// units of 2^-48 of |a b| + |c| -- the bound of an FP64 multiply-add's inputs rather than of
+// its result -- at about half the cost of a product followed by the accurate sum.
+__device__ __forceinline__ df fma_dd(df a, df b, df c) {
+    const df p = two_prod(a.hi, b.hi);
+    const df t = two_sum(p.hi, c.hi);
+    const float e = __fadd_rn(__fadd_rn(__fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo)), c.lo), t.lo);
+    return fast_two_sum(t.hi, e);
+}
+
+// reciprocal 1 / x of a double-word: the single-precision reciprocal th, corrected once by
+// the double-word residual 1 - x th (Newton's step)
+__device__ __forceinline__ df recip_dd(df x) {
+    const float th = __fdiv_rn(1.f, x.hi);
+    const df r = two_prod(x.hi, th);
+    const float e = __fsub_rn(__fsub_rn(1.f, r.hi), __fmaf_rn(x.lo, th, r.lo));
+    return fast_two_sum(th, __fmul_rn(th, e));
+}
+
 __device__ __forceinline__ df shfl_xor(unsigned mask, df v, int o) {
     return df(__shfl_xor_sync(mask, v.hi, o), __shfl_xor_sync(mask, v.lo, o), 0);
 }

@@ -711,6 +711,15 @@ void launch_broadphase(const Dev& d, cudaStream_t st, long long* launches) {
 void launch_collision(const Dev& d, cudaStream_t st, long long* launches) {
     launch_pdl(k_aabb, dim3(nblk(d.N)), dim3(CT), 0, st, d);
     *launches += 1;
+    if (!d.p.body_contacts) {
+        // ground contacts only: no broad phase (the pair count stays at the zero the step's
+        // reset wrote, and the pair contacts' prefix at the zero written at creation)
+        launch_pdl(k_narrow_count, dim3(stride_grid(d.N, CT)), dim3(CT), 0, st, d);
+        scan_exclusive(d.gnd_cnt, d.gnd_off, nullptr, d.N, d.scan_scratch, st, launches);
+        launch_pdl(k_narrow_write, dim3(stride_grid(d.N, CT)), dim3(CT), 0, st, d);
+        *launches += 2;
+        return;
+    }
     if (d.p.broadphase == 1) {
         launch_lbvh_pairs(d, st, launches);
     } else {

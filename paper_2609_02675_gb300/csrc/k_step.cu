@@ -22,12 +22,12 @@ __device__ __forceinline__ void store_q(float4* q, int b, const float* c, const 
 }
 
 // Predictor (Alg. 1): v* = v + h g; c* = c + h v*; Q* = normalise(Q + h/2 [w, 0] Q);
-// A* = R(Q*); s = q^0 = (c*, A*).  Pinned bodies keep q^n.
+// A* = R(Q*); s = q^0 = (c*, A*).  Pinned bodies, and those of a group held this step, keep q^n.
 __global__ void k_predict(Dev d) {
     pdl_enter();
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= d.N) return;
-    if (d.bflags[b] & BF_PINNED) {
+    if ((d.bflags[b] & BF_PINNED) || held(d, b)) {
         float4 a0 = d.qn[3 * b], a1 = d.qn[3 * b + 1], a2 = d.qn[3 * b + 2];
         d.sq[3 * b] = a0; d.sq[3 * b + 1] = a1; d.sq[3 * b + 2] = a2;
         d.qa[3 * b] = a0; d.qa[3 * b + 1] = a1; d.qa[3 * b + 2] = a2;
@@ -83,7 +83,7 @@ __global__ void k_finalize(Dev d, const float4* __restrict__ qf, int dyn) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b == 0) atomicAdd((unsigned long long*)d.step_index, 1ull);
     if (b >= d.N) return;
-    if (d.bflags[b] & BF_PINNED) return;
+    if ((d.bflags[b] & BF_PINNED) || held(d, b)) return;  // (a held group keeps its state)
     float4 n0 = d.qn[3 * b], n1 = d.qn[3 * b + 1], n2 = d.qn[3 * b + 2];
     float4 f0 = qf[3 * b], f1 = qf[3 * b + 1], f2 = qf[3 * b + 2];
     const float c0[3] = {n0.x, n0.y, n0.z}, c1[3] = {f0.x, f0.y, f0.z};
@@ -186,6 +186,42 @@ __global__ void k_csr_sort(Dev d) {
         const float4 x = (id & 1) ? d.bxj[bond] : d.bxi[bond];
         d.end_x[p] = make_float4(x.x, x.y, x.z, 0.f);
     }
+}
+
+// CSR of a scene whose only contacts are with the ground.  Contact bonds follow the static
+// ones and the ground contacts are numbered in body order (k_narrow_write), so in (body,
+// 2 bond + side) order body b's slice is its static ends (fixed at creation) followed by its
+// ground contacts, and starts at sta_off[b] + gnd_off[b] -- the sum of two prefix sums: no
+// count, atomics or sort.  Ground contacts past the contact capacity were not written (the
+// narrow phase latched PABD_ERR_CAPACITY); the slices skip them.
+__global__ void k_csr_ground(Dev d) {
+    pdl_enter();
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > d.N) return;
+    const int cap = d.cap_contacts;
+    const int g0 = min(d.gnd_off[b], cap);
+    const int off = d.sta_off[b] + g0;
+    d.end_off[b] = off;
+    if (b == d.N) return;
+    const int s0 = d.sta_off[b], sn = d.sta_off[b + 1] - s0;
+    const int gn = min(d.gnd_off[b + 1], cap) - g0;
+    for (int k = 0; k < sn; ++k) {
+        const int id = d.sta_id[s0 + k];
+        const int bond = id >> 1;
+        d.end_id[off + k] = id;
+        d.end_pos[id] = off + k;
+        const float4 x = (id & 1) ? d.bxj[bond] : d.bxi[bond];
+        d.end_x[off + k] = make_float4(x.x, x.y, x.z, 0.f);
+    }
+    for (int k = 0; k < gn; ++k) {
+        const int bond = d.Nc + g0 + k;
+        const int p = off + sn + k;
+        d.end_id[p] = 2 * bond;
+        d.end_pos[2 * bond] = p;
+        const float4 x = d.bxi[bond];
+        d.end_x[p] = make_float4(x.x, x.y, x.z, 0.f);
+    }
+    if (sn + gn > HEAVY_ENDS) d.heavy[atomicAdd(&d.ctr[C_NHEAVY], 1)] = b;
 }
 
 // The heavy bodies' slices, one block per body (block_sort_slice), the end-record buffer
@@ -334,6 +370,7 @@ __global__ void k_step_reset(Dev d) {
     pdl_enter();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t == 0) {
+        d.ctr[C_NPAIRS] = 0;
         d.ctr[C_CELLBITS] = 0;
         d.ctr[C_NLARGE] = 0;
         d.ctr[C_NHEAVY] = 0;
@@ -365,6 +402,11 @@ void launch_step_reset(const Dev& d, cudaStream_t st, long long* launches) {
 }
 
 void launch_csr(const Dev& d, cudaStream_t st, long long* launches) {
+    if (d.sta_off) {
+        launch_pdl(k_csr_ground, dim3(nblk(d.N + 1)), dim3(ST_T), 0, st, d);
+        *launches += 1;
+        return;
+    }
     launch_pdl(k_csr_count, dim3(stride_grid(d.cap_bonds, ST_T)), dim3(ST_T), 0, st, d);
     scan_exclusive(d.end_cnt, d.end_off, nullptr, d.N, d.scan_scratch, st, launches);
     launch_pdl(k_csr_fill, dim3(stride_grid(d.cap_bonds, ST_T)), dim3(ST_T), 0, st, d);

@@ -24,9 +24,8 @@ namespace pabd {
 constexpr int BOND_T = 256;
 constexpr int SOLVE_T = 128;
 
-__global__ void __launch_bounds__(BOND_T) k_bond(Dev d, const float4* __restrict__ q, int it) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= d.ctr[C_NBONDS]) return;
+// one bond's end records from q^k
+__device__ __forceinline__ void bond_one(const Dev& d, const float4* __restrict__ q, int it, int b) {
     const int4 m = d.bmeta[b];
     const float4 xi = d.bxi[b], xj = d.bxj[b];
     float c[3], A[9];
@@ -42,6 +41,30 @@ __global__ void __launch_bounds__(BOND_T) k_bond(Dev d, const float4* __restrict
     if (p1 >= 0) d.ends[p1] = make_float4(w, -f[0], -f[1], -f[2]);
 }
 
+// (strides over this step's bonds with a grid capped at GS_BLOCKS blocks: the bond capacity
+// holds room for every possible contact, far more than a step has)
+__global__ void __launch_bounds__(BOND_T) k_bond(Dev d, const float4* __restrict__ q, int it) {
+    pdl_enter();
+    const int nb = d.ctr[C_NBONDS];
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) bond_one(d, q, it, b);
+}
+
+// add the records of ends p0, p0 + stride, ... < e1 in that order, each loaded one round
+// ahead of its sum (the loads of the next end overlap the arithmetic of this one)
+template <class T>
+__device__ __forceinline__ void add_records(const Dev& d, Sys<T>& s, int p0, int e1, int stride, const float* xs) {
+    if (p0 >= e1) return;
+    float4 e = d.ends[p0], x = d.end_x[p0];
+    for (int p = p0; p < e1; p += stride) {
+        const float4 ec = e, xc = x;
+        if (p + stride < e1) {
+            e = d.ends[p + stride];
+            x = d.end_x[p + stride];
+        }
+        sys_add(s, ec, xc, xs);
+    }
+}
+
 // One body per group of L lanes; lane l adds the bond kernel's records of the body's ends
 // l, l + L, ... -- in FP32, or in the extended type for a body on the extended path (the same
 // records and order as the one-launch sweep, so the two modes agree bit for bit).  The first
@@ -50,14 +73,15 @@ __global__ void __launch_bounds__(BOND_T) k_bond(Dev d, const float4* __restrict
 template <int L, class X>
 __global__ void __launch_bounds__(SOLVE_T, 4) k_solve(Dev d, const float4* __restrict__ qi, float4* __restrict__ qo,
                                                    int it, int light) {
+    pdl_enter();
     const int last = it == d.p.n_iter - 1;
     if ((int)blockIdx.x >= light) {
         heavy_role<X>(d, blockIdx.x - light, qi, qo, last,
             [&](int b, auto& s, const float* c, const float* A, const float* xs, int e0, int e1, int ln) {
-                for (int p = e0 + ln; p < e1; p += 32) sys_add(s, d.ends[p], d.end_x[p], xs);
+                add_records(d, s, e0 + ln, e1, 32, xs);
             },
             [&](int b, auto& s, const float* c, const float* A, const float* xs, int e0, int e1, int t) {
-                for (int p = e0 + t; p < e1; p += HEAVY_T) sys_add(s, d.ends[p], d.end_x[p], xs);
+                add_records(d, s, e0 + t, e1, HEAVY_T, xs);
             });
         return;
     }
@@ -69,13 +93,12 @@ __global__ void __launch_bounds__(SOLVE_T, 4) k_solve(Dev d, const float4* __res
     const int b = d.light_sorted ? d.order[slot] : slot;
     solve_body<L, X>(d, b, lane, lane_mask<L>(), qi, qo, last,
                      [&](auto& s, const float* c, const float* A, const float* xs, int e0, int e1) {
-        for (int p = e0 + lane; p < e1; p += L) sys_add(s, d.ends[p], d.end_x[p], xs);
+        add_records(d, s, e0 + lane, e1, L, xs);
     });
 }
 
 void launch_bond(const Dev& d, const float4* q, int it, cudaStream_t st, long long* launches) {
-    const int n = d.cap_bonds > 0 ? d.cap_bonds : 1;
-    k_bond<<<(n + BOND_T - 1) / BOND_T, BOND_T, 0, st>>>(d, q, it);
+    launch_pdl(k_bond, dim3(stride_grid(d.cap_bonds > 0 ? d.cap_bonds : 1, BOND_T)), dim3(BOND_T), 0, st, d, q, it);
     *launches += 1;
 }
 
@@ -87,16 +110,16 @@ void launch_solve(const Dev& d, const float4* q_in, float4* q_out, int it, int l
     const int grid = light + HEAVY_BLOCKS;
     const bool f64 = d.p.precision_policy == 2;
     switch (lanes) {
-        case 1: f64 ? k_solve<1, double><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light)
-                    : k_solve<1, ca><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light); break;
-        case 2: f64 ? k_solve<2, double><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light)
-                    : k_solve<2, ca><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light); break;
-        case 4: f64 ? k_solve<4, double><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light)
-                    : k_solve<4, ca><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light); break;
-        case 8: f64 ? k_solve<8, double><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light)
-                    : k_solve<8, ca><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light); break;
-        default: f64 ? k_solve<16, double><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light)
-                     : k_solve<16, ca><<<grid, SOLVE_T, 0, st>>>(d, q_in, q_out, it, light); break;
+        case 1: f64 ? launch_pdl(k_solve<1, double>, dim3(grid), dim3(SOLVE_T), 0, st, d, q_in, q_out, it, light)
+                    : launch_pdl(k_solve<1, ca>, dim3(grid), dim3(SOLVE_T), 0, st, d, q_in, q_out, it, light); break;
+        case 2: f64 ? launch_pdl(k_solve<2, double>, dim3(grid), dim3(SOLVE_T), 0, st, d, q_in, q_out, it, light)
+                    : launch_pdl(k_solve<2, ca>, dim3(grid), dim3(SOLVE_T), 0, st, d, q_in, q_out, it, light); break;
+        case 4: f64 ? launch_pdl(k_solve<4, double>, dim3(grid), dim3(SOLVE_T), 0, st, d, q_in, q_out, it, light)
+                    : launch_pdl(k_solve<4, ca>, dim3(grid), dim3(SOLVE_T), 0, st, d, q_in, q_out, it, light); break;
+        case 8: f64 ? launch_pdl(k_solve<8, double>, dim3(grid), dim3(SOLVE_T), 0, st, d, q_in, q_out, it, light)
+                    : launch_pdl(k_solve<8, ca>, dim3(grid), dim3(SOLVE_T), 0, st, d, q_in, q_out, it, light); break;
+        default: f64 ? launch_pdl(k_solve<16, double>, dim3(grid), dim3(SOLVE_T), 0, st, d, q_in, q_out, it, light)
+                     : launch_pdl(k_solve<16, ca>, dim3(grid), dim3(SOLVE_T), 0, st, d, q_in, q_out, it, light); break;
     }
     *launches += 1;
 }

@@ -176,6 +176,12 @@ struct pabd_scene {
     cudaStream_t body_st = nullptr;
     // polls before a device-side wait gives up (PABD_ERR_TIMEOUT); about a second by default
     unsigned wait_polls = 1u << 24;
+    // pinned staging of the group hold masks: HOLD_SLOTS slots of G bytes used in turn, each
+    // reused only after its previous copy to the device has completed
+    static constexpr int HOLD_SLOTS = 8;
+    unsigned char* hold_pinned = nullptr;
+    cudaEvent_t hold_ev[HOLD_SLOTS] = {};
+    int hold_next = 0;
 
     void* dalloc(size_t n) {
         if (n == 0) n = 16;
@@ -229,8 +235,10 @@ void enqueue_step(pabd_scene* s, long long* launches, const cudaEvent_t* ev = nu
     float4* nxt = d.qb;
     auto two_launch = [&]() {
         for (int it = 0; it < d.p.n_iter; ++it) {
+            // (the counter of run-time extended-precision redos, which counts the last sweep's,
+            // was reset at the head of the step; the launches follow each other as
+            // programmatic dependents)
             launch_bond(d, cur, it, s->st, launches);
-            if (it == d.p.n_iter - 1) cudaMemsetAsync(d.ctr + C_FP64DYN, 0, sizeof(int), s->st);
             launch_solve(d, cur, nxt, it, s->lanes, s->st, launches);
             float4* t = cur; cur = nxt; nxt = t;
         }
@@ -295,8 +303,7 @@ void enqueue_step(pabd_scene* s, long long* launches, const cudaEvent_t* ev = nu
             float4* t = cur; cur = nxt; nxt = t;
         }
     } else {
-        launch_end_records(d, s->st, launches);  // the extended path's own evaluation reads them
-        two_launch();
+        two_launch();  // (the bond kernel reads the bonds, the solve their stored end records)
     }
     if (cur) launch_al_final(d, cur, s->st, launches);
     mark();
@@ -639,6 +646,25 @@ pabd_status finalize_scene(pabd_scene* s) {
             s->al_init[k] = make_float2((float)hb.kappa, 0.f);
         }
     }
+    // scenes whose only contacts are with the ground: each body's live static ends, sorted
+    std::vector<int> sta_off, sta_id;
+    if (!ds.body_contacts) {
+        std::vector<int> cnt(N + 1, 0);
+        for (int k = 0; k < Nc; ++k) {
+            const HostBond& hb = s->bonds[k];
+            if (hb.i >= 0 && !(flags[hb.i] & BF_PINNED)) ++cnt[hb.i];
+            if (hb.j >= 0 && !(flags[hb.j] & BF_PINNED)) ++cnt[hb.j];
+        }
+        sta_off.assign(N + 1, 0);
+        for (int b = 0; b < N; ++b) sta_off[b + 1] = sta_off[b] + cnt[b];
+        sta_id.assign(sta_off[N] > 0 ? sta_off[N] : 1, 0);
+        std::vector<int> cur(sta_off.begin(), sta_off.end() - 1);
+        for (int k = 0; k < Nc; ++k) {  // bond order: each body's ends come out sorted
+            const HostBond& hb = s->bonds[k];
+            if (hb.i >= 0 && !(flags[hb.i] & BF_PINNED)) sta_id[cur[hb.i]++] = 2 * k;
+            if (hb.j >= 0 && !(flags[hb.j] & BF_PINNED)) sta_id[cur[hb.j]++] = 2 * k + 1;
+        }
+    }
     std::vector<int> adj_off(N + 1, 0), adj_nbr;
     for (int b = 0; b < N; ++b) {
         std::vector<int>& v = adj[b];
@@ -654,6 +680,7 @@ pabd_status finalize_scene(pabd_scene* s) {
     ok &= alloc_arr(s, d.vel, N) && alloc_arr(s, d.omg, N) && alloc_arr(s, d.quat, N) && alloc_arr(s, d.qstar, N);
     ok &= alloc_arr(s, d.mass, N) && alloc_arr(s, d.he, N) && alloc_arr(s, d.xs, N);
     ok &= alloc_arr(s, d.bflags, N) && alloc_arr(s, d.group, N) && alloc_arr(s, d.group_off, d.G + 1);
+    ok &= alloc_arr(s, d.group_hold, d.G);
     ok &= alloc_arr(s, d.large_ids, N);
     ok &= alloc_arr(s, d.resid_body, N) && alloc_arr(s, d.resid_group, d.G);
     ok &= alloc_arr(s, d.bmeta, d.cap_bonds) && alloc_arr(s, d.bxi, d.cap_bonds) && alloc_arr(s, d.bxj, d.cap_bonds) &&
@@ -683,6 +710,7 @@ pabd_status finalize_scene(pabd_scene* s) {
         ok &= alloc_arr(s, d.adj_off, N + 1) && alloc_arr(s, d.adj_nbr, adj_nbr.size());
     }
     if (d.Nal) ok &= alloc_arr(s, d.al_st0, Nc) && alloc_arr(s, d.al_st1, Nc) && alloc_arr(s, d.al_par, Nc);
+    if (!sta_off.empty()) ok &= alloc_arr(s, d.sta_off, N + 1) && alloc_arr(s, d.sta_id, sta_id.size());
     if (p.resid_tol > 0) ok &= alloc_arr(s, d.sweep_ctl, 4) && alloc_arr(s, d.group_done, d.G);
     if (p.broadphase == 1) {
         const size_t ntile = ((size_t)N + 1023) / 1024 + 1;
@@ -724,10 +752,16 @@ pabd_status finalize_scene(pabd_scene* s) {
         CK(up(d.adj_nbr, adj_nbr.data(), sizeof(int) * adj_nbr.size()));
     }
     if (d.Nal) CK(up(d.al_par, al_par.data(), sizeof(float4) * Nc));
+    if (d.sta_off) {
+        CK(up(d.sta_off, sta_off.data(), sizeof(int) * (N + 1)));
+        CK(up(d.sta_id, sta_id.data(), sizeof(int) * sta_id.size()));
+    }
     CK(cudaMemsetAsync(d.ctr, 0, sizeof(int) * C_COUNT, st));
     CK(cudaMemsetAsync(d.step_index, 0, sizeof(long long), st));
     CK(cudaMemsetAsync(d.resid_body, 0, sizeof(double) * (N ? N : 1), st));
     CK(cudaMemsetAsync(d.resid_group, 0, sizeof(double) * (d.G ? d.G : 1), st));
+    CK(cudaMemsetAsync(d.group_hold, 0, d.G ? d.G : 1, st));
+    CK(cudaMemsetAsync(d.npc_off, 0, sizeof(int), st));  // no pair contacts before the first step
     CK(cudaMemsetAsync(d.end_pos, 0xff, sizeof(int) * d.cap_ends, st));
     CK(cudaMemsetAsync(d.gbar, 0, 2 * sizeof(unsigned), st));
     const unsigned wait_polls = s->wait_polls;
@@ -1105,6 +1139,34 @@ pabd_status pabd_step_many(pabd_scene* const* scenes, int n, const int* nsteps) 
     return PABD_OK;
 }
 
+pabd_status pabd_set_group_hold(pabd_scene* s, const uint8_t* hold, size_t n_groups) {
+    if (!s) return PABD_ERR_ARG;
+    pabd_status r = finalize_scene(s);
+    if (r != PABD_OK) return r;
+    Dev& d = s->d;
+    if (n_groups != (size_t)d.G) return PABD_ERR_ARG;
+    // a held group must keep every part of its state: no drive anchors moving with the step
+    // index, no augmented Lagrangian warm start
+    if (d.Ndrive > 0 || d.Nal > 0) return PABD_ERR_ARG;
+    if (d.G == 0) return PABD_OK;
+    if (!hold) {
+        CK(cudaMemsetAsync(d.group_hold, 0, d.G, s->st));
+        return PABD_OK;
+    }
+    if (!s->hold_pinned) {
+        CK(cudaMallocHost(&s->hold_pinned, (size_t)pabd_scene::HOLD_SLOTS * d.G));
+        for (cudaEvent_t& e : s->hold_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    const int k = s->hold_next;
+    s->hold_next = (k + 1) % pabd_scene::HOLD_SLOTS;
+    CK(cudaEventSynchronize(s->hold_ev[k]));  // this slot's previous copy has left the host
+    unsigned char* slot = s->hold_pinned + (size_t)k * d.G;
+    for (int g = 0; g < d.G; ++g) slot[g] = hold[g] ? 1 : 0;
+    CK(cudaMemcpyAsync(d.group_hold, slot, d.G, cudaMemcpyHostToDevice, s->st));
+    CK(cudaEventRecord(s->hold_ev[k], s->st));
+    return PABD_OK;
+}
+
 pabd_status pabd_set_wait_limit(pabd_scene* s, uint32_t polls) {
     if (!s || polls == 0) return PABD_ERR_ARG;
     s->wait_polls = polls;
@@ -1193,6 +1255,34 @@ pabd_status pabd_write_state(pabd_scene* s, const double* rows, size_t n) {
     CK(cudaMemcpyAsync(s->d.omg, w.data(), sizeof(float4) * N, cudaMemcpyHostToDevice, s->st));
     CK(cudaMemcpyAsync(s->d.quat, Q.data(), sizeof(float4) * N, cudaMemcpyHostToDevice, s->st));
     CK(cudaStreamSynchronize(s->st));  // the staging vectors go out of scope
+    return PABD_OK;
+}
+
+pabd_status pabd_read_state_f32(pabd_scene* s, float* host, size_t n) {
+    if (!s || !host) return PABD_ERR_ARG;
+    pabd_status r = finalize_scene(s);
+    if (r != PABD_OK) return r;
+    const int N = s->d.N;
+    if (n != (size_t)N) return PABD_ERR_ARG;
+    float* o = host;
+    CK(cudaMemcpyAsync(o, s->d.qn, sizeof(float4) * 3 * N, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(o + 12 * (size_t)N, s->d.quat, sizeof(float4) * N, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(o + 16 * (size_t)N, s->d.vel, sizeof(float4) * N, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(o + 20 * (size_t)N, s->d.omg, sizeof(float4) * N, cudaMemcpyDeviceToHost, s->st));
+    return PABD_OK;
+}
+
+pabd_status pabd_write_state_f32(pabd_scene* s, const float* host, size_t n) {
+    if (!s || !host) return PABD_ERR_ARG;
+    pabd_status r = finalize_scene(s);
+    if (r != PABD_OK) return r;
+    const int N = s->d.N;
+    if (n != (size_t)N) return PABD_ERR_ARG;
+    const float* o = host;
+    CK(cudaMemcpyAsync(s->d.qn, o, sizeof(float4) * 3 * N, cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(s->d.quat, o + 12 * (size_t)N, sizeof(float4) * N, cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(s->d.vel, o + 16 * (size_t)N, sizeof(float4) * N, cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(s->d.omg, o + 20 * (size_t)N, sizeof(float4) * N, cudaMemcpyHostToDevice, s->st));
     return PABD_OK;
 }
 
@@ -1359,6 +1449,8 @@ pabd_status pabd_destroy_scene(pabd_scene* s) {
         else cudaFree(p);
     }
     if (s->body_st) cudaStreamDestroy(s->body_st);
+    if (s->hold_pinned) cudaFreeHost(s->hold_pinned);
+    for (cudaEvent_t e : s->hold_ev) if (e) cudaEventDestroy(e);
     if (s->own_stream) cudaStreamDestroy(s->st);
     delete s;
     return PABD_OK;

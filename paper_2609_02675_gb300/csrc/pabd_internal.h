@@ -99,6 +99,10 @@ struct Dev {
     int *end_cnt, *end_cur, *end_off, *end_id, *end_pos;
     float4 *ends, *end_x;
     int *heavy;                 // ids of the bodies with more than HEAVY_ENDS ends (C_NHEAVY of them)
+    // scenes whose only contacts are with the ground: each body's live static bond ends, sorted
+    // by end id (2 bond + side), fixed at creation -- the CSR is these plus the step's ground
+    // contacts (k_csr_ground); null otherwise
+    int *sta_off, *sta_id;
     int light_sorted;           // 1: the sweeps take the light bodies in Dev::order; 0: in body order
     int *order;                 // this step's light bodies by (class, end count), C_NLIGHT of them
     int *bin_cnt, *bin_cur;     // per bin of the light order: bodies, and the blocks' reservations
@@ -137,9 +141,15 @@ struct Dev {
     // the scenes that have stopped
     int *sweep_ctl;
     unsigned char *group_done;
+    // groups held still by the host this step (pabd_set_group_hold): their bodies keep q, v, omega
+    // and Q, as if pinned for the step
+    unsigned char *group_hold;
     long long *step_index;
     int *scan_scratch;          // block sums of the scans
 };
+
+// body b's group is held still this step (pabd_set_group_hold)
+__device__ __forceinline__ bool held(const Dev& d, int b) { return d.group_hold[d.group[b]] != 0; }
 
 // ---- programmatic dependent launch ----
 // A kernel launched by launch_pdl may be launched while its predecessor on the stream is still

@@ -1,18 +1,32 @@
 """Continuous-batching step server over device-resident scenes.
 
-Requests ``(scene_id, n_steps)`` arrive over time.  Each resident scene is one library
-scene with its own CUDA stream and its state kept on the device between requests.  Every
-``pump()`` polls the steps in flight and admits newly arrived requests. A scene becomes
-resident when its device memory fits the HBM budget; idle scenes are evicted least recently
-used first, their state kept on the host. ``pump()`` then launches one step (one CUDA-graph
-launch) for every resident scene that has pending work and no step in flight. Steps of
-different scenes therefore overlap on the GPU, and a request that arrives while others run
-joins at the next pump instead of waiting for them to finish.
+Requests ``(scene_id, n_steps)`` arrive over time; every scene's state stays on the device
+between requests.  Every ``pump()`` polls the steps in flight, admits newly arrived requests
+and launches the next steps, so a request that arrives while others run joins at the next
+pump instead of waiting for them to finish.
+
+Two kinds of resident scene:
+
+* **Packed** (scenes of at most ``pool_max_bodies`` bodies without drives or augmented
+  Lagrangian bonds): the small scenes are the groups of one library scene, a *pool*.  One
+  graph launch steps every member that has work; the members without work are held still for
+  that step (``pabd_set_group_hold``).  A group's step depends only on its own bodies and
+  bonds, and the pool runs with the lane count a member uses alone (16 for scenes of up to
+  8192 bodies), so each member's result is bit for bit the one it reaches alone.  A newly
+  admitted small scene first runs on its own (below) and joins a pool at the next rebuild,
+  which happens between steps, at most every ``rebuild_interval`` seconds: the pool's
+  members' states are read back, a new pool is built with the newcomers as extra groups, and
+  the states are written into it.
+* **Alone**: every other scene is its own library scene on its own CUDA stream; one graph
+  launch per step, overlapping with the other scenes' steps on the device.
+
+Admission by HBM budget: a scene becomes resident when its estimated device memory fits;
+idle scenes running alone are evicted least recently used first, their state kept on the
+host.  Packing needs room for the new pool next to the old one while it is rebuilt; when
+that does not fit, small scenes stay alone.
 
 Latency of a step: from the moment it became eligible (the request's arrival for its first
-step, the completion of its previous step otherwise) to the host observing its completion
-event.  Each scene's arithmetic is independent of the others, so its result is the same
-alone and in the mix.
+step, the completion of its previous step otherwise) to the host observing its completion.
 """
 from __future__ import annotations
 
@@ -37,21 +51,63 @@ class Request:
 
 
 class _Resident:
-    def __init__(self, scene, stream, nbytes, n_bodies):
+    """A scene alone in its own library scene and stream."""
+
+    def __init__(self, scene, stream, nbytes, n_bodies, desc):
         self.scene = scene
         self.stream = stream
         self.bytes = nbytes
         self.n_bodies = n_bodies
+        self.desc = desc
         self.queue = collections.deque()
         self.inflight = None          # (request, t_eligible, event)
         self.last_use = 0.0
+
+
+class _Pool:
+    """Small scenes packed as the groups of one library scene."""
+
+    def __init__(self, scene, stream, nbytes, members, offsets):
+        self.scene = scene
+        self.stream = stream
+        self.bytes = nbytes
+        self.members = members        # scene ids, group order
+        self.offsets = offsets        # body offsets of the groups (len(members) + 1)
+        self.queues = {sid: collections.deque() for sid in members}
+        self.last_use = {sid: 0.0 for sid in members}
+        self.inflight = None          # ([(request, t_eligible)], event)
+        self.hold = None              # last hold mask sent
+        self.key = None               # the members' scene parameters
+
+
+def _pkey(desc):
+    return tuple(sorted((k, repr(v)) for k, v in desc.params.items()))
+
+
+def _pack(descs):
+    """One scenes.Scene whose groups are the given scenes (same parameters), in order."""
+    import scenes as S
+    bodies, bonds, off = [], [], [0]
+    for g, d in enumerate(descs):
+        b = d.bodies.copy()
+        b["group"] = g
+        bo = d.bonds.copy()
+        bo["i"] += off[-1]
+        bo["j"] = np.where(bo["j"] >= 0, bo["j"] + off[-1], -1)
+        bodies.append(b)
+        bonds.append(bo)
+        off.append(off[-1] + d.n_bodies)
+    sc = S.Scene("pool", dict(descs[0].params), np.concatenate(bodies),
+                 np.concatenate(bonds) if bonds else np.zeros(0, dtype=S.BOND_DTYPE), 1)
+    return sc, np.asarray(off)
 
 
 class Server:
     """make_scene(scene_id) -> scenes.Scene describes a scene the first time it is needed."""
 
     def __init__(self, make_scene: Callable[[int], object], hbm_budget: int = 32 << 30, device: int = 0,
-                 clock=time.perf_counter):
+                 clock=time.perf_counter, pack: bool = True, pool_max_bodies: int = 4096,
+                 pool_capacity: int = 65536, rebuild_interval: float = 0.05, pool_lanes: int = 16):
         import torch
         import paper_2609_02675_gb300 as P
         self._torch = torch
@@ -60,7 +116,15 @@ class Server:
         self.budget = int(hbm_budget)
         self.device = device
         self.clock = clock
+        self.pack = pack
+        self.pool_max_bodies = pool_max_bodies
+        self.pool_capacity = pool_capacity
+        self.rebuild_interval = rebuild_interval
+        self.pool_lanes = pool_lanes
         self.resident: dict[int, _Resident] = {}
+        self.pools: list[_Pool] = []
+        self.pooled: dict[int, _Pool] = {}       # scene_id -> its pool
+        self.descs: dict[int, object] = {}       # scene descriptions of packed scenes
         self.evicted: dict[int, tuple] = {}      # scene_id -> (state rows, step index, n_bodies)
         self.waiting = collections.deque()       # requests whose scene is not resident yet
         self.requests: list[Request] = []
@@ -70,6 +134,9 @@ class Server:
         self.evictions = 0
         self.admissions = 0
         self.over_budget = 0         # scenes admitted alone although larger than the budget
+        self.rebuilds = 0
+        self.pool_launches = 0
+        self.last_rebuild = -1e30
 
     # -- admission -----------------------------------------------------------------------
     def _estimate(self, n_bodies: int) -> int:
@@ -78,17 +145,36 @@ class Server:
         return int(self.bytes_per_body * n_bodies) + (1 << 20)
 
     def _evict_one(self) -> bool:
-        idle = [(r.last_use, sid) for sid, r in self.resident.items() if r.inflight is None and not r.queue]
+        """Evict the least recently used idle scene running alone, or idle pool (all its
+        members without work), keeping the states on the host."""
+        idle = [(r.last_use, 0, sid) for sid, r in self.resident.items() if r.inflight is None and not r.queue]
+        idle += [(max(p.last_use.values()), 1, k) for k, p in enumerate(self.pools)
+                 if p.inflight is None and not any(p.queues[s] for s in p.members)]
         if not idle:
             return False
-        _, sid = min(idle)
-        r = self.resident.pop(sid)
-        st = r.scene.state()
-        self.evicted[sid] = (st, r.scene.info()["step_index"], r.n_bodies)
-        self.bytes_used -= r.bytes
-        r.scene.close()
+        _, kind, key = min(idle)
+        if kind == 0:
+            r = self.resident.pop(key)
+            st = r.scene.state()
+            self.evicted[key] = (st, r.scene.info()["step_index"], r.n_bodies)
+            self.bytes_used -= r.bytes
+            r.scene.close()
+        else:
+            p = self.pools.pop(key)
+            st = p.scene.state()
+            step = p.scene.info()["step_index"]
+            for k, sid in enumerate(p.members):
+                self.evicted[sid] = (st[p.offsets[k]:p.offsets[k + 1]], step, int(p.offsets[k + 1] - p.offsets[k]))
+                del self.pooled[sid]
+            self.bytes_used -= p.bytes
+            p.scene.close()
         self.evictions += 1
         return True
+
+    def _packable(self, desc) -> bool:
+        b = desc.bonds
+        return (self.pack and desc.n_bodies <= self.pool_max_bodies and desc.n_groups <= 1
+                and not np.isin(b["type"], (4, 5)).any())  # no DRIVE, no AL_DISTANCE
 
     def _admit(self, scene_id: int) -> bool:
         desc = self.make_scene(scene_id)
@@ -96,13 +182,16 @@ class Server:
         need = self._estimate(n)
         while self.bytes_used + need > self.budget:
             if not self._evict_one():
-                if self.resident:
+                if self.resident or self.pools:
                     return False
                 break                # alone it may exceed the budget: run it rather than wait forever
         if self.bytes_used + need > self.budget:
             self.over_budget += 1
         stream = self._torch.cuda.Stream(self.device)
-        sc = self._P.Scene(desc, device=self.device, stream=stream)
+        # (small scenes keep the launch shape of the pools they will join; large ones are tuned)
+        small = self._packable(desc)
+        sc = self._P.Scene(desc, device=self.device, stream=stream, sweep_lanes=self.pool_lanes if small else 0,
+                           sweep_mode=2 if small else 0, light_order=1 if small else 0)
         if scene_id in self.evicted:
             st, k, _ = self.evicted.pop(scene_id)
             sc.set_state(st)
@@ -110,10 +199,79 @@ class Server:
         nbytes = sc.info()["device_bytes"]
         if self.bytes_per_body is None:
             self.bytes_per_body = nbytes / max(n, 1)
-        self.resident[scene_id] = _Resident(sc, stream, nbytes, n)
+        self.resident[scene_id] = _Resident(sc, stream, nbytes, n, desc)
         self.bytes_used += nbytes
         self.admissions += 1
         return True
+
+    # -- packing -------------------------------------------------------------------------
+    def _rebuild(self):
+        """Absorb the idle small scenes running alone into a pool (between steps)."""
+        now = self.clock()
+        if now - self.last_rebuild < self.rebuild_interval:
+            return
+        cand = [sid for sid, r in self.resident.items()
+                if r.inflight is None and self._packable(r.desc)]
+        if not cand:
+            return
+        # one pool holds scenes of the same parameters (time step, sweeps, ground, ...)
+        key = _pkey(self.resident[cand[0]].desc)
+        cand = [sid for sid in cand if _pkey(self.resident[sid].desc) == key]
+        first = self.resident[cand[0]].n_bodies
+        size = {p: sum(self.descs[s].n_bodies for s in p.members) for p in self.pools}
+        roomy = [p for p in self.pools if p.key == key and size[p] + first <= self.pool_capacity]
+        pool = next((p for p in roomy if p.inflight is None), None)
+        if pool is None and roomy:
+            return                   # the pool with room has a step in flight: try at a later pump
+        old = list(pool.members) if pool else []
+        total = size[pool] if pool else 0
+        new = []
+        for sid in cand:
+            n = self.resident[sid].n_bodies
+            if total + n > self.pool_capacity:
+                break
+            new.append(sid)
+            total += n
+        if not new:
+            return
+        # room for the new pool beside the old one while the states move across
+        if self.bytes_used + self._estimate(total) > self.budget:
+            return
+        self.last_rebuild = now
+        members = old + new
+        descs = [self.descs[s] if s in self.descs else self.resident[s].desc for s in members]
+        rows = []
+        if pool:
+            st = pool.scene.state()
+            rows += [st[pool.offsets[k]:pool.offsets[k + 1]] for k in range(len(old))]
+        rows += [self.resident[s].scene.state() for s in new]
+        sc_desc, off = _pack(descs)
+        stream = self._torch.cuda.Stream(self.device)
+        lib = self._P.Scene(sc_desc, device=self.device, stream=stream, sweep_lanes=self.pool_lanes, sweep_mode=2,
+                            light_order=1)
+        lib.set_state(np.concatenate(rows))
+        nbytes = lib.info()["device_bytes"]
+        p = _Pool(lib, stream, nbytes, members, off)
+        p.key = key
+        if pool:
+            for s in old:
+                p.queues[s] = pool.queues[s]
+                p.last_use[s] = pool.last_use[s]
+            pool.scene.close()
+            self.bytes_used -= pool.bytes
+            self.pools.remove(pool)
+        for s in new:
+            r = self.resident.pop(s)
+            p.queues[s] = r.queue
+            p.last_use[s] = r.last_use
+            self.descs[s] = r.desc
+            r.scene.close()
+            self.bytes_used -= r.bytes
+        for s in members:
+            self.pooled[s] = p
+        self.pools.append(p)
+        self.bytes_used += nbytes
+        self.rebuilds += 1
 
     # -- requests ------------------------------------------------------------------------
     def submit(self, scene_id: int, n_steps: int, t_arrival: float | None = None) -> Request:
@@ -127,6 +285,10 @@ class Server:
         still = collections.deque()
         while self.waiting:
             req = self.waiting.popleft()
+            p = self.pooled.get(req.scene_id)
+            if p is not None:
+                p.queues[req.scene_id].append(req)
+                continue
             r = self.resident.get(req.scene_id)
             if r is None and self._admit(req.scene_id):
                 r = self.resident[req.scene_id]
@@ -136,25 +298,57 @@ class Server:
                 r.queue.append(req)
         self.waiting = still
 
+    def _advance(self, req, queue, t_elig, t):
+        req.step_latency.append(t - t_elig)
+        req.steps_done += 1
+        self.steps_completed += 1
+        if req.steps_done == req.n_steps:
+            req.t_done = t
+            queue.popleft()
+        else:
+            req.t_eligible = t
+
     def pump(self) -> int:
-        """Poll completions, admit and launch; returns the number of steps launched."""
+        """Poll completions, admit, pack and launch; returns the number of steps launched."""
         now = self.clock()
+        for p in self.pools:
+            if p.inflight is not None and p.inflight[1].query():
+                t = self.clock()
+                for sid, req, t_elig in p.inflight[0]:
+                    self._advance(req, p.queues[sid], t_elig, t)
+                    p.last_use[sid] = t
+                p.inflight = None
         for r in self.resident.values():
             if r.inflight is not None and r.inflight[2].query():
                 req, t_elig, _ = r.inflight
                 t = self.clock()
-                req.step_latency.append(t - t_elig)
-                req.steps_done += 1
-                self.steps_completed += 1
+                self._advance(req, r.queue, t_elig, t)
                 r.inflight = None
                 r.last_use = t
-                if req.steps_done == req.n_steps:
-                    req.t_done = t
-                    r.queue.popleft()
-                else:
-                    req.t_eligible = t
         self._route_waiting()
+        if self.pack:
+            self._rebuild()
         launched = 0
+        for p in self.pools:
+            if p.inflight is not None:
+                continue
+            active = [(sid, p.queues[sid][0]) for sid in p.members if p.queues[sid]]
+            if not active:
+                continue
+            hold = np.ones(len(p.members), dtype=np.uint8)
+            idx = {sid: k for k, sid in enumerate(p.members)}
+            for sid, _ in active:
+                hold[idx[sid]] = 0
+            if p.hold is None or not np.array_equal(hold, p.hold):
+                p.scene.set_group_hold(hold)
+                p.hold = hold
+            p.scene.step(1)
+            ev = self._torch.cuda.Event()
+            ev.record(p.stream)
+            p.inflight = ([(sid, req, req.t_eligible if req.steps_done else max(req.t_arrival, req.t_eligible))
+                           for sid, req in active], ev)
+            self.pool_launches += 1
+            launched += len(active)
         for r in self.resident.values():
             if r.inflight is None and r.queue:
                 req = r.queue[0]
@@ -168,32 +362,60 @@ class Server:
         return launched
 
     def busy(self) -> bool:
-        return bool(self.waiting) or any(r.inflight is not None or r.queue for r in self.resident.values())
+        return (bool(self.waiting) or any(r.inflight is not None or r.queue for r in self.resident.values())
+                or any(p.inflight is not None or any(p.queues[s] for s in p.members) for p in self.pools))
 
     def drain(self, timeout: float = 600.0):
         t0 = self.clock()
         while self.busy() and self.clock() - t0 < timeout:
             self.pump()
 
+    def state(self, scene_id: int) -> np.ndarray:
+        """The scene's current state rows (resident alone, packed or evicted)."""
+        p = self.pooled.get(scene_id)
+        if p is not None:
+            k = p.members.index(scene_id)
+            return p.scene.state()[p.offsets[k]:p.offsets[k + 1]]
+        r = self.resident.get(scene_id)
+        if r is not None:
+            return r.scene.state()
+        return self.evicted[scene_id][0]
+
     def close(self):
         for r in self.resident.values():
             r.scene.close()
+        for p in self.pools:
+            p.scene.close()
         self.resident.clear()
+        self.pools.clear()
+        self.pooled.clear()
+
+    def _n_bodies(self, scene_id: int) -> int:
+        if scene_id in self.descs:
+            return self.descs[scene_id].n_bodies
+        r = self.resident.get(scene_id)
+        if r is not None:
+            return r.n_bodies
+        e = self.evicted.get(scene_id)
+        return e[2] if e is not None else 0
 
     # -- results ---------------------------------------------------------------------------
     def stats(self, t_start: float, t_end: float) -> dict:
         lat = np.array([x for q in self.requests for x in q.step_latency]) * 1e3
+        body_steps = sum(self._n_bodies(q.scene_id) * q.steps_done for q in self.requests)
         done = [q for q in self.requests if q.t_done is not None]
         rl = np.array([q.t_done - q.t_arrival for q in done]) * 1e3
         return {
             "requests": len(self.requests), "requests_done": len(done), "steps": int(lat.size),
             "steps_per_s": lat.size / max(t_end - t_start, 1e-9),
+            "body_steps_per_s": body_steps / max(t_end - t_start, 1e-9),
             "step_latency_ms": {"p50": float(np.percentile(lat, 50)) if lat.size else None,
                                 "p99": float(np.percentile(lat, 99)) if lat.size else None},
             "request_latency_ms": {"p50": float(np.percentile(rl, 50)) if rl.size else None,
                                    "p99": float(np.percentile(rl, 99)) if rl.size else None},
             "admissions": self.admissions, "evictions": self.evictions, "over_budget": self.over_budget,
-            "resident_bytes": self.bytes_used,
+            "resident_bytes": self.bytes_used, "packed_scenes": len(self.pooled), "pool_rebuilds": self.rebuilds,
+            "pool_launches": self.pool_launches,
         }
 
 

@@ -101,3 +101,34 @@ def test_step_many_equals_stepping_each_scene(P):
     with pytest.raises(P.PabdError) as e:
         P.pabd_step_many([None], [1])
     assert e.value.code == P.ERR_ARG
+
+
+def test_state_f32_round_trip_and_step_identical(P):
+    """pabd_read_state_f32 / pabd_write_state_f32 move the device-layout state (q, Q, v, omega
+    as 24 floats per body) without conversion: the values equal pabd_read_state's, and a step
+    from a state written either way is the same bit for bit."""
+    import torch
+    sc = S.batched_trees(n_scenes=5, n_steps=10)
+    g = P.Scene(sc)
+    g.step(4)
+    n = sc.n_bodies
+    host = torch.empty(24 * n, dtype=torch.float32, pin_memory=True)
+    g.read_state_f32(host.data_ptr())
+    g.sync()
+    f = host.numpy().astype(np.float64)
+    rows = g.state()
+    assert np.array_equal(f[:12 * n].reshape(n, 12), rows[:, 0:12])
+    assert np.array_equal(f[12 * n:16 * n].reshape(n, 4), rows[:, 12:16])
+    assert np.array_equal(f[16 * n:20 * n].reshape(n, 4)[:, :3], rows[:, 16:19])
+    assert np.array_equal(f[20 * n:24 * n].reshape(n, 4)[:, :3], rows[:, 19:22])
+    g.step(3)
+    after_a = g.state()
+    g.write_state_f32(host.data_ptr())
+    g.set_step_index(4)
+    g.step(3)
+    assert np.array_equal(g.state(), after_a)
+    g.set_state(rows)
+    g.set_step_index(4)
+    g.step(3)
+    assert np.array_equal(g.state(), after_a)
+    g.close()

@@ -1,0 +1,93 @@
+"""Per-result error of the single-precision path against the FP64 oracle, per workload and
+precision policy: the largest per-step position error over teacher-forced steps (each GPU
+step starts from the oracle's state), as a fraction of the scene diagonal.
+
+Policies: 0 FP32 only; 1 (default) FP32 bonds and solves, with the ill-conditioned or stiffly
+jointed bodies' sums compensated and their 4x4 systems factored in double-float; 2 the same
+bodies summed and factored in FP64.  Policies 1 and 2 must meet the 1e-5 tolerance on every
+workload; policy 0 is reported.  A step whose error exceeds the tolerance only because a
+contact at its activation threshold switched branch is measured under the activation
+envelope (the oracle at the threshold moved by 8 units of single-precision rounding); a body
+beyond it next to a contact within that distance of the threshold is counted apart (the
+activation reading of the design notes).
+The table is printed (pytest -s) in the form quoted in the design notes."""
+import numpy as np
+import pytest
+
+import oracle as O
+import scenes as S
+from tests.gpu_helpers import REL_TOL, rel_err, threshold_rule_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2609_02675_gb300 as mod
+    return mod
+
+
+CASES = [
+    ("chain pendulum, 7 stiff spherical joints", lambda: S.chain_pendulum(n_steps=30), 30),
+    ("chain joined at opposite corners (ill-conditioned)", lambda: S.chain_pendulum(diagonal=True, n_steps=30), 30),
+    ("box pile 6^3 (contacts, friction)", lambda: S.box_pile(nx=6, ny=6, nz=6, spacing=2.3, n_steps=90), 90),
+    ("24 batched trees (joints, elastic bonds, ground)", lambda: S.batched_trees(n_scenes=24, n_steps=40), 40),
+    ("quadruped on a 12x2x12 bed + 16-segment rod", lambda: S.quadruped_bed_rod(bed=(12, 2, 12), n_rod=16,
+                                                                                n_steps=30), 30),
+    ("E5 mass-ratio stack", lambda: S.mass_ratio_stack(n_steps=60), 60),
+    ("E6 two-box spring", lambda: S.two_box_spring(n_steps=30), 30),
+    ("E7 11x11 spring net", lambda: S.spring_net(n_steps=30), 30),
+    ("three-box chain of augmented Lagrangian bonds", lambda: S.mass_ratio_chain(n=3, ratio=1.0, n_steps=10), 10),
+]
+
+
+def _worst(P, sc, policy, states, al_states):
+    he = np.ascontiguousarray(sc.bodies["he"], dtype=np.float64)
+    g = P.Scene(sc, precision_policy=policy)
+    worst, accepted = 0.0, []
+    for k in range(len(states) - 1):
+        st0, k0 = states[k]
+        g.set_state(st0)
+        g.set_step_index(k0)
+        if al_states is not None:
+            g.set_bond_state(al_states[k])
+        g.step(1)
+        a = g.state()
+        b = states[k + 1][0]
+        e = rel_err(a, b, he)
+        if e >= REL_TOL and sc.params["has_ground"]:
+            e, acc = threshold_rule_err(sc, st0, k0, a, he, O)
+            accepted += [(k0, x, ex) for x, ex in acc]
+        worst = max(worst, e)
+    g.close()
+    return worst, accepted
+
+
+def test_precision_policy_error_table(P):
+    rows = []
+    for name, make, n in CASES:
+        sc = make()
+        ref = O.OracleScene(sc)
+        has_al = bool((sc.bonds["type"] == S.AL_DISTANCE).any()) if len(sc.bonds) else False
+        states, al_states = [(ref.state(), ref.step_index)], ([ref.al_state()] if has_al else None)
+        for _ in range(n):
+            ref.step(1)
+            states.append((ref.state(), ref.step_index))
+            if has_al:
+                al_states.append(ref.al_state())
+        res = {pol: _worst(P, sc, pol, states, al_states) for pol in (0, 1, 2)}
+        rows.append((name, sc.n_bodies, n, {p: r[0] for p, r in res.items()}, {p: r[1] for p, r in res.items()}))
+    print("\n| workload | bodies | steps | policy 0 (FP32) | policy 1 (default) | policy 2 (FP64) |")
+    print("|---|---:|---:|---:|---:|---:|")
+    for name, nb, n, e, acc in rows:
+        note = "".join(f" ({len(acc[p])} at the threshold)" if acc[p] else "" for p in (1,))
+        print(f"| {name} | {nb} | {n} | {e[0]:.1e} | {e[1]:.1e}{note} | {e[2]:.1e} |")
+    for name, nb, n, e, acc in rows:
+        assert e[1] < REL_TOL and e[2] < REL_TOL, (name, e)
+        for p in (1, 2):
+            assert len(acc[p]) <= 3 and all(x < 1e-3 for _, _, x in acc[p]), (name, p, acc[p])
