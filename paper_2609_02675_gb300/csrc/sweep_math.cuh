@@ -293,16 +293,44 @@ __device__ __forceinline__ void sys_init(Sys<T>& s, float4 mass, const float* dc
     }
 }
 
-// the same initial system for the compensated accumulator, formed in double-float
+// the same initial system for the compensated accumulator: every product formed exactly by
+// TwoProd (m x_s as a double-word), every sum by TwoSum, the errors kept in the accumulator
 __device__ __forceinline__ void sys_init(Sys<ca>& s, float4 mass, const float* dc, const float* dA, const float* xs) {
-    Sys<df> t;
-    sys_init(t, mass, dc, dA, xs);
+    const float m = mass.x;
+    const float pi[3] = {mass.y, mass.z, mass.w};
+    df mx[3];
 #pragma unroll
-    for (int k = 0; k < 10; ++k) s.g[k] = ca_of(t.g[k]);
+    for (int a = 0; a < 3; ++a) mx[a] = two_prod(m, xs[a]);
+    s.g[0] = ca(m);
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int a = 0; a < 3; ++a) s.g[1 + a] = ca(-mx[a].hi, -mx[a].lo);
+    int k = 4;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) s.r[r][k] = ca_of(t.r[r][k]);
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = a; b < 3; ++b, ++k) {
+            const df p = two_prod(mx[a].hi, xs[b]);
+            const float lo = __fmaf_rn(mx[a].lo, xs[b], p.lo);
+            if (a == b) {
+                const df t = two_sum(pi[a], p.hi);
+                s.g[k] = ca(t.hi, __fadd_rn(t.lo, lo));
+            } else {
+                s.g[k] = ca(p.hi, lo);
+            }
+        }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const df r0 = two_prod(m, dc[c]);
+        s.r[0][c] = ca(r0.hi, r0.lo);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const df p1 = two_prod(pi[a], dA[3 * c + a]);
+            const df p2 = two_prod(mx[a].hi, dc[c]);
+            const float lo2 = __fmaf_rn(mx[a].lo, dc[c], p2.lo);
+            const df t = two_sum(p1.hi, -p2.hi);
+            s.r[1 + a][c] = ca(t.hi, __fadd_rn(t.lo, __fsub_rn(p1.lo, lo2)));
+        }
+    }
 }
 
 // the exact difference a - b of two floats in the extended type

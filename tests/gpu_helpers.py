@@ -130,11 +130,12 @@ def threshold_rule_err(sc, st0, k0, st_gpu, he, oracle_mod, ulps: float = 8.0):
 
     Each body is compared with the closest of the oracle's results at the activation
     thresholds dhat and dhat +- delta (delta = `ulps` units of single-precision rounding at the
-    scene's scale).  A body still beyond the tolerance is accepted only if it, or a body it
-    touches through a contact, had a contact within delta of the threshold during the step
-    (the oracle's activation margin): several such contacts switching in different sweeps are
-    reproduced by no single shift.  Returns (max error over the other bodies, [(body, error)]
-    of the accepted ones)."""
+    scene's scale).  A body still beyond the tolerance is accepted only if a body at most two
+    links away -- links being this step's contacts and the scene's user bonds -- had a contact
+    within delta of the threshold during the step (the oracle's activation margin): several
+    such contacts switching in different sweeps are reproduced by no single shift, and the
+    sweeps carry a switch through contacts and stiff joints to the neighbours.  Returns (max
+    error over the other bodies, [(body, error)] of the accepted ones)."""
     ref = oracle_mod.OracleScene(sc)
     ref.set_state(st0)
     ref.step_index = k0
@@ -155,15 +156,18 @@ def threshold_rule_err(sc, st0, k0, st_gpu, he, oracle_mod, ulps: float = 8.0):
         return float(best.max()) if best.size else 0.0, []
     margin = ref.activation_margin()
     cm = ref.contacts()[0]
-    touch = {}
-    for i, j in zip(cm[:, 1], cm[:, 2]):
+    links = {}
+    pairs = list(zip(cm[:, 1], cm[:, 2])) + (list(zip(sc.bonds["i"], sc.bonds["j"])) if len(sc.bonds) else [])
+    for i, j in pairs:
         if j >= 0:
-            touch.setdefault(int(i), []).append(int(j))
-            touch.setdefault(int(j), []).append(int(i))
+            links.setdefault(int(i), set()).add(int(j))
+            links.setdefault(int(j), set()).add(int(i))
     accepted = []
     keep = np.ones(best.shape, dtype=bool)
     for x in bad:
-        near = min([margin[x]] + [margin[y] for y in touch.get(int(x), [])])
+        ring = {int(x)} | links.get(int(x), set())
+        ring = ring.union(*[links.get(y, set()) for y in list(ring)])
+        near = min(margin[y] for y in ring)
         if near < delta:
             accepted.append((int(x), float(best[x])))
             keep[x] = False

@@ -222,12 +222,12 @@ def test_quadruped_full_size_landed_step(P):
     """The full quadruped scene (13-body driven quadruped, 50 000-cube bed, 64-segment rod) in
     the bench's launch configuration, while the bed's layers land on each other (oracle steps
     4..7, teacher-forced).  Pairs and contacts are bit-exact.  Positions meet the tolerance
-    for every body outright or under the activation envelope, except bodies at a contact whose
-    gap sits within 8 units of single-precision rounding of the threshold -- in the body itself
-    or in a body it touches -- over some sweep of the step (the oracle's activation margin):
-    with hundreds of thousands of contacts landing, a body can have several of them switch in
-    different sweeps, which no single shift of the threshold reproduces.  Those must be few,
-    and stay within 1e-3 of the scene diagonal."""
+    for every body outright or under the activation envelope, except bodies within two links
+    (contacts or joints) of a contact whose gap sat within 8 units of single-precision
+    rounding of the threshold during the step (the oracle's activation margin): with hundreds
+    of thousands of contacts landing, a body can have several of them switch in different
+    sweeps, which no single shift of the threshold reproduces.  Those must be few, and stay
+    within 1e-3 of the scene diagonal."""
     sc = S.quadruped_bed_rod()
     ref = O.OracleScene(sc)
     ref.step(4)
