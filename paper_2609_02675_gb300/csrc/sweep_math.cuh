@@ -251,7 +251,10 @@ __device__ __forceinline__ ca shfl_xor(unsigned mask, ca v, int o) {
     return ca{__shfl_xor_sync(mask, v.s, o), __shfl_xor_sync(mask, v.e, o)};
 }
 __device__ __forceinline__ ca ca_of(df v) { return ca{v.hi, v.lo}; }
-__device__ __forceinline__ df ca_to_df(ca v) { return two_sum(v.s, v.e); }
+// the accumulated value as a double-word for the factorisation, without renormalising: the
+// error sum is far below the float sum (a few rounding errors of the partial sums), and the
+// double-word operations that consume it carry both parts
+__device__ __forceinline__ df ca_to_df(ca v) { return df(v.s, v.e, 0); }
 
 // the extended system as it is factored: double-float from the compensated sums, FP64 as
 // summed under policy 2
@@ -489,18 +492,28 @@ __device__ __forceinline__ void sys_solve_ldl(const Sys<df>& s, df out[4][3]) {
     const df l32 = u32 * r2;
     const df d3 = fma_dd(-l32, u32, fma_dd(-l31, u31, fma_dd(m30, g[3], g[9])));
     const df r3 = recip_dd(d3);
+    // the three right-hand sides through one copy of the substitution code (a short
+    // instruction footprint): each pass solves column 0 and rotates the columns left, the
+    // solution entering as column 2, so after three passes the columns hold the solutions in order
+    df c0[4], c1[4], c2[4];
 #pragma unroll
+    for (int r = 0; r < 4; ++r) { c0[r] = s.r[r][0]; c1[r] = s.r[r][1]; c2[r] = s.r[r][2]; }
+#pragma unroll 1
     for (int k = 0; k < 3; ++k) {
-        const df y0 = s.r[0][k];
-        const df y1 = fma_dd(m10, y0, s.r[1][k]);
-        const df y2 = fma_dd(-l21, y1, fma_dd(m20, y0, s.r[2][k]));
-        const df y3 = fma_dd(-l32, y2, fma_dd(-l31, y1, fma_dd(m30, y0, s.r[3][k])));
+        const df y0 = c0[0];
+        const df y1 = fma_dd(m10, y0, c0[1]);
+        const df y2 = fma_dd(-l21, y1, fma_dd(m20, y0, c0[2]));
+        const df y3 = fma_dd(-l32, y2, fma_dd(-l31, y1, fma_dd(m30, y0, c0[3])));
         const df x3 = y3 * r3;
         const df x2 = fma_dd(-l32, x3, y2 * r2);
         const df x1 = fma_dd(-l31, x3, fma_dd(-l21, x2, y1 * r1));
         const df x0 = fma_dd(m30, x3, fma_dd(m20, x2, fma_dd(m10, x1, y0 * r0)));
-        out[0][k] = x0; out[1][k] = x1; out[2][k] = x2; out[3][k] = x3;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) { c0[r] = c1[r]; c1[r] = c2[r]; }
+        c2[0] = x0; c2[1] = x1; c2[2] = x2; c2[3] = x3;
     }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) { out[r][0] = c0[r]; out[r][1] = c1[r]; out[r][2] = c2[r]; }
 }
 
 // the extended system's solve: LDL^T in double-float, Cholesky in FP64
