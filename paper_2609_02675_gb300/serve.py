@@ -8,17 +8,26 @@ pump instead of waiting for them to finish.
 Two kinds of resident scene:
 
 * **Packed** (scenes of at most ``pool_max_bodies`` bodies without drives or augmented
-  Lagrangian bonds): the small scenes are the groups of one library scene, a *pool*.  One
-  graph launch steps every member that has work; the members without work are held still for
-  that step (``pabd_set_group_hold``).  A group's step depends only on its own bodies and
-  bonds, and the pool runs with the lane count a member uses alone (16 for scenes of up to
-  8192 bodies), so each member's result is bit for bit the one it reaches alone.  A newly
+  Lagrangian bonds): such scenes are the groups of one library scene, a *pool*.  One graph
+  launch steps every member that has work; the members without work are held still for that
+  step (``pabd_set_group_hold``).  A group's step depends only on its own bodies and bonds, and
+  a pool holds scenes that use the same lane count alone (the library's choice for the scene's
+  size: 16 up to 8192 bodies, 8 up to 16384, ...) and runs with it, so each member's result is
+  bit for bit the one it reaches alone.  Small and mid-size scenes are bound by launches and
+  latency rather than by the GPU's throughput, so stepping many in one set of launches raises
+  the steps served per second.  A newly
   admitted small scene first runs on its own (below) and joins a pool at the next rebuild,
   which happens between steps, at most every ``rebuild_interval`` seconds: the pool's
   members' states are read back, a new pool is built with the newcomers as extra groups, and
   the states are written into it.
 * **Alone**: every other scene is its own library scene on its own CUDA stream; one graph
   launch per step, overlapping with the other scenes' steps on the device.
+
+Every scene (and pool) keeps up to ``depth`` steps enqueued on the device, so its next step
+never waits for the host to observe the last one.  Packed and small scenes run on
+high-priority streams: when the device is oversubscribed, the GPU's scheduler takes their
+short kernels before the large scenes' ones, which keeps small steps fast and raises the
+steps served per second, at the expense of the large scenes' latency.
 
 Admission by HBM budget: a scene becomes resident when its estimated device memory fits;
 idle scenes running alone are evicted least recently used first, their state kept on the
@@ -45,6 +54,7 @@ class Request:
     n_steps: int
     t_arrival: float
     steps_done: int = 0
+    launched: int = 0             # steps enqueued on the device so far
     t_eligible: float = 0.0       # when the next step became launchable
     t_done: float | None = None
     step_latency: list = field(default_factory=list)
@@ -60,7 +70,7 @@ class _Resident:
         self.n_bodies = n_bodies
         self.desc = desc
         self.queue = collections.deque()
-        self.inflight = None          # (request, t_eligible, event)
+        self.inflight = collections.deque()   # (request, event) per enqueued step, in order
         self.last_use = 0.0
 
 
@@ -75,7 +85,7 @@ class _Pool:
         self.offsets = offsets        # body offsets of the groups (len(members) + 1)
         self.queues = {sid: collections.deque() for sid in members}
         self.last_use = {sid: 0.0 for sid in members}
-        self.inflight = None          # ([(request, t_eligible)], event)
+        self.inflight = collections.deque()   # ([(scene id, request)], event) per enqueued step
         self.hold = None              # last hold mask sent
         self.key = None               # the members' scene parameters
 
@@ -106,8 +116,8 @@ class Server:
     """make_scene(scene_id) -> scenes.Scene describes a scene the first time it is needed."""
 
     def __init__(self, make_scene: Callable[[int], object], hbm_budget: int = 32 << 30, device: int = 0,
-                 clock=time.perf_counter, pack: bool = True, pool_max_bodies: int = 4096,
-                 pool_capacity: int = 65536, rebuild_interval: float = 0.05, pool_lanes: int = 16):
+                 clock=time.perf_counter, pack: bool = True, pool_max_bodies: int = 8192,
+                 pool_capacity: int = 65536, rebuild_interval: float = 0.1, depth: int = 4):
         import torch
         import paper_2609_02675_gb300 as P
         self._torch = torch
@@ -120,7 +130,7 @@ class Server:
         self.pool_max_bodies = pool_max_bodies
         self.pool_capacity = pool_capacity
         self.rebuild_interval = rebuild_interval
-        self.pool_lanes = pool_lanes
+        self.depth = depth
         self.resident: dict[int, _Resident] = {}
         self.pools: list[_Pool] = []
         self.pooled: dict[int, _Pool] = {}       # scene_id -> its pool
@@ -137,6 +147,7 @@ class Server:
         self.rebuilds = 0
         self.pool_launches = 0
         self.last_rebuild = -1e30
+        self.pending = None          # (key, pool, scene ids) of a rebuild waiting for their steps to drain
 
     # -- admission -----------------------------------------------------------------------
     def _estimate(self, n_bodies: int) -> int:
@@ -147,9 +158,9 @@ class Server:
     def _evict_one(self) -> bool:
         """Evict the least recently used idle scene running alone, or idle pool (all its
         members without work), keeping the states on the host."""
-        idle = [(r.last_use, 0, sid) for sid, r in self.resident.items() if r.inflight is None and not r.queue]
+        idle = [(r.last_use, 0, sid) for sid, r in self.resident.items() if not r.inflight and not r.queue]
         idle += [(max(p.last_use.values()), 1, k) for k, p in enumerate(self.pools)
-                 if p.inflight is None and not any(p.queues[s] for s in p.members)]
+                 if not p.inflight and not any(p.queues[s] for s in p.members)]
         if not idle:
             return False
         _, kind, key = min(idle)
@@ -187,56 +198,75 @@ class Server:
                 break                # alone it may exceed the budget: run it rather than wait forever
         if self.bytes_used + need > self.budget:
             self.over_budget += 1
-        stream = self._torch.cuda.Stream(self.device)
         # (small scenes keep the launch shape of the pools they will join; large ones are tuned)
         small = self._packable(desc)
-        sc = self._P.Scene(desc, device=self.device, stream=stream, sweep_lanes=self.pool_lanes if small else 0,
-                           sweep_mode=2 if small else 0, light_order=1 if small else 0)
+        stream = self._torch.cuda.Stream(self.device, priority=-1 if small else 0)
+        sc = self._P.Scene(desc, device=self.device, stream=stream, sweep_mode=2 if small else 0,
+                           light_order=1 if small else 0)
         if scene_id in self.evicted:
             st, k, _ = self.evicted.pop(scene_id)
             sc.set_state(st)
             sc.set_step_index(k)
-        nbytes = sc.info()["device_bytes"]
+        info = sc.info()
+        nbytes = info["device_bytes"]
         if self.bytes_per_body is None:
             self.bytes_per_body = nbytes / max(n, 1)
         self.resident[scene_id] = _Resident(sc, stream, nbytes, n, desc)
+        self.resident[scene_id].lanes = info["sweep_lanes"]
         self.bytes_used += nbytes
         self.admissions += 1
         return True
 
     # -- packing -------------------------------------------------------------------------
     def _rebuild(self):
-        """Absorb the idle small scenes running alone into a pool (between steps)."""
+        """Absorb small scenes running alone into a pool, between steps: once a rebuild is
+        due, the chosen scenes and the pool they join stop enqueueing steps; when their
+        enqueued steps have completed the pool is rebuilt with them."""
         now = self.clock()
-        if now - self.last_rebuild < self.rebuild_interval:
-            return
-        cand = [sid for sid, r in self.resident.items()
-                if r.inflight is None and self._packable(r.desc)]
-        if not cand:
-            return
-        # one pool holds scenes of the same parameters (time step, sweeps, ground, ...)
-        key = _pkey(self.resident[cand[0]].desc)
-        cand = [sid for sid in cand if _pkey(self.resident[sid].desc) == key]
-        first = self.resident[cand[0]].n_bodies
-        size = {p: sum(self.descs[s].n_bodies for s in p.members) for p in self.pools}
-        roomy = [p for p in self.pools if p.key == key and size[p] + first <= self.pool_capacity]
-        pool = next((p for p in roomy if p.inflight is None), None)
-        if pool is None and roomy:
-            return                   # the pool with room has a step in flight: try at a later pump
-        old = list(pool.members) if pool else []
-        total = size[pool] if pool else 0
-        new = []
-        for sid in cand:
-            n = self.resident[sid].n_bodies
-            if total + n > self.pool_capacity:
-                break
-            new.append(sid)
-            total += n
+        if self.pending is None:
+            if now - self.last_rebuild < self.rebuild_interval:
+                return
+            cand = [sid for sid, r in self.resident.items() if self._packable(r.desc)]
+            if not cand:
+                return
+
+            # one pool holds scenes of the same parameters (time step, sweeps, ground, ...)
+            # and the same lane count alone
+            def key_of(sid):
+                r = self.resident[sid]
+                return _pkey(r.desc), r.lanes
+
+            key = key_of(cand[0])
+            cand = [sid for sid in cand if key_of(sid) == key]
+            # a pool is only as large as the library keeps the members' lane count for (it
+            # halves the lanes above 2^17 lanes x bodies)
+            cap = min(self.pool_capacity, (1 << 17) // key[1])
+            first = self.resident[cand[0]].n_bodies
+            size = {p: sum(self.descs[s].n_bodies for s in p.members) for p in self.pools}
+            pool = next((p for p in self.pools if p.key == key and size[p] + first <= cap), None)
+            total = size[pool] if pool else 0
+            new = []
+            for sid in cand:
+                n = self.resident[sid].n_bodies
+                if total + n > cap:
+                    continue
+                new.append(sid)
+                total += n
+            # room for the new pool beside the old one while the states move across
+            if not new or self.bytes_used + self._estimate(total) > self.budget:
+                self.last_rebuild = now
+                return
+            self.pending = (key, pool, new)
+        key, pool, new = self.pending
+        if pool is not None and pool not in self.pools:
+            pool = None              # evicted meanwhile: the newcomers start a pool of their own
+        new = [sid for sid in new if sid in self.resident]
+        if (pool is not None and pool.inflight) or any(self.resident[sid].inflight for sid in new):
+            return                   # their enqueued steps are still running
+        self.pending = None
         if not new:
             return
-        # room for the new pool beside the old one while the states move across
-        if self.bytes_used + self._estimate(total) > self.budget:
-            return
+        old = list(pool.members) if pool else []
         self.last_rebuild = now
         members = old + new
         descs = [self.descs[s] if s in self.descs else self.resident[s].desc for s in members]
@@ -246,8 +276,8 @@ class Server:
             rows += [st[pool.offsets[k]:pool.offsets[k + 1]] for k in range(len(old))]
         rows += [self.resident[s].scene.state() for s in new]
         sc_desc, off = _pack(descs)
-        stream = self._torch.cuda.Stream(self.device)
-        lib = self._P.Scene(sc_desc, device=self.device, stream=stream, sweep_lanes=self.pool_lanes, sweep_mode=2,
+        stream = self._torch.cuda.Stream(self.device, priority=-1)
+        lib = self._P.Scene(sc_desc, device=self.device, stream=stream, sweep_lanes=key[1], sweep_mode=2,
                             light_order=1)
         lib.set_state(np.concatenate(rows))
         nbytes = lib.info()["device_bytes"]
@@ -298,8 +328,9 @@ class Server:
                 r.queue.append(req)
         self.waiting = still
 
-    def _advance(self, req, queue, t_elig, t):
-        req.step_latency.append(t - t_elig)
+    def _complete(self, req, queue, t):
+        """One step of req observed complete at t."""
+        req.step_latency.append(t - req.t_eligible)
         req.steps_done += 1
         self.steps_completed += 1
         if req.steps_done == req.n_steps:
@@ -308,62 +339,82 @@ class Server:
         else:
             req.t_eligible = t
 
+    @staticmethod
+    def _next(queue):
+        """The first request of a queue with steps not yet enqueued (requests run in order)."""
+        for req in queue:
+            if req.launched < req.n_steps:
+                return req
+        return None
+
     def pump(self) -> int:
-        """Poll completions, admit, pack and launch; returns the number of steps launched."""
-        now = self.clock()
+        """Poll completions, admit, pack and launch; returns the number of steps launched.
+        Each scene (and each pool) keeps up to `depth` steps enqueued on the device, so it
+        never waits for the host to observe a step before the next one starts."""
         for p in self.pools:
-            if p.inflight is not None and p.inflight[1].query():
+            while p.inflight and p.inflight[0][1].query():
+                members, _ = p.inflight.popleft()
                 t = self.clock()
-                for sid, req, t_elig in p.inflight[0]:
-                    self._advance(req, p.queues[sid], t_elig, t)
+                for sid, req in members:
+                    self._complete(req, p.queues[sid], t)
                     p.last_use[sid] = t
-                p.inflight = None
         for r in self.resident.values():
-            if r.inflight is not None and r.inflight[2].query():
-                req, t_elig, _ = r.inflight
+            while r.inflight and r.inflight[0][1].query():
+                req, _ = r.inflight.popleft()
                 t = self.clock()
-                self._advance(req, r.queue, t_elig, t)
-                r.inflight = None
+                self._complete(req, r.queue, t)
                 r.last_use = t
         self._route_waiting()
         if self.pack:
             self._rebuild()
         launched = 0
+        draining = set(self.pending[2]) if self.pending else set()
+        drain_pool = self.pending[1] if self.pending else None
         for p in self.pools:
-            if p.inflight is not None:
+            if p is drain_pool:
                 continue
-            active = [(sid, p.queues[sid][0]) for sid in p.members if p.queues[sid]]
-            if not active:
+            idx = None
+            while len(p.inflight) < self.depth:
+                active = [(sid, self._next(p.queues[sid])) for sid in p.members]
+                active = [(sid, req) for sid, req in active if req is not None]
+                if not active:
+                    break
+                if idx is None:
+                    idx = {sid: k for k, sid in enumerate(p.members)}
+                hold = np.ones(len(p.members), dtype=np.uint8)
+                for sid, _ in active:
+                    hold[idx[sid]] = 0
+                if p.hold is None or not np.array_equal(hold, p.hold):
+                    p.scene.set_group_hold(hold)
+                    p.hold = hold
+                p.scene.step(1)
+                ev = self._torch.cuda.Event()
+                ev.record(p.stream)
+                for _, req in active:
+                    req.launched += 1
+                p.inflight.append((active, ev))
+                self.pool_launches += 1
+                launched += len(active)
+        now = self.clock()
+        for sid, r in self.resident.items():
+            if sid in draining:
                 continue
-            hold = np.ones(len(p.members), dtype=np.uint8)
-            idx = {sid: k for k, sid in enumerate(p.members)}
-            for sid, _ in active:
-                hold[idx[sid]] = 0
-            if p.hold is None or not np.array_equal(hold, p.hold):
-                p.scene.set_group_hold(hold)
-                p.hold = hold
-            p.scene.step(1)
-            ev = self._torch.cuda.Event()
-            ev.record(p.stream)
-            p.inflight = ([(sid, req, req.t_eligible if req.steps_done else max(req.t_arrival, req.t_eligible))
-                           for sid, req in active], ev)
-            self.pool_launches += 1
-            launched += len(active)
-        for r in self.resident.values():
-            if r.inflight is None and r.queue:
-                req = r.queue[0]
-                t_elig = req.t_eligible if req.steps_done else max(req.t_arrival, req.t_eligible)
+            while len(r.inflight) < self.depth:
+                req = self._next(r.queue)
+                if req is None:
+                    break
                 r.scene.step(1)
                 ev = self._torch.cuda.Event()
                 ev.record(r.stream)
-                r.inflight = (req, t_elig, ev)
+                req.launched += 1
+                r.inflight.append((req, ev))
                 r.last_use = now
                 launched += 1
         return launched
 
     def busy(self) -> bool:
-        return (bool(self.waiting) or any(r.inflight is not None or r.queue for r in self.resident.values())
-                or any(p.inflight is not None or any(p.queues[s] for s in p.members) for p in self.pools))
+        return (bool(self.waiting) or any(r.inflight or r.queue for r in self.resident.values())
+                or any(p.inflight or any(p.queues[s] for s in p.members) for p in self.pools))
 
     def drain(self, timeout: float = 600.0):
         t0 = self.clock()
