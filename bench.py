@@ -460,9 +460,10 @@ def measure(P, torch, sc, name, start, K, W, dev, stream, world=1, flush=None, s
 
 
 def roofline(m, sc, name, start, stacked=False):
-    """Roofline of the sweep kernel inside the timed window: algorithmic bytes per launch
-    (164 B per body + 148 B per bond, this window's own mean bond count) / its mean duration
-    (the sweep stage's events bracket all its launches of a step)."""
+    """Roofline of the sweep inside the timed window, per sweep (the sweep's launches: one, or a
+    bond and a solve launch): algorithmic bytes (164 B per body + 148 B per bond, this
+    window's own mean bond count) / its mean duration (the sweep stage's events bracket all of
+    a step's sweep launches)."""
     prof, info = m["prof"], m["info"]
     steps = max(prof["steps"], 1)
     n_it = sc.params["n_iter"]
@@ -471,14 +472,13 @@ def roofline(m, sc, name, start, stacked=False):
     mode = info["sweep_mode"]
     per_sweep = 164.0 * N + 148.0 * bonds_avg
     if mode == 3:
-        kernel, per_launch = "k_sweep_fused", n_it * per_sweep
+        kernel, per_launch = "k_sweep_fused", per_sweep  # (one launch runs all sweeps; per sweep)
     elif mode == 2:
         kernel, per_launch = "k_sweep_one", per_sweep
     else:
         kernel, per_launch = "k_bond+k_solve", per_sweep
-    ms_launch = prof["sweep_ms"] / max(prof["sweep_launches"], 1)
-    if mode == 1:
-        ms_launch *= 2.0  # one bond + one solve launch per sweep
+    # (the sweep stage's events bracket all of a step's sweep launches; per sweep)
+    ms_launch = prof["sweep_ms"] / max(prof["sweeps"], 1)
     achieved = per_launch / (ms_launch * 1e-3) / 1e9
     peak, peak_kind = _peaks()
     key = window_key(name, N, start, stacked)
