@@ -10,7 +10,7 @@
 namespace pabd {
 
 constexpr int LONG_T = 1024;
-constexpr int LONG_SMEM = 32768;  // ints of dynamic shared memory (128 KB)
+constexpr int LONG_SMEM = 4096;  // ints of dynamic shared memory (16 KB: several blocks per SM, no carve-out change)
 
 // 64 keys held two per lane (key k in lane k / 2, slot k % 2) sorted ascending by the 32
 // lanes of a warp: a bitonic network of shuffles
