@@ -250,14 +250,15 @@ __global__ void __launch_bounds__(LONG_T) k_csr_sort_long(Dev d) {
 constexpr int BIN_T = 256;
 
 // bin of body b in the light order, or -1 for a body on the heavy list: the bodies on the
-// extended path (statically flagged) in bins 0..HEAVY_ENDS by end count, the others after them
+// extended path (statically flagged) in bins 0..HEAVY_ENDS by descending end count, the others
+// after them in the same way
 __device__ __forceinline__ int light_bin(const Dev& d, int b) {
     const int fl = d.bflags[b];
     const int n = d.end_off[b + 1] - d.end_off[b];
     if (fl & BF_PINNED) return END_BINS;
     if (n > HEAVY_ENDS) return -1;
     const bool ext = d.p.precision_policy == 3 || (d.p.precision_policy && (fl & BF_FP64));
-    return (ext ? 0 : END_BINS) + n;
+    return (ext ? 0 : END_BINS) + (HEAVY_ENDS - n);
 }
 
 // bodies per bin: a block histogram in shared memory, one global atomic per bin and block

@@ -45,6 +45,9 @@ __device__ __forceinline__ void bond_one(const Dev& d, const float4* __restrict_
 // holds room for every possible contact, far more than a step has)
 __global__ void __launch_bounds__(BOND_T) k_bond(Dev d, const float4* __restrict__ q, int it) {
     pdl_enter();
+    // the solve launch that follows hands out its light bodies from this counter (the previous
+    // solve launch has finished: pdl_enter waited for it)
+    if (blockIdx.x == 0 && threadIdx.x == 0) d.ctr[C_SOLVE_NEXT] = 0;
     const int nb = d.ctr[C_NBONDS];
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) bond_one(d, q, it, b);
 }
@@ -68,15 +71,15 @@ __device__ __forceinline__ void add_records(const Dev& d, Sys<T>& s, int p0, int
 // One body per group of L lanes; lane l adds the bond kernel's records of the body's ends
 // l, l + L, ... -- in FP32, or in the extended type for a body on the extended path (the same
 // records and order as the one-launch sweep, so the two modes agree bit for bit).  The first
-// `light` blocks take the bodies with at most HEAVY_ENDS ends; the HEAVY_BLOCKS blocks after
-// them take the heavy bodies, a block each.
+// HEAVY_BLOCKS blocks take the heavy bodies (more than HEAVY_ENDS ends), a block each, and are
+// dispatched first; the blocks after them stay resident and take the light bodies.
 template <int L, class X>
 __global__ void __launch_bounds__(SOLVE_T, 4) k_solve(Dev d, const float4* __restrict__ qi, float4* __restrict__ qo,
-                                                   int it, int light) {
+                                                   int it) {
     pdl_enter();
     const int last = it == d.p.n_iter - 1;
-    if ((int)blockIdx.x >= light) {
-        heavy_role<X>(d, blockIdx.x - light, qi, qo, last,
+    if ((int)blockIdx.x < HEAVY_BLOCKS) {
+        heavy_role<X>(d, blockIdx.x, qi, qo, last,
             [&](int b, auto& s, const float* c, const float* A, const float* xs, int e0, int e1, int ln) {
                 add_records(d, s, e0 + ln, e1, 32, xs);
             },
@@ -87,13 +90,13 @@ __global__ void __launch_bounds__(SOLVE_T, 4) k_solve(Dev d, const float4* __res
     }
     // the light bodies in this step's (class, end count) order, or in body order (a body on
     // the heavy list then returns at once); either way the same arithmetic per body
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int slot = tid / L, lane = tid & (L - 1);
-    if (slot >= (d.light_sorted ? d.ctr[C_NLIGHT] : d.N)) return;
-    const int b = d.light_sorted ? d.order[slot] : slot;
-    solve_body<L, X>(d, b, lane, lane_mask<L>(), qi, qo, last,
-                     [&](auto& s, const float* c, const float* A, const float* xs, int e0, int e1) {
-        add_records(d, s, e0 + lane, e1, L, xs);
+    const int lane = threadIdx.x & (L - 1);
+    for_light_slots<L>(&d.ctr[C_SOLVE_NEXT], d.light_sorted ? d.ctr[C_NLIGHT] : d.N, HEAVY_BLOCKS, [&](int slot) {
+        const int b = d.light_sorted ? d.order[slot] : slot;
+        solve_body<L, X>(d, b, lane, lane_mask<L>(), qi, qo, last,
+                         [&](auto& s, const float* c, const float* A, const float* xs, int e0, int e1) {
+            add_records(d, s, e0 + lane, e1, L, xs);
+        });
     });
 }
 
@@ -105,21 +108,25 @@ void launch_bond(const Dev& d, const float4* q, int it, cudaStream_t st, long lo
 void launch_solve(const Dev& d, const float4* q_in, float4* q_out, int it, int lanes, cudaStream_t st,
                   long long* launches) {
     static_assert(SOLVE_T == HEAVY_T, "the solve launch's blocks are the heavy bodies' blocks");
+    // resident light blocks: as many as fit beside each other (4 per SM by the launch bounds),
+    // fewer when the bodies do not need them
+    const int slots = resident_slots(4);
     const long long n = (long long)(d.N > 0 ? d.N : 1) * lanes;
-    const int light = (int)((n + SOLVE_T - 1) / SOLVE_T);
-    const int grid = light + HEAVY_BLOCKS;
+    const long long need = (n + SOLVE_T - 1) / SOLVE_T;
+    const int light = (int)(need < slots ? need : slots);
+    const int grid = HEAVY_BLOCKS + light;
     const bool f64 = d.p.precision_policy == 2;
     switch (lanes) {
-        case 1: f64 ? launch_pdl(k_solve<1, double>, dim3(grid), dim3(SOLVE_T), 0, st, d, q_in, q_out, it, light)
-                    : launch_pdl(k_solve<1, ca>, dim3(grid), dim3(SOLVE_T), 0, st, d, q_in, q_out, it, light); break;
-        case 2: f64 ? launch_pdl(k_solve<2, double>, dim3(grid), dim3(SOLVE_T), 0, st, d, q_in, q_out, it, light)
-                    : launch_pdl(k_solve<2, ca>, dim3(grid), dim3(SOLVE_T), 0, st, d, q_in, q_out, it, light); break;
-        case 4: f64 ? launch_pdl(k_solve<4, double>, dim3(grid), dim3(SOLVE_T), 0, st, d, q_in, q_out, it, light)
-                    : launch_pdl(k_solve<4, ca>, dim3(grid), dim3(SOLVE_T), 0, st, d, q_in, q_out, it, light); break;
-        case 8: f64 ? launch_pdl(k_solve<8, double>, dim3(grid), dim3(SOLVE_T), 0, st, d, q_in, q_out, it, light)
-                    : launch_pdl(k_solve<8, ca>, dim3(grid), dim3(SOLVE_T), 0, st, d, q_in, q_out, it, light); break;
-        default: f64 ? launch_pdl(k_solve<16, double>, dim3(grid), dim3(SOLVE_T), 0, st, d, q_in, q_out, it, light)
-                     : launch_pdl(k_solve<16, ca>, dim3(grid), dim3(SOLVE_T), 0, st, d, q_in, q_out, it, light); break;
+        case 1: f64 ? launch_pdl(k_solve<1, double>, dim3(grid), dim3(SOLVE_T), 0, st, d, q_in, q_out, it)
+                    : launch_pdl(k_solve<1, ca>, dim3(grid), dim3(SOLVE_T), 0, st, d, q_in, q_out, it); break;
+        case 2: f64 ? launch_pdl(k_solve<2, double>, dim3(grid), dim3(SOLVE_T), 0, st, d, q_in, q_out, it)
+                    : launch_pdl(k_solve<2, ca>, dim3(grid), dim3(SOLVE_T), 0, st, d, q_in, q_out, it); break;
+        case 4: f64 ? launch_pdl(k_solve<4, double>, dim3(grid), dim3(SOLVE_T), 0, st, d, q_in, q_out, it)
+                    : launch_pdl(k_solve<4, ca>, dim3(grid), dim3(SOLVE_T), 0, st, d, q_in, q_out, it); break;
+        case 8: f64 ? launch_pdl(k_solve<8, double>, dim3(grid), dim3(SOLVE_T), 0, st, d, q_in, q_out, it)
+                    : launch_pdl(k_solve<8, ca>, dim3(grid), dim3(SOLVE_T), 0, st, d, q_in, q_out, it); break;
+        default: f64 ? launch_pdl(k_solve<16, double>, dim3(grid), dim3(SOLVE_T), 0, st, d, q_in, q_out, it)
+                     : launch_pdl(k_solve<16, ca>, dim3(grid), dim3(SOLVE_T), 0, st, d, q_in, q_out, it); break;
     }
     *launches += 1;
 }

@@ -8,11 +8,12 @@ namespace pabd {
 // One sweep per launch: the same per-body work as the fused kernel, with the launch boundary
 // (a graph edge) in place of the grid barrier.  Capped at 128 registers (4 blocks per SM),
 // without spills (the fused kernel, which loops over the sweeps, spills a few bytes).  The
-// first `light` blocks take the bodies with at most HEAVY_ENDS ends (L lanes each, in the
-// step's light order); the HEAVY_BLOCKS blocks after them take the heavy bodies.
+// first HEAVY_BLOCKS blocks take the heavy bodies (more than HEAVY_ENDS ends) and are
+// dispatched first; the blocks after them stay resident and take the light bodies (L lanes
+// each, in the step's light order), a warp's worth at a time (for_light_slots).
 template <int L, class X>
 __global__ void __launch_bounds__(128, 4) k_sweep_one(Dev d, const float4* __restrict__ qi, float4* __restrict__ qo,
-                                                   int it, int light) {
+                                                   int it) {
     // Programmatic dependent launch: wait until the previous sweep has completed and its writes
     // are visible (a no-op when launched without the attribute); no early signal to the next
     // sweep, whose waiting blocks would take SM slots (measured slower)
@@ -27,8 +28,12 @@ __global__ void __launch_bounds__(128, 4) k_sweep_one(Dev d, const float4* __res
         qo = (it & 1) ? d.qa : d.qb;
         last = 1;
     }
-    if ((int)blockIdx.x >= light) {
-        heavy_role<X>(d, blockIdx.x - light, qi, qo, last,
+    // this sweep's counter of light chunks, and the next sweep's zeroed (the previous sweep,
+    // which used it, has finished)
+    int* next = &d.ctr[C_SWEEP_NEXT + (it & 1)];
+    if (blockIdx.x == 0 && threadIdx.x == 0) d.ctr[C_SWEEP_NEXT + ((it + 1) & 1)] = 0;
+    if ((int)blockIdx.x < HEAVY_BLOCKS) {
+        heavy_role<X>(d, blockIdx.x, qi, qo, last,
             [&](int b, auto& s, const float* c, const float* A, const float* xs, int e0, int e1, int ln) {
                 gather_ends<32>(d, qi, b, c, A, xs, e0, e1, ln, it, s);
             },
@@ -39,17 +44,18 @@ __global__ void __launch_bounds__(128, 4) k_sweep_one(Dev d, const float4* __res
     }
     // the light bodies in this step's (class, end count) order, or in body order (a body on
     // the heavy list then returns at once); either way the same arithmetic per body
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int slot = tid / L, lane = tid & (L - 1);
-    if (slot >= (d.light_sorted ? d.ctr[C_NLIGHT] : d.N)) return;
-    const int b = d.light_sorted ? d.order[slot] : slot;
-    solve_body<L, X>(d, b, lane, lane_mask<L>(), qi, qo, last, [&](auto& s, const float* c, const float* A, const float* xs, int e0, int e1) {
-        gather_ends<L>(d, qi, b, c, A, xs, e0, e1, lane, it, s);
+    const int lane = threadIdx.x & (L - 1);
+    for_light_slots<L>(next, d.light_sorted ? d.ctr[C_NLIGHT] : d.N, HEAVY_BLOCKS, [&](int slot) {
+        const int b = d.light_sorted ? d.order[slot] : slot;
+        solve_body<L, X>(d, b, lane, lane_mask<L>(), qi, qo, last,
+                         [&](auto& s, const float* c, const float* A, const float* xs, int e0, int e1) {
+            gather_ends<L>(d, qi, b, c, A, xs, e0, e1, lane, it, s);
+        });
     });
 }
 
 template <int L, class X>
-static void sweep_one_ex(const Dev& d, const float4* qi, float4* qo, int it, int light, int grid, bool pdl,
+static void sweep_one_ex(const Dev& d, const float4* qi, float4* qo, int it, int grid, bool pdl,
                          cudaStream_t st) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -61,18 +67,18 @@ static void sweep_one_ex(const Dev& d, const float4* qi, float4* qo, int it, int
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
-    cudaLaunchKernelEx(&cfg, k_sweep_one<L, X>, d, qi, qo, it, light);
+    cudaLaunchKernelEx(&cfg, k_sweep_one<L, X>, d, qi, qo, it);
 }
 
 template <class X>
-static void sweep_one_l(const Dev& d, const float4* qi, float4* qo, int it, int L, int light, int grid, bool pdl,
+static void sweep_one_l(const Dev& d, const float4* qi, float4* qo, int it, int L, int grid, bool pdl,
                         cudaStream_t st) {
     switch (L) {
-        case 1: sweep_one_ex<1, X>(d, qi, qo, it, light, grid, pdl, st); break;
-        case 2: sweep_one_ex<2, X>(d, qi, qo, it, light, grid, pdl, st); break;
-        case 4: sweep_one_ex<4, X>(d, qi, qo, it, light, grid, pdl, st); break;
-        case 8: sweep_one_ex<8, X>(d, qi, qo, it, light, grid, pdl, st); break;
-        default: sweep_one_ex<16, X>(d, qi, qo, it, light, grid, pdl, st); break;
+        case 1: sweep_one_ex<1, X>(d, qi, qo, it, grid, pdl, st); break;
+        case 2: sweep_one_ex<2, X>(d, qi, qo, it, grid, pdl, st); break;
+        case 4: sweep_one_ex<4, X>(d, qi, qo, it, grid, pdl, st); break;
+        case 8: sweep_one_ex<8, X>(d, qi, qo, it, grid, pdl, st); break;
+        default: sweep_one_ex<16, X>(d, qi, qo, it, grid, pdl, st); break;
     }
 }
 
@@ -82,11 +88,12 @@ void launch_sweep_one(const Dev& d, const float4* qi, float4* qo, int it, int L,
                       long long* launches, bool pdl) {
     static_assert(HEAVY_T == 128, "the sweep launch's blocks are the heavy bodies' blocks");
     const long long n = (long long)(d.N > 0 ? d.N : 1) * L;
-    const int light = (int)((n + 127) / 128);
-    const int grid = light + HEAVY_BLOCKS;
+    const long long need = (n + 127) / 128;
+    const int slots = resident_slots(4);
+    const int grid = HEAVY_BLOCKS + (int)(need < slots ? need : slots);
     // the extended type of ill-conditioned bodies: FP64 under policy 2, double-float otherwise
-    if (d.p.precision_policy == 2) sweep_one_l<double>(d, qi, qo, it, L, light, grid, pdl, st);
-    else sweep_one_l<ca>(d, qi, qo, it, L, light, grid, pdl, st);
+    if (d.p.precision_policy == 2) sweep_one_l<double>(d, qi, qo, it, L, grid, pdl, st);
+    else sweep_one_l<ca>(d, qi, qo, it, L, grid, pdl, st);
     *launches += 1;
 }
 

@@ -400,6 +400,9 @@ pabd_status autotune_default(pabd_scene* s) {
         if ((!tune_mode && mode != s->mode) || (!tune_order && dd.light_sorted != d.light_sorted)) continue;
         float tot = 0.f;
         for (int r = 0; r < 3; ++r) {
+            // the one-launch sweeps' chunk counters, as the step's reset leaves them (each
+            // sweep zeroes the next sweep's counter, so a pass must start from clean ones)
+            CK(cudaMemsetAsync(dd.ctr + C_SWEEP_NEXT, 0, 2 * sizeof(int), s->st));
             CK(cudaEventRecord(e0, s->st));
             float4* cur = dd.qa;
             float4* nxt = dd.qb;

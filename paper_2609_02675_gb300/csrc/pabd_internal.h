@@ -37,6 +37,9 @@ enum Counter {
     C_CELLBITS1,       // float bits of the widest box of grid level 1 (multilevel grid)
     C_CELLBITS2,       // ... of grid level 2
     C_NLIGHT,          // bodies on this step's light list (Dev::order)
+    C_SOLVE_NEXT,      // next chunk of light bodies for the solve launch's warps (reset by k_bond)
+    C_SWEEP_NEXT,      // the same for the one-launch sweeps, one counter per sweep parity: sweep k
+    C_SWEEP_NEXT1,     // takes counter k & 1 and zeroes the other one for sweep k + 1
     C_COUNT
 };
 
@@ -60,12 +63,13 @@ constexpr int HEAVY_ENDS = 64;
 constexpr int HEAVY_T = 128;
 // of those, bodies with up to WIDE_ENDS ends are summed by one warp (32 lanes), more by the block
 constexpr int WIDE_ENDS = 256;
-// blocks appended to each sweep launch for the heavy bodies (they loop over the heavy list)
+// blocks of each sweep launch for the heavy bodies (they loop over the heavy list)
 constexpr int HEAVY_BLOCKS = 152;
 // The light bodies (at most HEAVY_ENDS ends) are ordered every step by (class, end count):
-// the bodies on the extended path first, then the rest, each class by its number of ends, so
-// that the lanes of one warp walk slices of the same length down the same path.  2 * END_BINS
-// bins; which lanes take a body never changes its arithmetic.
+// the bodies on the extended path first, then the rest, each class from the most ends to the
+// fewest, so that the lanes of one warp walk slices of the same length down the same path and
+// the longest warps start first (the launch does not end on them).  2 * END_BINS bins; which
+// lanes take a body never changes its arithmetic.
 constexpr int END_BINS = HEAVY_ENDS + 1;
 
 struct Dev {
@@ -169,6 +173,18 @@ constexpr int GS_BLOCKS = 152 * 8;
 inline int stride_grid(long long cap, int block) {
     const long long b = (cap + block - 1) / block;
     return (int)(b < 1 ? 1 : (b > GS_BLOCKS ? GS_BLOCKS : b));
+}
+
+// blocks of a kernel with `per_sm` resident blocks per SM that fit on the current device at once
+inline int resident_slots(int per_sm) {
+    static const int sms = [] {
+        int dev = 0, n = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+            n = 152;
+        return n;
+    }();
+    return per_sm * sms;
 }
 
 template <class... KArgs, class... Args>

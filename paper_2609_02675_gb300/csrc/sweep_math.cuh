@@ -626,6 +626,17 @@ __device__ __noinline__ static void polar_higham(float* X) {
     }
 }
 
+// The out-of-line fallback works on a copy: were X's own address passed to it, X could not
+// stay in registers, and every Newton-Schulz step of every body would go through local memory.
+__device__ __forceinline__ void polar_fallback(float* X) {
+    float T[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) T[k] = X[k];
+    polar_higham(T);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) X[k] = T[k];
+}
+
 // Rotation of A^{k+1/2} (local solve).  A near-orthogonal A (||A^T A - I||_F < 1/2, det > 0)
 // is taken by the Newton-Schulz iteration X <- X (3 I - X^T X) / 2 (Higham 1986, Kovarik
 // 1970), which converges quadratically to the orthogonal polar factor and needs only
@@ -646,7 +657,7 @@ __device__ __forceinline__ void polar_rotation(float* X) {
         if (it == 0) {
             const float det = X[0] * (X[4] * X[8] - X[5] * X[7]) - X[1] * (X[3] * X[8] - X[5] * X[6]) +
                               X[2] * (X[3] * X[7] - X[4] * X[6]);
-            if (!(e2 < 0.25f) || !(det > 0.f)) { polar_higham(X); return; }
+            if (!(e2 < 0.25f) || !(det > 0.f)) { polar_fallback(X); return; }
         }
         if (e2 < 1e-13f) break;
         // X <- X (3I - X^T X)/2 = X (I - E/2)
@@ -682,6 +693,29 @@ __device__ __forceinline__ void sys_reduce(Sys<T>& s, unsigned mask) {
         for (int r = 0; r < 4; ++r)
 #pragma unroll
             for (int k = 0; k < 3; ++k) s.r[r][k] += shfl_xor(mask, s.r[r][k], o);
+    }
+}
+
+// The light bodies' slots 0..n-1, a warp's worth (32 / L slots) at a time, for the blocks from
+// first_block on: each warp first takes the chunk of its own index, then the chunks past the
+// grid's from the counter `next` until none are left, so the warps that finish early take more
+// and a launch does not end on a few long blocks.  No counter traffic when the grid's warps
+// cover every chunk.  f(slot) runs on the L lanes of each slot.
+template <int L, class F>
+__device__ __forceinline__ void for_light_slots(int* next, int n, int first_block, F&& f) {
+    constexpr int PER_WARP = 32 / L;
+    const int wpb = blockDim.x >> 5, wl = threadIdx.x & 31;
+    const int warps = (gridDim.x - first_block) * wpb;
+    const int chunks = (n + PER_WARP - 1) / PER_WARP;
+    int chunk = (blockIdx.x - first_block) * wpb + (threadIdx.x >> 5);
+    while (chunk < chunks) {
+        const int slot = chunk * PER_WARP + wl / L;
+        if (slot < n) f(slot);
+        __syncwarp();
+        if (warps >= chunks) return;
+        int t = 0;
+        if (wl == 0) t = atomicAdd(next, 1);
+        chunk = warps + __shfl_sync(0xffffffffu, t, 0);
     }
 }
 
