@@ -269,8 +269,6 @@ __device__ __forceinline__ Sys<df> ext_sys(const Sys<ca>& s) {
     return t;
 }
 __device__ __forceinline__ const Sys<double>& ext_sys(const Sys<double>& s) { return s; }
-template <class X> struct ext_type { using T = X; };
-template <> struct ext_type<ca> { using T = df; };
 
 // The system is assembled about a per-body expansion point x_s (Dev::xs; zero for most
 // bodies): with z = x - x_s the unknowns are c' = c + A x_s and A, so G = diag(m, Pi) +
@@ -477,7 +475,13 @@ __device__ __forceinline__ T sys_solve(const Sys<T>& s, T out[4][3]) {
 // half the work and half the code of the double-float Cholesky, at the same accuracy for these
 // systems (errors of order 2^-48 of the entries, far below the single-precision result).
 //   D0 = g00, L_k0 = g_0k / D0; D1 = g11 - L10 g01, u_k1 = g_1k - L_k0 g_0k (= L_k1 D1), ...
-__device__ __forceinline__ void sys_solve_ldl(const Sys<df>& s, df out[4][3]) {
+// The forward substitution y = L^-1 r stays in double-float: its last rows cancel (the soft
+// directions of a stiffly jointed body's G), and the pivots' inverses then magnify what is
+// left.  The rest, x = L^-T (D^-1 y), runs in single precision from the rounded y, D^-1 and L:
+// a triangular solve's componentwise error is set by its unit factor L (the scaling by D^-1 is
+// exact to rounding), which is well conditioned here, so x keeps single-precision accuracy
+// relative to its own entries -- all that the single-precision update q + x can hold.
+__device__ __forceinline__ void sys_solve_ldl(const Sys<df>& s, float out[4][3]) {
     const df* g = s.g;
     const df r0 = recip_dd(g[0]);
     const df l10 = g[1] * r0, l20 = g[2] * r0, l30 = g[3] * r0;
@@ -492,33 +496,45 @@ __device__ __forceinline__ void sys_solve_ldl(const Sys<df>& s, df out[4][3]) {
     const df l32 = u32 * r2;
     const df d3 = fma_dd(-l32, u32, fma_dd(-l31, u31, fma_dd(m30, g[3], g[9])));
     const df r3 = recip_dd(d3);
+    const float f10 = (float)l10, f20 = (float)l20, f30 = (float)l30, f21 = (float)l21, f31 = (float)l31,
+                f32 = (float)l32;
+    const float i0 = (float)r0, i1 = (float)r1, i2 = (float)r2, i3 = (float)r3;
     // the three right-hand sides through one copy of the substitution code (a short
     // instruction footprint): each pass solves column 0 and rotates the columns left, the
-    // solution entering as column 2, so after three passes the columns hold the solutions in order
+    // solution entering as column 2 of the output, so after three passes both hold theirs in order
     df c0[4], c1[4], c2[4];
+    float o0[4], o1[4], o2[4];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) { c0[r] = s.r[r][0]; c1[r] = s.r[r][1]; c2[r] = s.r[r][2]; }
+    for (int r = 0; r < 4; ++r) { c0[r] = s.r[r][0]; c1[r] = s.r[r][1]; c2[r] = s.r[r][2]; o0[r] = o1[r] = o2[r] = 0.f; }
 #pragma unroll 1
     for (int k = 0; k < 3; ++k) {
         const df y0 = c0[0];
         const df y1 = fma_dd(m10, y0, c0[1]);
         const df y2 = fma_dd(-l21, y1, fma_dd(m20, y0, c0[2]));
         const df y3 = fma_dd(-l32, y2, fma_dd(-l31, y1, fma_dd(m30, y0, c0[3])));
-        const df x3 = y3 * r3;
-        const df x2 = fma_dd(-l32, x3, y2 * r2);
-        const df x1 = fma_dd(-l31, x3, fma_dd(-l21, x2, y1 * r1));
-        const df x0 = fma_dd(m30, x3, fma_dd(m20, x2, fma_dd(m10, x1, y0 * r0)));
+        const float x3 = (float)y3 * i3;
+        const float x2 = __fmaf_rn(-f32, x3, (float)y2 * i2);
+        const float x1 = __fmaf_rn(-f31, x3, __fmaf_rn(-f21, x2, (float)y1 * i1));
+        const float x0 = __fmaf_rn(-f30, x3, __fmaf_rn(-f20, x2, __fmaf_rn(-f10, x1, (float)y0 * i0)));
 #pragma unroll
-        for (int r = 0; r < 4; ++r) { c0[r] = c1[r]; c1[r] = c2[r]; }
-        c2[0] = x0; c2[1] = x1; c2[2] = x2; c2[3] = x3;
+        for (int r = 0; r < 4; ++r) { c0[r] = c1[r]; c1[r] = c2[r]; o0[r] = o1[r]; o1[r] = o2[r]; }
+        o2[0] = x0; o2[1] = x1; o2[2] = x2; o2[3] = x3;
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r) { out[r][0] = c0[r]; out[r][1] = c1[r]; out[r][2] = c2[r]; }
+    for (int r = 0; r < 4; ++r) { out[r][0] = o0[r]; out[r][1] = o1[r]; out[r][2] = o2[r]; }
 }
 
-// the extended system's solve: LDL^T in double-float, Cholesky in FP64
-__device__ __forceinline__ void ext_solve(const Sys<df>& s, df out[4][3]) { sys_solve_ldl(s, out); }
-__device__ __forceinline__ void ext_solve(const Sys<double>& s, double out[4][3]) { sys_solve(s, out); }
+// the extended system's solve into the single-precision update: LDL^T in double-float,
+// Cholesky in FP64
+__device__ __forceinline__ void ext_solve(const Sys<df>& s, float out[4][3]) { sys_solve_ldl(s, out); }
+__device__ __forceinline__ void ext_solve(const Sys<double>& s, float out[4][3]) {
+    double x[4][3];
+    sys_solve(s, x);
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) out[r][k] = (float)x[r][k];
+}
 
 // ---- local solve: rotation of A ----
 
@@ -785,12 +801,7 @@ __device__ __forceinline__ void solve_body(const Dev& d, int b, int lane, unsign
         gather(s, c, A, xs, e0, e1);
         sys_reduce<L>(s, mask);
         const auto se = ext_sys(s);
-        typename ext_type<X>::T Xd[4][3];
-        ext_solve(se, Xd);
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) Xs[r][k] = (float)Xd[r][k];
+        ext_solve(se, Xs);
     }
     unshift(Xs, xs);
     finish_body(d, b, lane, qo, last, c, A, Xs);
@@ -937,12 +948,7 @@ __device__ __forceinline__ void solve_heavy(const Dev& d, int b, const float4* _
         block_reduce(s, reinterpret_cast<Sys<X>*>(buf_raw));
         if (t == 0) {
             const auto se = ext_sys(s);
-            typename ext_type<X>::T Xd[4][3];
-            ext_solve(se, Xd);
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int k = 0; k < 3; ++k) Xs[r][k] = (float)Xd[r][k];
+            ext_solve(se, Xs);
         }
     }
     if (t == 0) {
