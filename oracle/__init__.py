@@ -78,6 +78,7 @@ def lib():
         L.po_get_al_state.argtypes = [P, D]
         L.po_get_activation_margin.argtypes = [P, D]
         L.po_set_activation_shift.argtypes = [P, ctypes.c_double]
+        L.po_set_round_iterates.argtypes = [P, ctypes.c_int]
         L.po_last_sweeps.argtypes = [P]
         L.po_last_sweeps.restype = ctypes.c_int
         L.po_set_al_state.argtypes = [P, D]
@@ -189,6 +190,11 @@ class OracleScene:
     def set_activation_shift(self, shift: float):
         """Test probe: contacts switch on at g < dhat + shift in the following steps (0 = the method)."""
         self.L.po_set_activation_shift(self.h, float(shift))
+
+    def set_round_iterates(self, on: bool):
+        """Test probe: every sweep's iterate rounded to single precision before the next sweep
+        reads it, in the following steps (False = the method)."""
+        self.L.po_set_round_iterates(self.h, 1 if on else 0)
 
     def set_al_state(self, st: np.ndarray):
         st = np.ascontiguousarray(st, dtype=np.float64)

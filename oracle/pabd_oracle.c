@@ -87,6 +87,7 @@ typedef struct {
     double* resid;          /* per group, last iteration of the last step */
     double* amargin;        /* per body: min over the last step's sweeps of |g - dhat| of its contacts */
     double act_shift;       /* test probe of the contact activation threshold, 0 in the method */
+    int round_iterates;     /* test probe: each sweep's iterate rounded to single precision (0 in the method) */
     int last_sweeps;        /* sweeps the last step ran (n_iter unless a residual threshold ended it) */
     /* adjacency of static bonds (pairs excluded from contact) */
     int n_excl, cap_excl;
@@ -948,6 +949,8 @@ static int step_once(po_scene* s) {
             r2g[s->bs[b].group] += r2;
         }
         memcpy(q, q1, sizeof(double) * 12 * nb);
+        if (s->round_iterates)
+            for (int k = 0; k < 12 * nb; ++k) q[k] = (double)(float)q[k];
         for (int e = 0; e < s->nc; ++e)
             if (s->cb[e].type == PO_AL) al_update(&s->cb[e], q);
         s->last_sweeps = it + 1;
@@ -1088,6 +1091,11 @@ int po_last_sweeps(void* h) { return ((po_scene*)h)->last_sweeps; }
 
 /* Test probe: contacts of the following steps switch on at g < dhat + shift (0 restores the method). */
 void po_set_activation_shift(void* h, double shift) { ((po_scene*)h)->act_shift = shift; }
+
+/* Test probe: with on != 0, every sweep's iterate q^{k+1} of the following steps is rounded to
+   single precision before the next sweep reads it -- the perturbation that a path storing its
+   iterates in single precision applies at every sweep (0 restores the method). */
+void po_set_round_iterates(void* h, int on) { ((po_scene*)h)->round_iterates = on; }
 
 /* Per body, the smallest |g - dhat| of its contacts over the sweeps of the last step
    (infinity for a body without contacts): how close a contact came to switching on or off. */

@@ -11,8 +11,8 @@
 //            diag(m, Pi) + sum w [1;x][1;x]^T), the 4x3 system G dX = M(s - q^k) + sum
 //            [1;x] f'^T; factors G by Cholesky (the 12x12 Cholesky factor is L (x) I3),
 //            solves the three right-hand sides, then takes the rotation of A^{k+1/2}
-//            (the polar decomposition of sweep_math.cuh: Newton-Schulz, with Higham's
-//            scaled Newton iteration and an eigen-decomposition of A^T A as fallbacks).
+//            (the polar decomposition of sweep_math.cuh: Higham's scaled Newton
+//            iteration, with an eigen-decomposition of A^T A as the fallback).
 //            FP32, except bodies whose 4x4 factorisation is ill-conditioned (statically
 //            flagged, or a Cholesky pivot below 1e-3 of its diagonal): those sum the same
 //            single-precision records and factor in an extended type -- double-float on

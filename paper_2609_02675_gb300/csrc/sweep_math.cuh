@@ -618,49 +618,41 @@ __device__ __noinline__ static void polar_eigen(float* X) {
         for (int c = 0; c < 3; ++c) X[3 * r + c] = u[0][r] * v[0][c] + u[1][r] * v[1][c] + u[2][r] * v[2][c];
 }
 
-// Higham's scaled Newton iteration for the orthogonal polar factor:
-// X <- (z X + X^-T / z) / 2, z = |det X|^(-1/3), X^-T = cofactor(X) / det X.  Falls back
-// to the eigen-decomposition route when det X is not clearly positive.
-__device__ __noinline__ static void polar_higham(float* X) {
-    float C[9];
-    const float nrm = X[0] * X[0] + X[1] * X[1] + X[2] * X[2] + X[3] * X[3] + X[4] * X[4] + X[5] * X[5] +
-                      X[6] * X[6] + X[7] * X[7] + X[8] * X[8];
-    for (int it = 0; it < 12; ++it) {
-        cofactor(X, C);
-        const float det = X[0] * C[0] + X[1] * C[1] + X[2] * C[2];
-        if (!(det > 1e-6f * nrm * sqrtf(nrm))) { polar_eigen(X); return; }
-        const float z = rcbrtf(det);
-        const float iz = 1.f / (z * det);
-        float diff = 0.f;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            float nx = 0.5f * (z * X[k] + C[k] * iz);
-            diff += (nx - X[k]) * (nx - X[k]);
-            X[k] = nx;
-        }
-        if (diff < 1e-12f) break;
-    }
-}
-
-// The out-of-line fallback works on a copy: were X's own address passed to it, X could not
-// stay in registers, and every Newton-Schulz step of every body would go through local memory.
+// The out-of-line eigen route works on a copy: were X's own address passed to it, X could not
+// stay in registers on the common path.
 __device__ __forceinline__ void polar_fallback(float* X) {
     float T[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) T[k] = X[k];
-    polar_higham(T);
+    polar_eigen(T);
 #pragma unroll
     for (int k = 0; k < 9; ++k) X[k] = T[k];
 }
 
-// Rotation of A^{k+1/2} (local solve).  A near-orthogonal A (||A^T A - I||_F < 1/2, det > 0)
-// is taken by the Newton-Schulz iteration X <- X (3 I - X^T X) / 2 (Higham 1986, Kovarik
-// 1970), which converges quadratically to the orthogonal polar factor and needs only
-// multiply-adds; anything else goes to Higham's scaled Newton iteration.
+// Rotation of A^{k+1/2} (local solve), the orthogonal polar factor of X = A^{k+1/2}, in one
+// inline loop for every body.  Each pass measures E = X^T X - I:
+//   - ||E||_F^2 < 1e-13: done;
+//   - ||E||_F^2 < 1/4: a Newton-Schulz step X <- X (3 I - X^T X) / 2 = X - X E / 2 (Higham
+//     1986, Kovarik 1970): quadratic convergence from there, and a correction of X rather than
+//     a recomputation, so it adds only the rounding of the correction;
+//   - farther out (a stiffly jointed body's global update stretches A along its joints' lever
+//     arms, past the Newton-Schulz region, for most jointed bodies of a batch of trees): a
+//     step of Higham's scaled Newton iteration X <- (z X + X^-T / z) / 2, z = det(X)^(-1/3),
+//     X^-T = cofactor(X) / det X, which converges from any nonsingular X.
+// A det(X) that is not clearly positive (an inverted or degenerate A) goes to the
+// eigen-decomposition route.
 __device__ __forceinline__ void polar_rotation(float* X) {
-    float E[9];
-    for (int it = 0; it < 8; ++it) {
-        // E = X^T X - I
+    float C[9];
+    cofactor(X, C);
+    float det = X[0] * C[0] + X[1] * C[1] + X[2] * C[2];
+    {
+        const float nrm = X[0] * X[0] + X[1] * X[1] + X[2] * X[2] + X[3] * X[3] + X[4] * X[4] +
+                          X[5] * X[5] + X[6] * X[6] + X[7] * X[7] + X[8] * X[8];
+        if (!(det > 1e-6f * nrm * sqrtf(nrm))) { polar_fallback(X); return; }
+    }
+#pragma unroll 1
+    for (int it = 0; it < 16; ++it) {
+        float E[9];
 #pragma unroll
         for (int r = 0; r < 3; ++r)
 #pragma unroll
@@ -670,21 +662,26 @@ __device__ __forceinline__ void polar_rotation(float* X) {
                 E[3 * c + r] = E[3 * r + c];
             }
         const float e2 = E[0] * E[0] + E[4] * E[4] + E[8] * E[8] + 2.f * (E[1] * E[1] + E[2] * E[2] + E[5] * E[5]);
-        if (it == 0) {
-            const float det = X[0] * (X[4] * X[8] - X[5] * X[7]) - X[1] * (X[3] * X[8] - X[5] * X[6]) +
-                              X[2] * (X[3] * X[7] - X[4] * X[6]);
-            if (!(e2 < 0.25f) || !(det > 0.f)) { polar_fallback(X); return; }
-        }
         if (e2 < 1e-13f) break;
-        // X <- X (3I - X^T X)/2 = X (I - E/2)
-        float Y[9];
+        if (e2 < 0.25f) {
+            float Y[9];
 #pragma unroll
-        for (int r = 0; r < 3; ++r)
+            for (int r = 0; r < 3; ++r)
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
-                Y[3 * r + c] = X[3 * r + c] - 0.5f * (X[3 * r] * E[c] + X[3 * r + 1] * E[3 + c] + X[3 * r + 2] * E[6 + c]);
+                for (int c = 0; c < 3; ++c)
+                    Y[3 * r + c] = X[3 * r + c] - 0.5f * (X[3 * r] * E[c] + X[3 * r + 1] * E[3 + c] + X[3 * r + 2] * E[6 + c]);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) X[k] = Y[k];
+            for (int k = 0; k < 9; ++k) X[k] = Y[k];
+        } else {
+            if (it > 0) {
+                cofactor(X, C);
+                det = X[0] * C[0] + X[1] * C[1] + X[2] * C[2];
+            }
+            const float z = rcbrtf(det);
+            const float iz = __frcp_rn(z * det);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) X[k] = 0.5f * (z * X[k] + C[k] * iz);
+        }
     }
 }
 

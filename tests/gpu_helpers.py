@@ -73,6 +73,36 @@ def activation_envelope_err(sc, st0, k0, st_gpu, st_ref, he, oracle_mod, ulps: f
     return float(best[k]) / scale, k, float(d[k]) / scale
 
 
+def rounding_sensitivity(make_scene, st0, k0, st_ref, he, oracle_mod, mask=None, seeds=(0, 1, 2, 3)):
+    """How far the oracle's own step moves under perturbations of single-precision size: the
+    largest corner deviation (over the bodies in `mask`, as a fraction of the scene diagonal)
+    of the oracle step from st0 against st_ref, over these probes:
+      - the start state rounded to single precision;
+      - the same, and every sweep's iterate rounded to single precision (the storage rounding
+        that a single-precision path applies at every sweep);
+      - for each seed, every start coordinate moved by one unit of single-precision rounding up
+        or down (signs drawn from the seed), with the iterates rounded as above.
+    Where the sweeps converge this is at the level of the rounding itself; where they do not, it
+    is the map's amplification of rounding, which bounds how closely any single-precision path
+    can follow the oracle there."""
+    scale = scene_scale(st_ref, he)
+    sel = np.ones(st_ref.shape[0], bool) if mask is None else np.asarray(mask, bool)
+    starts = [(st0.astype(np.float32).astype(np.float64), False), (st0.astype(np.float32).astype(np.float64), True)]
+    for seed in seeds:
+        rng = np.random.default_rng(1000 + seed)
+        starts.append((st0 * (1.0 + np.ldexp(rng.choice([-1.0, 1.0], st0.shape), -24)), True))
+    worst = 0.0
+    for st, rnd in starts:
+        r = oracle_mod.OracleScene(make_scene())
+        r.set_round_iterates(rnd)
+        r.set_state(st)
+        r.step_index = k0
+        r.step(1)
+        d = np.linalg.norm(corners(r.state(), he) - corners(st_ref, he), axis=-1).max(axis=1)
+        worst = max(worst, float(d[sel].max()) / scale if sel.any() else 0.0)
+    return worst
+
+
 def same_contacts(gpu_c, ref_c):
     """Bit-exact contact lists: same (type, i, j) rows in the same order and the same
     single-precision geometry; dhat and w agree to single-precision rounding."""

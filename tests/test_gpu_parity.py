@@ -6,8 +6,9 @@ import pytest
 
 import oracle as O
 import scenes as S
-from tests.gpu_helpers import (REL_TOL, activation_envelope_err, corners, rel_err, residual_ratio, same_contacts,
-                               scene_scale, teacher_forced_step, threshold_rule_err, velocity_ratios, worst_body)
+from tests.gpu_helpers import (REL_TOL, activation_envelope_err, corners, rel_err, residual_ratio,
+                               rounding_sensitivity, same_contacts, scene_scale, teacher_forced_step,
+                               threshold_rule_err, velocity_ratios, worst_body)
 
 pytestmark = pytest.mark.gpu
 
@@ -587,43 +588,46 @@ def test_residual_threshold_matches_oracle(P):
 
     Once the trees stand on the ground, one group's sweeps stop converging (its residual
     stays near 0.2 for all 40 sweeps) and the Jacobi map amplifies perturbations there: the
-    oracle itself, started from the single-precision rounding of its own state, moves by up
-    to ~1e-5.  On a step where the oracle ran all n_iter sweeps without reaching the
-    threshold, the bound is max(REL_TOL, AMP * s), s = that oracle-vs-oracle difference: no
-    single-precision path can agree more closely than the map's response to its own input
-    rounding.  Every other step keeps REL_TOL."""
-    tol, n_iter, AMP = 1e-3, 40, 4.0
+    oracle itself, perturbed at the size of single-precision rounding, moves by up to ~3e-5
+    (rounding_sensitivity).  The bodies of a group that ran all n_iter sweeps without reaching
+    the threshold are held to max(REL_TOL, AMP * s), s = that sensitivity over the group's
+    bodies: no single-precision path can agree more closely than the map's response to
+    rounding.  The bodies of every other group keep REL_TOL on every step."""
+    tol, n_iter, AMP = 1e-3, 40, 2.0
     sc = _trees_tol(tol)
     ref = O.OracleScene(sc)
     g = P.Scene(sc)
     he = _he(sc)
+    group = np.asarray(sc.bodies["group"])
     worst, sweeps, widened = 0.0, [], []
     for k in range(sc.n_steps):
         st0, k0 = ref.state(), ref.step_index
         a, b = teacher_forced_step(g, ref)
-        e = rel_err(a, b, he)
-        if e >= REL_TOL:
+        scale = scene_scale(b, he)
+        d = np.linalg.norm(corners(a, he) - corners(b, he), axis=-1).max(axis=1)
+        if d.max() / scale >= REL_TOL:
             # a scene whose residual lands within rounding of the threshold may stop one sweep
             # earlier or later on the two sides (the GPU forms it from the FP32 iterates):
             # compare each body with the oracle at thresholds moved by 0.2 %
-            d = np.linalg.norm(corners(a, he) - corners(b, he), axis=-1).max(axis=1)
             for t in (tol * 1.002, tol * 0.998):
                 r = O.OracleScene(_trees_tol(t))
                 r.set_state(st0)
                 r.step_index = k0
                 r.step(1)
                 d = np.minimum(d, np.linalg.norm(corners(a, he) - corners(r.state(), he), axis=-1).max(axis=1))
-            e = float(d.max()) / scene_scale(b, he)
-        bound = REL_TOL
-        if e >= REL_TOL and ref.last_sweeps() == n_iter:
-            r = O.OracleScene(_trees_tol(tol))
-            r.set_state(st0.astype(np.float32).astype(np.float64))
-            r.step_index = k0
-            r.step(1)
-            s = rel_err(r.state(), b, he)
-            bound = max(REL_TOL, AMP * s)
-            widened.append((k, e, s))
-        worst = max(worst, e / bound)
+        # groups that ran every sweep without reaching the threshold
+        open_groups = np.nonzero(ref.residual() > tol)[0] if ref.last_sweeps() == n_iter else np.zeros(0, int)
+        loose = np.isin(group, open_groups)
+        e_closed = float(d[~loose].max()) / scale if (~loose).any() else 0.0
+        worst = max(worst, e_closed / REL_TOL)
+        if loose.any():
+            e_open = float(d[loose].max()) / scale
+            bound = REL_TOL
+            if e_open >= REL_TOL:
+                s = rounding_sensitivity(lambda: _trees_tol(tol), st0, k0, b, he, O, mask=loose)
+                bound = max(REL_TOL, AMP * s)
+                widened.append((k, e_open, s))
+            worst = max(worst, e_open / bound)
         sweeps.append((g.info()["last_sweeps"], ref.last_sweeps()))
     assert worst < 1.0, (worst, widened)
     assert len(widened) <= 3, widened

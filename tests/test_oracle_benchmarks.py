@@ -179,3 +179,43 @@ def test_unconverged_sweeps_amplify_input_rounding():
     assert ref.last_sweeps() == 40  # some group never reached the threshold
     assert sens[10] < 1e-6
     assert sens[40] > 3e-6 and sens[40] > 10.0 * sens[10], sens
+
+
+def test_iterate_rounding_probe():
+    """The oracle's iterate-rounding probe and the sensitivity measure built on it.  Off, a step
+    is the method's bit for bit.  On the 7-joint chain (10 sweeps, converging) it moves the step
+    by about the rounding itself.  On the batched trees at step 17, where one group's 40 sweeps
+    do not converge, perturbations of single-precision size move that group by more than the
+    1e-5 tolerance while the converged groups stay at the rounding level: the tolerance cannot
+    be met there by any single-precision path, only the map's own sensitivity."""
+    from tests.gpu_helpers import rounding_sensitivity
+
+    sc = S.chain_pendulum(n_steps=10)
+    he = np.asarray(sc.bodies["he"], dtype=float)
+    a, b, c = O.OracleScene(sc), O.OracleScene(sc), O.OracleScene(sc)
+    b.set_round_iterates(False)
+    c.set_round_iterates(True)
+    for o in (a, b, c):
+        o.step(5)
+    assert np.array_equal(a.state(), b.state())
+    dev = _corner_dev(c.state(), a.state(), he)
+    assert 0.0 < dev < 1e-6, dev
+
+    def mk():
+        t = S.batched_trees(n_scenes=24, n_steps=30)
+        t.params = dict(t.params, n_iter=40, resid_tol=1e-3)
+        return t
+
+    sc = mk()
+    he = np.asarray(sc.bodies["he"], dtype=float)
+    ref = O.OracleScene(sc)
+    ref.step(17)
+    st0, k0 = ref.state(), ref.step_index
+    ref.step(1)
+    assert ref.last_sweeps() == 40
+    open_groups = np.nonzero(ref.residual() > 1e-3)[0]
+    loose = np.isin(np.asarray(sc.bodies["group"]), open_groups)
+    assert 0 < loose.sum() < len(loose)
+    s_open = rounding_sensitivity(mk, st0, k0, ref.state(), he, O, mask=loose)
+    s_closed = rounding_sensitivity(mk, st0, k0, ref.state(), he, O, mask=~loose)
+    assert s_open > 1e-5 and s_closed < 1e-6, (s_open, s_closed)
