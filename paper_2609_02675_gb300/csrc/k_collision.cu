@@ -24,6 +24,7 @@
 // __fadd_rn / __fsub_rn so that no multiply-add is contracted into an FMA.
 #include "pair_filter.cuh"
 #include "sort_slices.cuh"
+#include "predict.cuh"
 
 namespace pabd {
 
@@ -62,10 +63,9 @@ __device__ __forceinline__ float body_infl(const Dev& d, int b) {
     return FA(FA(dh, FM(d.p.h, sp)), d.p.margin);
 }
 
-__global__ void k_aabb(Dev d) {
-    pdl_enter();
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= d.N) return;
+// One body's AABB, inflation and grid level (one thread per body, b = the thread's global
+// index, the threads at and above N already returned: the per-warp maximum below relies on it).
+__device__ __forceinline__ void aabb_body(const Dev& d, int b) {
     float c[3], A[9];
     load_q(d.qn, b, c, A);
     float4 h = d.he[b];
@@ -109,6 +109,13 @@ __global__ void k_aabb(Dev d) {
     d.cell[b] = make_int4(0, 0, 0, large ? -1 : 0);
     if (d.blevel) d.blevel[b] = large ? -1 : lv;
     if (large && d.large_ids) d.large_ids[atomicAdd(&d.ctr[C_NLARGE], 1)] = b;
+}
+
+__global__ void k_aabb(Dev d) {
+    pdl_enter();
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= d.N) return;
+    aabb_body(d, b);
 }
 
 __device__ __forceinline__ int cell_coord(float x, float inv_cs) {
@@ -688,6 +695,84 @@ __global__ void k_narrow_write(Dev d) {
 }
 
 static inline int nblk(int n) { return (n + CT - 1) / CT > 0 ? (n + CT - 1) / CT : 1; }
+
+// ---- the front of a step in scenes whose only contacts are with the ground ----
+//
+// Three launches in place of the AABB, ground-count, contact-write, CSR and predictor kernels
+// (the same arithmetic, fewer launch boundaries): k_ground_prelude per body, the scan of the
+// ground-contact counts, k_ground_bonds_csr per static end and per body.
+
+// per body: AABB and inflation, ground contacts counted, predictor
+__global__ void k_ground_prelude(Dev d) {
+    pdl_enter();
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= d.N) return;
+    aabb_body(d, b);
+    int n = 0;
+    if (d.p.has_ground && !(d.bflags[b] & BF_PINNED)) {
+        FBox fa;
+        load_box(d, b, fa);
+        n = ground_corners(d, fa, b, [](int, int, const float*, const float*, const float*, int) {});
+    }
+    d.gnd_cnt[b] = n;
+    predict_body(d, b);
+}
+
+// After the scan: items [0, Ns) are the static ends in Dev::sta_id order -- end e of body b
+// takes slot e + g0(b), g0(b) = the ground contacts of the bodies before b (at most the
+// contact capacity); items Ns + b, b <= N, the bodies -- slice start sta_off[b] + g0(b), the
+// body's ground contacts written as bonds Nc + g0(b) + k and given slots after its static ends,
+// and the heavy list.  The same CSR, in the same order, as counting, filling and sorting it.
+__global__ void k_ground_bonds_csr(Dev d) {
+    pdl_enter();
+    const int nb = d.N, Ns = d.sta_off[nb], cap = d.cap_contacts;
+    const int items = Ns + nb + 1;
+    for (int tt = blockIdx.x * blockDim.x + threadIdx.x; tt < items; tt += gridDim.x * blockDim.x) {
+        if (tt < Ns) {
+            const int b = d.sta_body[tt];
+            const int slot = tt + min(d.gnd_off[b], cap);
+            const int id = d.sta_id[tt], bond = id >> 1;
+            d.end_id[slot] = id;
+            d.end_pos[id] = slot;
+            const float4 x = (id & 1) ? d.bxj[bond] : d.bxi[bond];
+            d.end_x[slot] = make_float4(x.x, x.y, x.z, 0.f);
+            continue;
+        }
+        const int b = tt - Ns;
+        const int g0 = min(d.gnd_off[b], cap);
+        d.end_off[b] = d.sta_off[b] + g0;
+        if (b == nb) continue;
+        const int gn = min(d.gnd_off[b + 1], cap) - g0;
+        if (gn > 0) {
+            FBox fa;
+            load_box(d, b, fa);
+            const int p0 = d.sta_off[b + 1] + g0;
+            ground_corners(d, fa, b, [&](int i, int j, const float* xi, const float* xj, const float* N, int k) {
+                if (k >= gn) return;  // past the contact capacity (latched below)
+                write_contact(d, g0 + k, K_GROUND, i, j, xi, xj, N);
+                const int bond = d.Nc + g0 + k, p = p0 + k;
+                d.end_id[p] = 2 * bond;
+                d.end_pos[2 * bond] = p;
+                d.end_x[p] = make_float4(xi[0], xi[1], xi[2], 0.f);
+            });
+        }
+        if (d.sta_off[b + 1] - d.sta_off[b] + gn > HEAVY_ENDS) d.heavy[atomicAdd(&d.ctr[C_NHEAVY], 1)] = b;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        int nk = d.gnd_off[nb];
+        if (nk > cap) { atomicOr(&d.ctr[C_STATUS], ST_CAPACITY); nk = cap; }
+        d.ctr[C_NPC] = 0;
+        d.ctr[C_NGC] = nk;
+        d.ctr[C_NBONDS] = d.Nc + nk;
+    }
+}
+
+void launch_ground_front(const Dev& d, cudaStream_t st, long long* launches) {
+    launch_pdl(k_ground_prelude, dim3(nblk(d.N)), dim3(CT), 0, st, d);
+    scan_exclusive(d.gnd_cnt, d.gnd_off, nullptr, d.N, d.scan_scratch, st, launches);
+    launch_pdl(k_ground_bonds_csr, dim3(stride_grid((long long)d.cap_ends + d.N + 1, CT)), dim3(CT), 0, st, d);
+    *launches += 2;
+}
 
 // The broad phase alone (bucket / counter resets, AABBs, grid, sorted pair list), on whatever
 // buffers `d` points at; used by the allocation-free entry point.

@@ -1,6 +1,7 @@
 // Per-step kernels around the sweep: the predictor and the velocity recovery of Alg. 1,
 // the time-dependent drive anchors, the CSR of bond ends and the per-group residual.
 #include "pabd_internal.h"
+#include "predict.cuh"
 #include "sort_slices.cuh"
 
 namespace pabd {
@@ -8,48 +9,12 @@ namespace pabd {
 constexpr int ST_T = 256;
 static inline int nblk(int n) { return n > 0 ? (n + ST_T - 1) / ST_T : 1; }
 
-__device__ __forceinline__ void quat_to_mat(float4 q, float* R) {
-    float x = q.x, y = q.y, z = q.z, w = q.w;
-    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - z * w);       R[2] = 2.f * (x * z + y * w);
-    R[3] = 2.f * (x * y + z * w);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - x * w);
-    R[6] = 2.f * (x * z - y * w);       R[7] = 2.f * (y * z + x * w);       R[8] = 1.f - 2.f * (x * x + y * y);
-}
-
-__device__ __forceinline__ void store_q(float4* q, int b, const float* c, const float* A) {
-    q[3 * b] = make_float4(c[0], c[1], c[2], A[0]);
-    q[3 * b + 1] = make_float4(A[1], A[2], A[3], A[4]);
-    q[3 * b + 2] = make_float4(A[5], A[6], A[7], A[8]);
-}
-
-// Predictor (Alg. 1): v* = v + h g; c* = c + h v*; Q* = normalise(Q + h/2 [w, 0] Q);
-// A* = R(Q*); s = q^0 = (c*, A*).  Pinned bodies, and those of a group held this step, keep q^n.
+// the predictor of every body (predict_body)
 __global__ void k_predict(Dev d) {
     pdl_enter();
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= d.N) return;
-    if ((d.bflags[b] & BF_PINNED) || held(d, b)) {
-        float4 a0 = d.qn[3 * b], a1 = d.qn[3 * b + 1], a2 = d.qn[3 * b + 2];
-        d.sq[3 * b] = a0; d.sq[3 * b + 1] = a1; d.sq[3 * b + 2] = a2;
-        d.qa[3 * b] = a0; d.qa[3 * b + 1] = a1; d.qa[3 * b + 2] = a2;
-        d.qb[3 * b] = a0; d.qb[3 * b + 1] = a1; d.qb[3 * b + 2] = a2;
-        d.qstar[b] = d.quat[b];
-        return;
-    }
-    const float h = d.p.h;
-    float4 v = d.vel[b], w = d.omg[b], Q = d.quat[b], c4 = d.qn[3 * b];
-    float vs[3] = {v.x + h * d.p.g[0], v.y + h * d.p.g[1], v.z + h * d.p.g[2]};
-    float cs[3] = {c4.x + h * vs[0], c4.y + h * vs[1], c4.z + h * vs[2]};
-    float4 wq = make_float4(w.x * Q.w + (w.y * Q.z - w.z * Q.y), w.y * Q.w + (w.z * Q.x - w.x * Q.z),
-                            w.z * Q.w + (w.x * Q.y - w.y * Q.x), -(w.x * Q.x + w.y * Q.y + w.z * Q.z));
-    const float hh = 0.5f * h;
-    float4 Qn = make_float4(Q.x + hh * wq.x, Q.y + hh * wq.y, Q.z + hh * wq.z, Q.w + hh * wq.w);
-    float inv = rsqrtf(Qn.x * Qn.x + Qn.y * Qn.y + Qn.z * Qn.z + Qn.w * Qn.w);
-    Qn.x *= inv; Qn.y *= inv; Qn.z *= inv; Qn.w *= inv;
-    float A[9];
-    quat_to_mat(Qn, A);
-    store_q(d.sq, b, cs, A);
-    store_q(d.qa, b, cs, A);
-    d.qstar[b] = Qn;
+    predict_body(d, b);
 }
 
 // Rotation matrix -> unit quaternion (Shepperd's method: divide by the largest of
@@ -416,9 +381,35 @@ void launch_csr(const Dev& d, cudaStream_t st, long long* launches) {
     *launches += 4;
 }
 
+// The same sums with one warp per group, for scenes of small groups (a block per group leaves
+// most of its threads idle and takes one block slot per group): lane l of the warp plays the
+// block's threads l, l + 32, ... (its RES_T / 32 accumulators), each accumulator is combined by
+// the same xor tree and the results added in the same order -- the block's value bit for bit.
+__global__ void k_group_resid_warp(Dev d) {
+    pdl_enter();
+    const int g = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (g >= d.G) return;
+    const int s = d.group_off[g], e = d.group_off[g + 1];
+    double acc[RES_T / 32];
+#pragma unroll
+    for (int w = 0; w < RES_T / 32; ++w) {
+        acc[w] = 0.0;
+        for (int b = s + 32 * w + lane; b < e; b += RES_T) acc[w] += d.resid_body[b];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[w] += __shfl_xor_sync(0xffffffffu, acc[w], o);
+    }
+    if (lane == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < RES_T / 32; ++w) t += acc[w];
+        d.resid_group[g] = sqrt(t);
+    }
+}
+
 void launch_finalize(const Dev& d, const float4* q_fin, cudaStream_t st, long long* launches) {
     launch_pdl(k_finalize, dim3(nblk(d.N)), dim3(ST_T), 0, st, d, q_fin, 0);
-    launch_pdl(k_group_resid, dim3(d.G > 0 ? d.G : 1), dim3(RES_T), 0, st, d);
+    if (d.small_groups) launch_pdl(k_group_resid_warp, dim3(nblk(32 * (d.G > 0 ? d.G : 1))), dim3(ST_T), 0, st, d);
+    else launch_pdl(k_group_resid, dim3(d.G > 0 ? d.G : 1), dim3(RES_T), 0, st, d);
     *launches += 2;
 }
 

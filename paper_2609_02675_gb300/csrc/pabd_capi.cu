@@ -223,12 +223,21 @@ void enqueue_step(pabd_scene* s, long long* launches, const cudaEvent_t* ev = nu
     mark();
     launch_step_reset(d, s->st, launches);
     launch_drive_update(d, s->st, launches);
-    launch_collision(d, s->st, launches);
-    mark();
-    launch_csr(d, s->st, launches);
-    if (d.light_sorted) launch_light_order(d, s->st, launches);
-    mark();
-    launch_predict(d, s->st, launches);
+    if (d.sta_off) {
+        // ground-only scene: collision, CSR and predictor in one fused front (the predictor's
+        // stage is then empty in the profiling graph's split)
+        launch_ground_front(d, s->st, launches);
+        mark();
+        if (d.light_sorted) launch_light_order(d, s->st, launches);
+        mark();
+    } else {
+        launch_collision(d, s->st, launches);
+        mark();
+        launch_csr(d, s->st, launches);
+        if (d.light_sorted) launch_light_order(d, s->st, launches);
+        mark();
+        launch_predict(d, s->st, launches);
+    }
     launch_al_warm(d, s->st, launches);
     mark();
     float4* cur = d.qa;
@@ -383,10 +392,14 @@ pabd_status autotune_default(pabd_scene* s) {
     Dev dd = d;
     launch_step_reset(dd, s->st, &lc);
     launch_drive_update(dd, s->st, &lc);
-    launch_collision(dd, s->st, &lc);
-    launch_csr(dd, s->st, &lc);
+    if (dd.sta_off) {
+        launch_ground_front(dd, s->st, &lc);
+    } else {
+        launch_collision(dd, s->st, &lc);
+        launch_csr(dd, s->st, &lc);
+        launch_predict(dd, s->st, &lc);
+    }
     launch_light_order(dd, s->st, &lc);
-    launch_predict(dd, s->st, &lc);
     launch_end_records(dd, s->st, &lc);
     CK(cudaGetLastError());
     cudaEvent_t e0, e1;
@@ -532,6 +545,8 @@ pabd_status finalize_scene(pabd_scene* s) {
         group_off[bd.group + 1] = b + 1;
     }
     for (int g = 1; g <= d.G; ++g) if (group_off[g] < group_off[g - 1]) group_off[g] = group_off[g - 1];
+    d.small_groups = 1;
+    for (int g = 0; g < d.G; ++g) if (group_off[g + 1] - group_off[g] > 4096) d.small_groups = 0;
     d.Nlarge = (int)large.size();
     bool cap_below_widest = false;
     p.cell = (float)grid_cell_cap(s->bodies, flags, ds, &cap_below_widest);
@@ -650,7 +665,7 @@ pabd_status finalize_scene(pabd_scene* s) {
         }
     }
     // scenes whose only contacts are with the ground: each body's live static ends, sorted
-    std::vector<int> sta_off, sta_id;
+    std::vector<int> sta_off, sta_id, sta_body;
     if (!ds.body_contacts) {
         std::vector<int> cnt(N + 1, 0);
         for (int k = 0; k < Nc; ++k) {
@@ -661,6 +676,9 @@ pabd_status finalize_scene(pabd_scene* s) {
         sta_off.assign(N + 1, 0);
         for (int b = 0; b < N; ++b) sta_off[b + 1] = sta_off[b] + cnt[b];
         sta_id.assign(sta_off[N] > 0 ? sta_off[N] : 1, 0);
+        sta_body.assign(sta_id.size(), 0);
+        for (int b = 0; b < N; ++b)
+            for (int e = sta_off[b]; e < sta_off[b + 1]; ++e) sta_body[e] = b;
         std::vector<int> cur(sta_off.begin(), sta_off.end() - 1);
         for (int k = 0; k < Nc; ++k) {  // bond order: each body's ends come out sorted
             const HostBond& hb = s->bonds[k];
@@ -713,7 +731,9 @@ pabd_status finalize_scene(pabd_scene* s) {
         ok &= alloc_arr(s, d.adj_off, N + 1) && alloc_arr(s, d.adj_nbr, adj_nbr.size());
     }
     if (d.Nal) ok &= alloc_arr(s, d.al_st0, Nc) && alloc_arr(s, d.al_st1, Nc) && alloc_arr(s, d.al_par, Nc);
-    if (!sta_off.empty()) ok &= alloc_arr(s, d.sta_off, N + 1) && alloc_arr(s, d.sta_id, sta_id.size());
+    if (!sta_off.empty())
+        ok &= alloc_arr(s, d.sta_off, N + 1) && alloc_arr(s, d.sta_id, sta_id.size()) &&
+              alloc_arr(s, d.sta_body, sta_body.size());
     if (p.resid_tol > 0) ok &= alloc_arr(s, d.sweep_ctl, 4) && alloc_arr(s, d.group_done, d.G);
     if (p.broadphase == 1) {
         const size_t ntile = ((size_t)N + 1023) / 1024 + 1;
@@ -758,6 +778,7 @@ pabd_status finalize_scene(pabd_scene* s) {
     if (d.sta_off) {
         CK(up(d.sta_off, sta_off.data(), sizeof(int) * (N + 1)));
         CK(up(d.sta_id, sta_id.data(), sizeof(int) * sta_id.size()));
+        CK(up(d.sta_body, sta_body.data(), sizeof(int) * sta_body.size()));
     }
     CK(cudaMemsetAsync(d.ctr, 0, sizeof(int) * C_COUNT, st));
     CK(cudaMemsetAsync(d.step_index, 0, sizeof(long long), st));

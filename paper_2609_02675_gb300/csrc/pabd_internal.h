@@ -85,6 +85,7 @@ struct Dev {
     float4 *he;                 // (hx, hy, hz, dhat)
     float4 *xs;                 // expansion point of the per-body system (x, y, z, 0), see sys_init
     int *bflags, *group, *group_off;
+    int small_groups;           // every group has at most 4096 bodies: one warp per group sums residuals
     int *large_ids;             // this step's bodies off the grid (C_NLARGE of them), or null
     int *adj_off, *adj_nbr;     // sorted partners joined by user bonds (no contact), or null
     double *resid_body, *resid_group;
@@ -107,6 +108,7 @@ struct Dev {
     // by end id (2 bond + side), fixed at creation -- the CSR is these plus the step's ground
     // contacts (k_csr_ground); null otherwise
     int *sta_off, *sta_id;
+    int *sta_body;              // the body of each entry of sta_id
     int light_sorted;           // 1: the sweeps take the light bodies in Dev::order; 0: in body order
     int *order;                 // this step's light bodies by (class, end count), C_NLIGHT of them
     int *bin_cnt, *bin_cur;     // per bin of the light order: bodies, and the blocks' reservations
@@ -213,6 +215,8 @@ int scan_scratch_ints(int n_cap);
 // zeroes the step's counters and accumulation scratch; precedes launch_collision / launch_csr
 void launch_step_reset(const Dev& d, cudaStream_t st, long long* launches);
 void launch_collision(const Dev& d, cudaStream_t st, long long* launches);
+// the front of a step in a ground-only scene: collision, CSR and predictor (k_collision.cu)
+void launch_ground_front(const Dev& d, cudaStream_t st, long long* launches);
 // LBVH pairs from this step's boxes (after k_aabb): the same output as the grid's pair stage
 void launch_lbvh_pairs(const Dev& d, cudaStream_t st, long long* launches);
 cudaError_t setup_pair_sort();
