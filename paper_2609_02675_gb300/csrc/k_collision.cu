@@ -698,24 +698,54 @@ static inline int nblk(int n) { return (n + CT - 1) / CT > 0 ? (n + CT - 1) / CT
 
 // ---- the front of a step in scenes whose only contacts are with the ground ----
 //
-// Three launches in place of the AABB, ground-count, contact-write, CSR and predictor kernels
-// (the same arithmetic, fewer launch boundaries): k_ground_prelude per body, the scan of the
-// ground-contact counts, k_ground_bonds_csr per static end and per body.
+// Three launches in place of the AABB, ground-count, scan, contact-write, CSR and predictor
+// kernels (the same arithmetic, fewer launch boundaries): k_ground_prelude per body, the scan of
+// its blocks' totals, k_ground_bonds_csr per static end and per body.
 
-// per body: AABB and inflation, ground contacts counted, predictor
-__global__ void k_ground_prelude(Dev d) {
+// per body: AABB and inflation, ground contacts counted, predictor; per block of CT bodies, the
+// exclusive prefix of the counts inside the block (Dev::gnd_loc) and their total (Dev::gnd_blk)
+__global__ void __launch_bounds__(CT) k_ground_prelude(Dev d) {
     pdl_enter();
+    __shared__ int wsum[CT / 32];
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= d.N) return;
-    aabb_body(d, b);
     int n = 0;
-    if (d.p.has_ground && !(d.bflags[b] & BF_PINNED)) {
-        FBox fa;
-        load_box(d, b, fa);
-        n = ground_corners(d, fa, b, [](int, int, const float*, const float*, const float*, int) {});
+    if (b < d.N) {
+        aabb_body(d, b);
+        if (d.p.has_ground && !(d.bflags[b] & BF_PINNED)) {
+            FBox fa;
+            load_box(d, b, fa);
+            n = ground_corners(d, fa, b, [](int, int, const float*, const float*, const float*, int) {});
+        }
+        d.gnd_cnt[b] = n;
+        predict_body(d, b);
     }
-    d.gnd_cnt[b] = n;
-    predict_body(d, b);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int inc = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < CT / 32 ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < CT / 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        if (lane < CT / 32) wsum[lane] = w;
+    }
+    __syncthreads();
+    if (b < d.N) d.gnd_loc[b] = (warp ? wsum[warp - 1] : 0) + inc - n;
+    if (threadIdx.x == 0) d.gnd_blk[blockIdx.x] = wsum[CT / 32 - 1];
+}
+
+// ground contacts of the bodies before b (b <= N), from the prelude's block prefixes and the
+// scan of its block totals (Dev::gnd_bof, whose last entry is the total)
+__device__ __forceinline__ int gnd_prefix(const Dev& d, int b) {
+    return b < d.N ? d.gnd_bof[b / CT] + d.gnd_loc[b] : d.gnd_bof[(d.N + CT - 1) / CT];
 }
 
 // After the scan: items [0, Ns) are the static ends in Dev::sta_id order -- end e of body b
@@ -730,7 +760,7 @@ __global__ void k_ground_bonds_csr(Dev d) {
     for (int tt = blockIdx.x * blockDim.x + threadIdx.x; tt < items; tt += gridDim.x * blockDim.x) {
         if (tt < Ns) {
             const int b = d.sta_body[tt];
-            const int slot = tt + min(d.gnd_off[b], cap);
+            const int slot = tt + min(gnd_prefix(d, b), cap);
             const int id = d.sta_id[tt], bond = id >> 1;
             d.end_id[slot] = id;
             d.end_pos[id] = slot;
@@ -739,10 +769,11 @@ __global__ void k_ground_bonds_csr(Dev d) {
             continue;
         }
         const int b = tt - Ns;
-        const int g0 = min(d.gnd_off[b], cap);
+        const int gb = gnd_prefix(d, b), g0 = min(gb, cap);
+        d.gnd_off[b] = gb;
         d.end_off[b] = d.sta_off[b] + g0;
         if (b == nb) continue;
-        const int gn = min(d.gnd_off[b + 1], cap) - g0;
+        const int gn = min(gnd_prefix(d, b + 1), cap) - g0;
         if (gn > 0) {
             FBox fa;
             load_box(d, b, fa);
@@ -759,7 +790,7 @@ __global__ void k_ground_bonds_csr(Dev d) {
         if (d.sta_off[b + 1] - d.sta_off[b] + gn > HEAVY_ENDS) d.heavy[atomicAdd(&d.ctr[C_NHEAVY], 1)] = b;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        int nk = d.gnd_off[nb];
+        int nk = gnd_prefix(d, nb);
         if (nk > cap) { atomicOr(&d.ctr[C_STATUS], ST_CAPACITY); nk = cap; }
         d.ctr[C_NPC] = 0;
         d.ctr[C_NGC] = nk;
@@ -769,7 +800,7 @@ __global__ void k_ground_bonds_csr(Dev d) {
 
 void launch_ground_front(const Dev& d, cudaStream_t st, long long* launches) {
     launch_pdl(k_ground_prelude, dim3(nblk(d.N)), dim3(CT), 0, st, d);
-    scan_exclusive(d.gnd_cnt, d.gnd_off, nullptr, d.N, d.scan_scratch, st, launches);
+    scan_exclusive(d.gnd_blk, d.gnd_bof, nullptr, nblk(d.N), d.scan_scratch, st, launches);
     launch_pdl(k_ground_bonds_csr, dim3(stride_grid((long long)d.cap_ends + d.N + 1, CT)), dim3(CT), 0, st, d);
     *launches += 2;
 }

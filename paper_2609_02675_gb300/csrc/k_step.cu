@@ -41,13 +41,7 @@ __device__ __forceinline__ float4 mat_to_quat(const float* R) {
 
 // Velocity recovery (Alg. 1, Sec. 4.4): v = (c^{n+1} - c^n)/h;
 // [w]x = skew part of (A^{n+1} - A^n)(A^n)^T / h; Q^{n+1} = quat(A^{n+1}), sign-continuous.
-__global__ void k_finalize(Dev d, const float4* __restrict__ qf, int dyn) {
-    pdl_enter();
-    // under a residual threshold the last iterate sits in the buffer of the sweep count's parity
-    if (dyn) qf = (d.sweep_ctl[0] & 1) ? d.qb : d.qa;
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b == 0) atomicAdd((unsigned long long*)d.step_index, 1ull);
-    if (b >= d.N) return;
+__device__ __forceinline__ void finalize_body(const Dev& d, int b, const float4* __restrict__ qf) {
     if ((d.bflags[b] & BF_PINNED) || held(d, b)) return;  // (a held group keeps its state)
     float4 n0 = d.qn[3 * b], n1 = d.qn[3 * b + 1], n2 = d.qn[3 * b + 2];
     float4 f0 = qf[3 * b], f1 = qf[3 * b + 1], f2 = qf[3 * b + 2];
@@ -79,6 +73,16 @@ __global__ void k_finalize(Dev d, const float4* __restrict__ qf, int dyn) {
     }
     d.quat[b] = Q;
     d.qn[3 * b] = f0; d.qn[3 * b + 1] = f1; d.qn[3 * b + 2] = f2;
+}
+
+__global__ void k_finalize(Dev d, const float4* __restrict__ qf, int dyn) {
+    pdl_enter();
+    // under a residual threshold the last iterate sits in the buffer of the sweep count's parity
+    if (dyn) qf = (d.sweep_ctl[0] & 1) ? d.qb : d.qa;
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b == 0) atomicAdd((unsigned long long*)d.step_index, 1ull);
+    if (b >= d.N) return;
+    finalize_body(d, b, qf);
 }
 
 // Drive anchors at t = (step + 1) h: x_i = x_i0 + arm (cos th r + sin th (u x r)),
@@ -381,15 +385,18 @@ void launch_csr(const Dev& d, cudaStream_t st, long long* launches) {
     *launches += 4;
 }
 
-// The same sums with one warp per group, for scenes of small groups (a block per group leaves
-// most of its threads idle and takes one block slot per group): lane l of the warp plays the
-// block's threads l, l + 32, ... (its RES_T / 32 accumulators), each accumulator is combined by
-// the same xor tree and the results added in the same order -- the block's value bit for bit.
-__global__ void k_group_resid_warp(Dev d) {
+// Scenes of small groups (a block per group leaves most of its threads idle and takes one block
+// slot per group): one warp per group recovers its bodies' velocities (finalize_body) and sums
+// their residuals.  Lane l plays the residual block's threads l, l + 32, ... (its RES_T / 32
+// accumulators), each accumulator is combined by the same xor tree and the results added in the
+// same order -- the block's value bit for bit.
+__global__ void k_finalize_groups(Dev d, const float4* __restrict__ qf) {
     pdl_enter();
     const int g = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (g == 0 && lane == 0) atomicAdd((unsigned long long*)d.step_index, 1ull);
     if (g >= d.G) return;
     const int s = d.group_off[g], e = d.group_off[g + 1];
+    for (int b = s + lane; b < e; b += 32) finalize_body(d, b, qf);
     double acc[RES_T / 32];
 #pragma unroll
     for (int w = 0; w < RES_T / 32; ++w) {
@@ -407,9 +414,13 @@ __global__ void k_group_resid_warp(Dev d) {
 }
 
 void launch_finalize(const Dev& d, const float4* q_fin, cudaStream_t st, long long* launches) {
+    if (d.small_groups) {
+        launch_pdl(k_finalize_groups, dim3(nblk(32 * (d.G > 0 ? d.G : 1))), dim3(ST_T), 0, st, d, q_fin);
+        *launches += 1;
+        return;
+    }
     launch_pdl(k_finalize, dim3(nblk(d.N)), dim3(ST_T), 0, st, d, q_fin, 0);
-    if (d.small_groups) launch_pdl(k_group_resid_warp, dim3(nblk(32 * (d.G > 0 ? d.G : 1))), dim3(ST_T), 0, st, d);
-    else launch_pdl(k_group_resid, dim3(d.G > 0 ? d.G : 1), dim3(RES_T), 0, st, d);
+    launch_pdl(k_group_resid, dim3(d.G > 0 ? d.G : 1), dim3(RES_T), 0, st, d);
     *launches += 2;
 }
 

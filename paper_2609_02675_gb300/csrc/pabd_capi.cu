@@ -733,7 +733,8 @@ pabd_status finalize_scene(pabd_scene* s) {
     if (d.Nal) ok &= alloc_arr(s, d.al_st0, Nc) && alloc_arr(s, d.al_st1, Nc) && alloc_arr(s, d.al_par, Nc);
     if (!sta_off.empty())
         ok &= alloc_arr(s, d.sta_off, N + 1) && alloc_arr(s, d.sta_id, sta_id.size()) &&
-              alloc_arr(s, d.sta_body, sta_body.size());
+              alloc_arr(s, d.sta_body, sta_body.size()) && alloc_arr(s, d.gnd_loc, N) &&
+              alloc_arr(s, d.gnd_blk, (N + 255) / 256 + 1) && alloc_arr(s, d.gnd_bof, (N + 255) / 256 + 1);
     if (p.resid_tol > 0) ok &= alloc_arr(s, d.sweep_ctl, 4) && alloc_arr(s, d.group_done, d.G);
     if (p.broadphase == 1) {
         const size_t ntile = ((size_t)N + 1023) / 1024 + 1;

@@ -109,6 +109,9 @@ struct Dev {
     // contacts (k_csr_ground); null otherwise
     int *sta_off, *sta_id;
     int *sta_body;              // the body of each entry of sta_id
+    // ground contacts of the bodies before b in the fused front of a ground-only scene: the
+    // prefix inside b's block of 256 bodies, the blocks' totals and their exclusive scan
+    int *gnd_loc, *gnd_blk, *gnd_bof;
     int light_sorted;           // 1: the sweeps take the light bodies in Dev::order; 0: in body order
     int *order;                 // this step's light bodies by (class, end count), C_NLIGHT of them
     int *bin_cnt, *bin_cur;     // per bin of the light order: bodies, and the blocks' reservations
