@@ -385,8 +385,9 @@ void launch_csr(const Dev& d, cudaStream_t st, long long* launches) {
     *launches += 4;
 }
 
-// Scenes of small groups (a block per group leaves most of its threads idle and takes one block
-// slot per group): one warp per group recovers its bodies' velocities (finalize_body) and sums
+// Scenes whose groups have at most 128 bodies (a block per group would leave most of its threads
+// idle and take one block slot per group; a larger group is better spread over the per-body
+// kernel): one warp per group recovers its bodies' velocities (finalize_body) and sums
 // their residuals.  Lane l plays the residual block's threads l, l + 32, ... (its RES_T / 32
 // accumulators), each accumulator is combined by the same xor tree and the results added in the
 // same order -- the block's value bit for bit.

@@ -546,7 +546,7 @@ pabd_status finalize_scene(pabd_scene* s) {
     }
     for (int g = 1; g <= d.G; ++g) if (group_off[g] < group_off[g - 1]) group_off[g] = group_off[g - 1];
     d.small_groups = 1;
-    for (int g = 0; g < d.G; ++g) if (group_off[g + 1] - group_off[g] > 4096) d.small_groups = 0;
+    for (int g = 0; g < d.G; ++g) if (group_off[g + 1] - group_off[g] > 128) d.small_groups = 0;
     d.Nlarge = (int)large.size();
     bool cap_below_widest = false;
     p.cell = (float)grid_cell_cap(s->bodies, flags, ds, &cap_below_widest);

@@ -85,7 +85,7 @@ struct Dev {
     float4 *he;                 // (hx, hy, hz, dhat)
     float4 *xs;                 // expansion point of the per-body system (x, y, z, 0), see sys_init
     int *bflags, *group, *group_off;
-    int small_groups;           // every group has at most 4096 bodies: one warp per group sums residuals
+    int small_groups;           // every group has at most 128 bodies: one warp per group finalizes it
     int *large_ids;             // this step's bodies off the grid (C_NLARGE of them), or null
     int *adj_off, *adj_nbr;     // sorted partners joined by user bonds (no contact), or null
     double *resid_body, *resid_group;
