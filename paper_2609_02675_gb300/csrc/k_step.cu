@@ -303,23 +303,51 @@ cudaError_t setup_csr_kernels() {
 // RES_T threads per group, fixed per-thread strides, warp shuffle tree, warps summed in
 // order by thread 0 (deterministic)
 constexpr int RES_T = 128;
-__global__ void __launch_bounds__(RES_T) k_group_resid(Dev d) {
-    pdl_enter();
-    __shared__ double part[RES_T / 32];
-    const int g = blockIdx.x;
-    if (g >= d.G) return;
-    const int s = d.group_off[g], e = d.group_off[g + 1];
+
+// the sum of resid_body over [s, e) in the fixed order: RES_T-strided per thread, a warp xor
+// tree, the warps in order (thread 0 returns it)
+__device__ __forceinline__ double block_resid_sum(const Dev& d, int s, int e, double* part) {
     double acc = 0.0;
     for (int b = s + threadIdx.x; b < e; b += RES_T) acc += d.resid_body[b];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
+    double t = 0.0;
+    if (threadIdx.x == 0)
         for (int w = 0; w < RES_T / 32; ++w) t += part[w];
-        d.resid_group[g] = sqrt(t);
-    }
+    return t;
+}
+
+// Scenes with a group of more than RES_CHUNK bodies: a block per chunk of at most RES_CHUNK
+// bodies of one group (Dev::res_chunk, the chunks of each group in order) sums it as
+// k_group_resid sums a group, then each group adds its chunks' sums in order.  A group of one
+// chunk gets k_group_resid's value bit for bit; a larger group is summed by as many blocks as it
+// has chunks instead of by one.
+__global__ void __launch_bounds__(RES_T) k_resid_chunks(Dev d) {
+    pdl_enter();
+    __shared__ double part[RES_T / 32];
+    const int2 c = d.res_chunk[blockIdx.x];
+    const double t = block_resid_sum(d, c.x, c.y, part);
+    if (threadIdx.x == 0) d.res_part[blockIdx.x] = t;
+}
+
+__global__ void k_resid_groups(Dev d) {
+    pdl_enter();
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= d.G) return;
+    double t = 0.0;
+    for (int c = d.res_coff[g]; c < d.res_coff[g + 1]; ++c) t += d.res_part[c];
+    d.resid_group[g] = sqrt(t);
+}
+
+__global__ void __launch_bounds__(RES_T) k_group_resid(Dev d) {
+    pdl_enter();
+    __shared__ double part[RES_T / 32];
+    const int g = blockIdx.x;
+    if (g >= d.G) return;
+    const double t = block_resid_sum(d, d.group_off[g], d.group_off[g + 1], part);
+    if (threadIdx.x == 0) d.resid_group[g] = sqrt(t);
 }
 
 void launch_predict(const Dev& d, cudaStream_t st, long long* launches) {
@@ -421,6 +449,12 @@ void launch_finalize(const Dev& d, const float4* q_fin, cudaStream_t st, long lo
         return;
     }
     launch_pdl(k_finalize, dim3(nblk(d.N)), dim3(ST_T), 0, st, d, q_fin, 0);
+    if (d.res_chunk) {
+        launch_pdl(k_resid_chunks, dim3(d.n_res_chunks), dim3(RES_T), 0, st, d);
+        launch_pdl(k_resid_groups, dim3(nblk(d.G)), dim3(ST_T), 0, st, d);
+        *launches += 3;
+        return;
+    }
     launch_pdl(k_group_resid, dim3(d.G > 0 ? d.G : 1), dim3(RES_T), 0, st, d);
     *launches += 2;
 }

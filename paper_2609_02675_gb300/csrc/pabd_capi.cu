@@ -411,8 +411,8 @@ pabd_status autotune_default(pabd_scene* s) {
         const int mode = c < 2 ? 2 : 1;
         dd.light_sorted = (c & 1) ? 0 : 1;
         if ((!tune_mode && mode != s->mode) || (!tune_order && dd.light_sorted != d.light_sorted)) continue;
-        float tot = 0.f;
-        for (int r = 0; r < 3; ++r) {
+        float tot = 1e30f;
+        for (int r = 0; r < 5; ++r) {
             // the one-launch sweeps' chunk counters, as the step's reset leaves them (each
             // sweep zeroes the next sweep's counter, so a pass must start from clean ones)
             CK(cudaMemsetAsync(dd.ctr + C_SWEEP_NEXT, 0, 2 * sizeof(int), s->st));
@@ -432,10 +432,11 @@ pabd_status autotune_default(pabd_scene* s) {
             CK(cudaEventSynchronize(e1));
             float t = 0.f;
             CK(cudaEventElapsedTime(&t, e0, e1));
-            if (r > 0) tot += t;  // the first pass warms the caches
+            if (r > 0) tot = std::min(tot, t);  // the first pass warms the caches; the fastest
+                                                // of the others (least disturbed) is the figure
         }
         CK(cudaGetLastError());
-        s->tune_ns[c] = (long long)(1e6 * tot / (2.0 * n_it));
+        s->tune_ns[c] = (long long)(1e6 * tot / (double)n_it);
         if (tot < best) { best = tot; s->mode = mode; d.light_sorted = dd.light_sorted; }
     }
     cudaEventDestroy(e0);
@@ -546,7 +547,23 @@ pabd_status finalize_scene(pabd_scene* s) {
     }
     for (int g = 1; g <= d.G; ++g) if (group_off[g] < group_off[g - 1]) group_off[g] = group_off[g - 1];
     d.small_groups = 1;
-    for (int g = 0; g < d.G; ++g) if (group_off[g + 1] - group_off[g] > 128) d.small_groups = 0;
+    bool big_group = false;
+    for (int g = 0; g < d.G; ++g) {
+        if (group_off[g + 1] - group_off[g] > 128) d.small_groups = 0;
+        if (group_off[g + 1] - group_off[g] > RES_CHUNK) big_group = true;
+    }
+    std::vector<int2> res_chunk;
+    std::vector<int> res_coff;
+    if (big_group) {
+        res_coff.assign(d.G + 1, 0);
+        for (int g = 0; g < d.G; ++g) {
+            for (int b = group_off[g]; b < group_off[g + 1]; b += RES_CHUNK)
+                res_chunk.push_back(make_int2(b, std::min(b + RES_CHUNK, group_off[g + 1])));
+            if (group_off[g + 1] == group_off[g]) res_chunk.push_back(make_int2(group_off[g], group_off[g]));
+            res_coff[g + 1] = (int)res_chunk.size();
+        }
+        d.n_res_chunks = (int)res_chunk.size();
+    }
     d.Nlarge = (int)large.size();
     bool cap_below_widest = false;
     p.cell = (float)grid_cell_cap(s->bodies, flags, ds, &cap_below_widest);
@@ -704,6 +721,9 @@ pabd_status finalize_scene(pabd_scene* s) {
     ok &= alloc_arr(s, d.group_hold, d.G);
     ok &= alloc_arr(s, d.large_ids, N);
     ok &= alloc_arr(s, d.resid_body, N) && alloc_arr(s, d.resid_group, d.G);
+    if (!res_chunk.empty())
+        ok &= alloc_arr(s, d.res_chunk, res_chunk.size()) && alloc_arr(s, d.res_coff, d.G + 1) &&
+              alloc_arr(s, d.res_part, res_chunk.size());
     ok &= alloc_arr(s, d.bmeta, d.cap_bonds) && alloc_arr(s, d.bxi, d.cap_bonds) && alloc_arr(s, d.bxj, d.cap_bonds) &&
           alloc_arr(s, d.bn, d.cap_bonds);
     ok &= alloc_arr(s, d.drv, 3 * d.Ndrive) && alloc_arr(s, d.drv_t, d.Ndrive) && alloc_arr(s, d.drv_bond, d.Ndrive);
@@ -764,6 +784,10 @@ pabd_status finalize_scene(pabd_scene* s) {
     CK(up(d.bflags, flags.data(), sizeof(int) * N));
     CK(up(d.group, group.data(), sizeof(int) * N));
     CK(up(d.group_off, group_off.data(), sizeof(int) * (d.G + 1)));
+    if (d.res_chunk) {
+        CK(up(d.res_chunk, res_chunk.data(), sizeof(int2) * res_chunk.size()));
+        CK(up(d.res_coff, res_coff.data(), sizeof(int) * (d.G + 1)));
+    }
     CK(up(d.bmeta, bmeta.data(), sizeof(int4) * Nc));
     CK(up(d.bxi, bxi.data(), sizeof(float4) * Nc));
     CK(up(d.bxj, bxj.data(), sizeof(float4) * Nc));

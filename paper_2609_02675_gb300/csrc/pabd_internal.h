@@ -71,6 +71,7 @@ constexpr int HEAVY_BLOCKS = 152;
 // the longest warps start first (the launch does not end on them).  2 * END_BINS bins; which
 // lanes take a body never changes its arithmetic.
 constexpr int END_BINS = HEAVY_ENDS + 1;
+constexpr int RES_CHUNK = 4096;
 
 struct Dev {
     Params p;
@@ -86,6 +87,12 @@ struct Dev {
     float4 *xs;                 // expansion point of the per-body system (x, y, z, 0), see sys_init
     int *bflags, *group, *group_off;
     int small_groups;           // every group has at most 128 bodies: one warp per group finalizes it
+    // a group of more than RES_CHUNK bodies: its residual summed by chunks (k_resid_chunks),
+    // (start, end) of each chunk, each group's first chunk, the chunks' sums; null otherwise
+    int2 *res_chunk;
+    int *res_coff;
+    double *res_part;
+    int n_res_chunks;
     int *large_ids;             // this step's bodies off the grid (C_NLARGE of them), or null
     int *adj_off, *adj_nbr;     // sorted partners joined by user bonds (no contact), or null
     double *resid_body, *resid_group;
