@@ -259,7 +259,8 @@ __global__ void k_pair_count(Dev d) {
                 n += (j < d.N && pair_ok(d, i, j, gi, fi, li, hi_)) ? 1 : 0;
             }
         } else {
-            n = lane_partners(d, i, lane, [](int, int) {});
+            int* st = d.pair_stash ? d.pair_stash + (size_t)(32 * i + lane) * PAIR_STASH : nullptr;
+            n = lane_partners(d, i, lane, [&](int j, int k) { if (st && k < PAIR_STASH) st[k] = j; });
         }
     }
     if (d.lane_cnt) d.lane_cnt[32 * i + lane] = n;
@@ -289,9 +290,15 @@ __global__ void k_pair_write(Dev d) {
         } else {
             const int mine = d.lane_cnt ? d.lane_cnt[32 * i + lane] : lane_partners(d, i, lane, [](int, int) {});
             const int base = s + warp_excl(mine, lane);
-            lane_partners(d, i, lane, [&](int j, int k) {
-                if (base + k < cap) d.pairs[base + k] = make_int2(i, j);
-            });
+            if (d.pair_stash && d.lane_cnt && mine <= PAIR_STASH) {  // the partners found while counting
+                const int* st = d.pair_stash + (size_t)(32 * i + lane) * PAIR_STASH;
+                for (int k = 0; k < mine; ++k)
+                    if (base + k < cap) d.pairs[base + k] = make_int2(i, st[k]);
+            } else {
+                lane_partners(d, i, lane, [&](int j, int k) {
+                    if (base + k < cap) d.pairs[base + k] = make_int2(i, j);
+                });
+            }
             __syncwarp();
             const int e = min(d.pair_off[i + 1], cap);
             if (e - s <= 32) {  // the slice sorted by j: each partner's rank among the slice
@@ -390,8 +397,17 @@ __global__ void k_ml_pair_count(Dev d) {
     pdl_enter();
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (i >= d.N || !d.p.body_contacts || d.cell[i].w < 0) return;
-    int n = lane_partners_ml(d, i, lane, [](int, int) {}, [&](int j) { atomicAdd(&d.pair_cnt[j], 1); });
+    int* st = d.pair_stash ? d.pair_stash + (size_t)(32 * i + lane) * PAIR_STASH : nullptr;
+    int tot = 0;  // entries: own partners and deliveries, in the order found
+    int n = lane_partners_ml(d, i, lane,
+        [&](int j, int) { if (st && tot < PAIR_STASH) st[tot] = j; ++tot; },
+        [&](int j) {
+            atomicAdd(&d.pair_cnt[j], 1);
+            if (st && tot < PAIR_STASH) st[tot] = j | STASH_DELIVER;
+            ++tot;
+        });
     d.lane_cnt[32 * i + lane] = n;
+    if (d.lane_tot) d.lane_tot[32 * i + lane] = tot;
     n = warp_sum(n);
     if (lane == 0) {
         d.pair_own[i] = n;
@@ -408,12 +424,23 @@ __global__ void k_ml_pair_write(Dev d) {
     const int cap = d.cap_pairs;
     if (d.p.body_contacts && d.cell[i].w >= 0) {
         const int base = d.pair_off[i] + warp_excl(d.lane_cnt[32 * i + lane], lane);
-        lane_partners_ml(d, i, lane,
-            [&](int j, int k) { if (base + k < cap) d.pair_j[base + k] = j; },
-            [&](int j) {
-                const int at = d.pair_off[j] + d.pair_own[j] + atomicAdd(&d.pair_cur[j], 1);
-                if (at < cap) d.pair_j[at] = i;
-            });
+        auto own = [&](int j, int k) { if (base + k < cap) d.pair_j[base + k] = j; };
+        auto deliver = [&](int j) {
+            const int at = d.pair_off[j] + d.pair_own[j] + atomicAdd(&d.pair_cur[j], 1);
+            if (at < cap) d.pair_j[at] = i;
+        };
+        const int tot = d.pair_stash && d.lane_tot ? d.lane_tot[32 * i + lane] : PAIR_STASH + 1;
+        if (tot <= PAIR_STASH) {  // the entries found while counting
+            const int* st = d.pair_stash + (size_t)(32 * i + lane) * PAIR_STASH;
+            int k = 0;
+            for (int t = 0; t < tot; ++t) {
+                const int v = st[t];
+                if (v & STASH_DELIVER) deliver(v & ~STASH_DELIVER);
+                else own(v, k++);
+            }
+        } else {
+            lane_partners_ml(d, i, lane, own, deliver);
+        }
     }
     if (i == d.N - 1 && lane == 0) {
         const int tot = d.pair_off[d.N];

@@ -739,6 +739,8 @@ pabd_status finalize_scene(pabd_scene* s) {
     ok &= alloc_arr(s, d.pair_cnt, N) && alloc_arr(s, d.pair_off, N + 1) && alloc_arr(s, d.pairs, d.cap_pairs);
     ok &= alloc_arr(s, d.brec_lo, N) && alloc_arr(s, d.brec_hi, N) && alloc_arr(s, d.brec_cell, N);
     ok &= alloc_arr(s, d.lane_cnt, (size_t)32 * N);
+    if (ds.body_contacts && p.broadphase == 0)
+        ok &= alloc_arr(s, d.pair_stash, (size_t)32 * PAIR_STASH * N) && alloc_arr(s, d.lane_tot, (size_t)32 * N);
     ok &= alloc_arr(s, d.npc, d.cap_pairs) && alloc_arr(s, d.npc_off, d.cap_pairs + 1);
     ok &= alloc_arr(s, d.gnd_cnt, N) && alloc_arr(s, d.gnd_off, N + 1);
     ok &= alloc_arr(s, d.ctr, C_COUNT) && alloc_arr(s, d.step_index, 1);

@@ -72,6 +72,8 @@ constexpr int HEAVY_BLOCKS = 152;
 // lanes take a body never changes its arithmetic.
 constexpr int END_BINS = HEAVY_ENDS + 1;
 constexpr int RES_CHUNK = 4096;
+constexpr int PAIR_STASH = 4;
+constexpr int STASH_DELIVER = 0x40000000;
 
 struct Dev {
     Params p;
@@ -134,6 +136,11 @@ struct Dev {
     float4 *brec_lo, *brec_hi;  // per bucket slot: (lo, body id bits), (hi, group bits)
     int4 *brec_cell;            // per bucket slot: (cell x, y, z, flags)
     int *lane_cnt;              // per body x 32 lanes: partners found by each lane
+    // per body x 32 lanes: the first PAIR_STASH partners each lane found while counting (a
+    // partner delivered to a smaller id tagged by STASH_DELIVER), and the lane's number of
+    // entries, so that writing the pairs replays them instead of scanning the cells again (a
+    // lane with more rescans); null where the pair kernels run without them
+    int *pair_stash, *lane_tot;
     int *pair_cnt, *pair_off;
     int2 *pairs;
     int *npc, *npc_off, *gnd_cnt, *gnd_off;
