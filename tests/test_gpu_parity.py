@@ -180,6 +180,27 @@ def test_pile_full_size_sampled(P):
     g.close()
 
 
+def test_large_group_residual_and_steps(P):
+    """One group of 5200 bodies (a stacked pile: more bodies than one residual block sums, so
+    the group's residual is summed by 4096-body chunks and their sums added in order): after 6
+    steps the layers press on each other; two teacher-forced steps stay within tolerance, and
+    the group's last-sweep residual (a8, Sec. 4.2) matches the oracle's."""
+    sc = S.box_pile(nx=20, ny=13, nz=20, stacked=True)
+    assert sc.n_bodies > 4096
+    ref = O.OracleScene(sc)
+    ref.step(6)
+    g = P.Scene(sc)
+    he = _he(sc)
+    grp = np.asarray(sc.bodies["group"])
+    for _ in range(2):
+        a, b = teacher_forced_step(g, ref)
+        assert len(ref.contacts()[0]) > 10000
+        assert rel_err(a, b, he) < REL_TOL
+        assert ref.residual()[0] > 0.0
+        assert residual_ratio(g.residual(), ref.residual(), a, b, he, grp) < 1.0
+    g.close()
+
+
 def test_trees_full_size_sampled(P):
     """All 4096 batched trees (139 690 bodies) in the launch configuration the bench times:
     the oracle steps every 64th tree (a tree steps alone exactly as inside the batch) to the
