@@ -24,32 +24,55 @@ namespace pabd {
 constexpr int BOND_T = 256;
 constexpr int SOLVE_T = 128;
 
+// What a bond's records need that no sweep writes: its metadata and material points, the CSR
+// slots of its ends and the ends' body flags (set at creation or by this step's front).
+struct BondStatic {
+    int4 m;
+    float4 xi, xj;
+    int p0, p1, fi, fj;
+};
+
+__device__ __forceinline__ BondStatic bond_static(const Dev& d, int b) {
+    BondStatic s;
+    s.m = d.bmeta[b];
+    s.xi = d.bxi[b];
+    s.xj = d.bxj[b];
+    s.p0 = d.end_pos[2 * b];
+    s.p1 = s.m.y >= 0 ? d.end_pos[2 * b + 1] : -1;
+    s.fi = d.bflags[s.m.x];
+    s.fj = s.m.y >= 0 ? d.bflags[s.m.y] : BF_PINNED;
+    return s;
+}
+
 // one bond's end records from q^k
-__device__ __forceinline__ void bond_one(const Dev& d, const float4* __restrict__ q, int it, int b) {
-    const int4 m = d.bmeta[b];
-    const float4 xi = d.bxi[b], xj = d.bxj[b];
+__device__ __forceinline__ void bond_one(const Dev& d, const float4* __restrict__ q, int it, int b,
+                                         const BondStatic& s) {
     float c[3], A[9];
-    ld_q(q, m.x, c, A);
-    const int4 mm = make_int4(m.x, m.y, m.z, b);
-    const int fi = d.bflags[m.x], fj = m.y >= 0 ? d.bflags[m.y] : BF_PINNED;
+    ld_q(q, s.m.x, c, A);
+    const int4 mm = make_int4(s.m.x, s.m.y, s.m.z, b);
     // a bond between two fixed ends is advanced by the final update alone (as in the sweep kernels)
-    const bool writer = !(fi & BF_PINNED) || !(fj & BF_PINNED);
+    const bool writer = !(s.fi & BF_PINNED) || !(s.fj & BF_PINNED);
     float f[3];
-    const float w = end_force(d, q, m.x, c, A, mm, xi, xj, it, writer, f);
-    const int p0 = d.end_pos[2 * b], p1 = (m.y >= 0) ? d.end_pos[2 * b + 1] : -1;
-    if (p0 >= 0) d.ends[p0] = make_float4(w, f[0], f[1], f[2]);
-    if (p1 >= 0) d.ends[p1] = make_float4(w, -f[0], -f[1], -f[2]);
+    const float w = end_force(d, q, s.m.x, c, A, mm, s.xi, s.xj, it, writer, f);
+    if (s.p0 >= 0) d.ends[s.p0] = make_float4(w, f[0], f[1], f[2]);
+    if (s.p1 >= 0) d.ends[s.p1] = make_float4(w, -f[0], -f[1], -f[2]);
 }
 
 // (strides over this step's bonds with a grid capped at GS_BLOCKS blocks: the bond capacity
-// holds room for every possible contact, far more than a step has)
+// holds room for every possible contact, far more than a step has).  Each thread loads its
+// first bond's static part before it waits for the previous sweep (pdl_enter), so that the
+// loads overlap that sweep's last blocks; q^k and the augmented Lagrangian state are read after.
 __global__ void __launch_bounds__(BOND_T) k_bond(Dev d, const float4* __restrict__ q, int it) {
+    const int nb = d.ctr[C_NBONDS];  // (set by the step's front, before the sweeps)
+    const int b0 = blockIdx.x * blockDim.x + threadIdx.x;
+    BondStatic s0;
+    if (b0 < nb) s0 = bond_static(d, b0);
     pdl_enter();
     // the solve launch that follows hands out its light bodies from this counter (the previous
     // solve launch has finished: pdl_enter waited for it)
     if (blockIdx.x == 0 && threadIdx.x == 0) d.ctr[C_SOLVE_NEXT] = 0;
-    const int nb = d.ctr[C_NBONDS];
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) bond_one(d, q, it, b);
+    if (b0 < nb) bond_one(d, q, it, b0, s0);
+    for (int b = b0 + gridDim.x * blockDim.x; b < nb; b += gridDim.x * blockDim.x) bond_one(d, q, it, b, bond_static(d, b));
 }
 
 // add the records of ends p0, p0 + stride, ... < e1 in that order, each loaded one round

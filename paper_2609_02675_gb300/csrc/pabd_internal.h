@@ -176,13 +176,22 @@ __device__ __forceinline__ bool held(const Dev& d, int b) { return d.group_hold[
 
 // ---- programmatic dependent launch ----
 // A kernel launched by launch_pdl may be launched while its predecessor on the stream is still
-// finishing: every kernel of the step calls pdl_enter() first, which waits until its
-// predecessor has completed and its writes are visible (a no-op for a launch without the
-// attribute).  The kernels do not signal their successors early (blocks signal as they exit):
-// measured, an early signal let waiting blocks of the successor take SM slots and made the
-// step slower.
+// finishing: every kernel of the step calls pdl_enter(), which waits until its predecessor
+// has completed and its writes are visible (a no-op for a launch without the attribute), before
+// it reads anything that the predecessor may write.  Only the light loop of the sweep launches
+// signals its successor before it exits (pdl_signal, once a warp has no work left): a signal
+// at a kernel's start let waiting blocks of the successor take SM slots and made the step
+// slower.
 __device__ __forceinline__ void pdl_enter() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+// The calling thread has no work left that the successor's blocks could delay: once every
+// thread of every block has signalled (or exited), the successor's grid may be launched.  Its
+// blocks then take the SM slots this grid frees and load what does not depend on this grid
+// (the bond launch's static part) while its last blocks finish; they still wait in pdl_enter
+// for its completion before reading its results.
+__device__ __forceinline__ void pdl_signal() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // Grid of a kernel that strides over a device-counted range sized for `cap` items: one

@@ -725,11 +725,12 @@ __device__ __forceinline__ void for_light_slots(int* next, int n, int first_bloc
         const int slot = chunk * PER_WARP + wl / L;
         if (slot < n) f(slot);
         __syncwarp();
-        if (warps >= chunks) return;
+        if (warps >= chunks) break;
         int t = 0;
         if (wl == 0) t = atomicAdd(next, 1);
         chunk = warps + __shfl_sync(0xffffffffu, t, 0);
     }
+    pdl_signal();  // nothing left for this warp
 }
 
 template <int L>
