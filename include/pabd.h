@@ -132,8 +132,9 @@ typedef struct {
                                  against all bodies); 1: linear BVH over the boxes' Morton codes
                                  (Sec. 5).  Both give the same pair list. */
     int light_order;          /* bodies with at most 64 bond ends, in each sweep: 1 ordered every
-                                 step by (extended path or not, end count), so a warp's lanes walk
-                                 slices of one length down one path; 2 in body order; 0 the
+                                 step by (extended path or not, end count, most ends first), so a
+                                 warp's lanes walk slices of one length down one path and the
+                                 longest warps start first; 2 in body order; 0 the
                                  library's choice (timed with sweep_mode 0, else ordered).  Other
                                  values: PABD_ERR_ARG.  Results do not depend on it. */
     void* stream;             /* cudaStream_t on which all work is enqueued (NULL: default) */
@@ -194,7 +195,8 @@ typedef struct {
                                  count), rebuilt every step; 0: in body order */
     int64_t tuned;            /* 1 if sweep_mode and light_order were chosen by timing (sweep_mode
                                  0 in the descriptor, no resid_tol, no AL_DISTANCE bonds) */
-    int64_t tune_sweep_ns[4]; /* the autotuner's mean sweep time per candidate, nanoseconds: one
+    int64_t tune_sweep_ns[4]; /* the autotuner's time per sweep for each candidate (the fastest of
+                                 four timed passes over n_iter sweeps), nanoseconds: one
                                  launch per sweep ordered / in body order, a bond and a solve
                                  launch per sweep ordered / in body order (0: not tuned) */
 } pabd_info;
